@@ -1,0 +1,101 @@
+/*
+ * dsoa_oracle.h -- sequential CPU oracle for the Single-Method Multiple-Objects
+ * (SMMO) runtime of DynaSOAr (Springer & Masuhara, ECOOP 2019).
+ *
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test-suite, the package
+ * smoke check and the benchmark's CPU-baseline leg may load this library.  It
+ * shares no code, header, table or helper with the CUDA path.
+ *
+ * What it models: the SMMO semantics of Sec. 2.1 -- `new`, `delete`,
+ * `parallel_new`, and `parallel_do` (run one method on every object of a type
+ * that existed when the do-all started) -- over a plain free-list object store.
+ * Placement is not modelled: the paper's allocator may put an object in any
+ * free slot, and every workload result here is a function of logical ids only.
+ *
+ * Parity status per function (see the test files under tests/ for the pins):
+ *   orc_philox4x32      pinned: published known-answer vectors (Salmon et al. SC'11)
+ *   orc_splitmix64      pinned: published first outputs of SplitMix64 from state 0
+ *   orc_micro_run       pinned: closed forms (x recurrence, expected live counts),
+ *                       brute-force recomputation per object, order independence
+ *   orc_gol_run         pinned: blinker, glider, block still-life, numpy roll-sum
+ *   orc_wator_run       pinned: hand-derived single/two-agent cases, conservation,
+ *                       order independence
+ *   orc_traffic_run     pinned: deterministic (p=0) closed forms of Nagel &
+ *                       Schreckenberg 1992, conservation, brute force on L=16
+ */
+#ifndef DSOA_ORACLE_H
+#define DSOA_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- counter-based generators (published definitions, own code) ---- */
+void     orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], int rounds,
+                        uint32_t out[4]);
+uint64_t orc_splitmix64(uint64_t state);             /* one output for `state` */
+uint64_t orc_sm2(uint64_t a, uint64_t b);            /* sm(sm(a) ^ b)          */
+uint64_t orc_sm3(uint64_t a, uint64_t b, uint64_t c);/* sm(sm2(a,b) ^ c)       */
+
+/* ---- microbench: 1 type {int32 id, float x, int64 tag} ---- */
+typedef struct {
+    uint64_t live;      /* objects alive at the end of the round           */
+    int64_t  sum_id;    /* sum of id over live objects                      */
+    uint64_t sum_tag;   /* wrapping sum of tag                              */
+    uint64_t xor_tag;   /* xor of tag                                       */
+    double   sum_x;     /* sum of (double)x                                 */
+    uint64_t news;      /* allocations this round                           */
+    uint64_t deletes;   /* deallocations this round                         */
+} orc_micro_round;
+
+/* Runs `rounds` rounds of {parallel_new n_per_round; do x=x*1.5f+id; delete
+ * where sm3(seed,id,round)&1}.  x_by_id / live_by_id (length rounds*n_per_round,
+ * nullable) receive the final per-object state.  order_seed != 0 visits every
+ * do-all snapshot in a shuffled order.  Returns 0, or -1 on allocation failure. */
+int orc_micro_run(uint64_t seed, uint32_t n_per_round, uint32_t rounds,
+                  uint64_t order_seed, orc_micro_round* out_rounds,
+                  float* x_by_id, uint8_t* live_by_id);
+
+/* ---- Game of Life as SMMO: Cell per site + Alive agent per live cell ---- */
+/* init: nullable w*h bytes (0/1); when NULL the grid is drawn from `seed`.
+ * out_grid: w*h bytes after `gens` generations.  alive_per_gen: gens+1 counts of
+ * live cells (index 0 = initial); alive_objs_per_gen: gens+1 counts of Alive
+ * objects in the store (must equal the former).  Returns 0 or -1. */
+int orc_gol_run(uint32_t w, uint32_t h, const uint8_t* init, uint64_t seed,
+                uint32_t gens, uint64_t order_seed, uint8_t* out_grid,
+                uint32_t* alive_per_gen, uint32_t* alive_objs_per_gen);
+
+/* ---- Wa-Tor predator-prey ---- */
+typedef struct {
+    uint32_t fish, sharks;              /* populations after the step       */
+    uint32_t fish_births, shark_births; /* objects created during the step  */
+    uint32_t eaten, starved;            /* fish eaten / sharks starved      */
+    uint32_t fish_moves, shark_moves;   /* successful moves                 */
+} orc_wator_step;
+
+/* init: nullable w*h bytes (0 empty, 1 fish, 2 shark; agents start at age 0,
+ * sharks with energy 3).  When NULL the grid is drawn from `seed`.  Step t uses
+ * Philox counters with step index t0 + t.  out_occ: final w*h grid.  stats:
+ * `steps` entries.  Returns 0 or -1. */
+int orc_wator_run(uint32_t w, uint32_t h, const uint8_t* init, uint64_t seed,
+                  uint32_t steps, uint32_t t0, uint64_t order_seed,
+                  uint8_t* out_occ, orc_wator_step* stats);
+
+/* ---- batched Nagel-Schreckenberg rings ---- */
+/* L[i], thr[i]: ring lengths and initial-density thresholds (u32 compare).
+ * init_occ / init_v: nullable sum(L) bytes each; when init_occ is NULL the rings
+ * are drawn from `seed`.  slow_thr / ramp_thr: u32 thresholds of the random
+ * slow-down and of the ramp events (0.2 and 0.05 in the configured workload).
+ * out_occ / out_v: sum(L) bytes (final occupancy and speed per cell).
+ * cars_per_step: nullable (steps+1)*n_inst counts.  Returns 0 or -1. */
+int orc_traffic_run(uint32_t n_inst, const uint32_t* L, const uint32_t* thr,
+                    uint64_t seed, uint32_t steps, uint32_t slow_thr,
+                    uint32_t ramp_thr, const uint8_t* init_occ,
+                    const uint8_t* init_v, uint64_t order_seed,
+                    uint8_t* out_occ, uint8_t* out_v, uint32_t* cars_per_step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
