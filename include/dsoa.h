@@ -1,0 +1,186 @@
+/*
+ * dsoa.h -- C ABI of the GB300 SMMO runtime: a lock-free device object
+ * allocator over a heap of 64-slot SOA blocks managed by hierarchical 64-bit
+ * bitmaps, plus the parallel do-all (DynaSOAr, Springer & Masuhara, ECOOP 2019).
+ *
+ * Conventions for every entry point below:
+ *   - Return value: DSOA_OK (0) or a negative DSOA_ERR_* code.  Nothing throws.
+ *   - Pointers named *_host are host memory; *_dev are device memory of the
+ *     heap's GPU.  The caller owns every buffer it passes in.
+ *   - All GPU work is stream-ordered on the heap's stream (a cudaStream_t passed
+ *     as void*, 0 = legacy default stream) and asynchronous, unless the
+ *     description says "synchronous".
+ *   - Device-side failures (out of memory inside a kernel, a spin limit reached,
+ *     a double free, a bad handle) never trap: they set bits in a sticky device
+ *     error word that dsoa_get_error() reads and clears.
+ *   - A heap is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef DSOA_H
+#define DSOA_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSOA_OK 0
+#define DSOA_ERR_INVALID_ARG (-1)
+#define DSOA_ERR_FROZEN (-2)          /* type registration after the layout froze */
+#define DSOA_ERR_TOO_MANY_TYPES (-3)
+#define DSOA_ERR_OOM (-4)             /* heap too small for its own metadata      */
+#define DSOA_ERR_CUDA (-5)            /* a CUDA runtime call failed               */
+#define DSOA_ERR_NOT_FROZEN (-6)      /* operation needs a frozen layout          */
+#define DSOA_ERR_UNKNOWN_METHOD (-7)  /* method / constructor id not built in     */
+#define DSOA_ERR_CAPTURE (-8)         /* synchronous call during stream capture   */
+
+/* bits of the sticky device error word (dsoa_get_error) */
+#define DSOA_DEV_OOM 1          /* an allocation found no free block: handle 0      */
+#define DSOA_DEV_SPIN 2         /* a bounded retry loop gave up                     */
+#define DSOA_DEV_DOUBLE_FREE 4  /* a slot was freed twice                           */
+#define DSOA_DEV_BAD_HANDLE 8   /* a handle did not decode to a valid type/block    */
+
+#define DSOA_MAX_TYPES 16       /* registered types per heap                        */
+#define DSOA_MAX_FIELDS 12      /* fields per type                                  */
+#define DSOA_SLOTS 64           /* object slots per block (Sec. 3.1, 64-bit bitmap) */
+
+/* Object handle (the paper's "fake pointer", Sec. 3.3, with the 35-bit address
+ * trick replaced by a block index): [63:56] type id + 1, [55:6] block index,
+ * [5:0] slot.  0 is the null handle. */
+typedef uint64_t dsoa_obj;
+typedef struct dsoa_heap dsoa_heap;
+typedef struct dsoa_graph dsoa_graph;
+
+/* Create a heap of `bytes` device bytes allocated with cudaMalloc, driven on
+ * `stream`.  The byte budget covers blocks and all metadata (bitmaps, block
+ * list, scratch).  Blocks are carved when the layout freezes (first allocation
+ * or dsoa_heap_freeze).  Sec. 3 ("the heap is divided into M blocks"). */
+int dsoa_heap_create(size_t bytes, void* stream, dsoa_heap** out);
+
+/* Same over caller-owned device memory `dev_ptr` (256-byte aligned, `bytes`
+ * long, e.g. a torch tensor); dsoa_heap_destroy does not free it. */
+int dsoa_heap_create_from(void* dev_ptr, size_t bytes, void* stream, dsoa_heap** out);
+
+/* Register an object type with `nfields` fields of `field_bytes[i]` bytes each
+ * (1, 2, 4, 8 or 16).  Each field becomes one 64-element SOA column inside a
+ * block, 128-byte aligned (Sec. 2.2 "clustered layout", Sec. 3.1).  Writes the
+ * new type id (0, 1, ...) to *type_out.  Fails with DSOA_ERR_FROZEN after the
+ * layout froze. */
+int dsoa_register_type(dsoa_heap* h, const uint32_t* field_bytes, int nfields, int* type_out);
+
+/* Freeze the layout: block bytes = largest registered type's data segment;
+ * M = blocks that fit with their metadata.  Initialises the bitmaps (every block
+ * free, Sec. 3.4).  Called implicitly by the first allocating call. */
+int dsoa_heap_freeze(dsoa_heap* h);
+
+/* Query the frozen layout (any pointer may be NULL). */
+int dsoa_heap_info(dsoa_heap* h, uint64_t* num_blocks, uint32_t* block_bytes,
+                   uint32_t* num_levels, uint64_t* metadata_bytes);
+
+/* Column byte offset of field `field` of `type` inside a block's data segment. */
+int dsoa_field_offset(dsoa_heap* h, int type, int field, uint32_t* offset_out);
+
+/* parallel_new<T>(n) (Sec. 2.1): one kernel, n logical threads; thread i
+ * allocates one object of `type` and runs built-in constructor `ctor_id` with
+ * index i and the `args_bytes` bytes at `args_host` (copied at launch).  A
+ * thread whose allocation fails (heap full) gets a null handle and sets
+ * DSOA_DEV_OOM.  Constructor ids and argument structs: dsoa_apps.h. */
+int dsoa_parallel_new(dsoa_heap* h, int type, uint64_t n, int ctor_id,
+                      const void* args_host, size_t args_bytes);
+
+/* parallel_do<T, f> (Sec. 2.1, Sec. 3.7): snapshot the allocation bitmaps of
+ * every block of `type`, compact the block list R from the type's allocated-
+ * block bitmap (hierarchical bitmap scan + prefix sum, Sec. 4.1.5, Fig. 7),
+ * then run built-in method `method_id` on every object in the snapshot.
+ * Objects created by the method are not visited; the method may delete `this`
+ * and objects of other types. */
+int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args_host,
+                     size_t args_bytes);
+
+/* Run built-in plain kernel `kernel_id` (dsoa_apps.h) with n logical threads:
+ * an ordinary CUDA kernel that may call device new/delete (Sec. 2.1, "new and
+ * destroy are device functions callable from GPU code"). */
+int dsoa_run_kernel(dsoa_heap* h, int kernel_id, uint64_t n, const void* args_host,
+                    size_t args_bytes);
+
+/* Enumerate only (the first two kernels of dsoa_parallel_do): after the call,
+ * R_dev[0..*r_dev) lists the blocks of `type` in increasing order and
+ * occ_dev[i] their occupied-slot masks.  The three pointers are library-owned
+ * and valid until the next enumeration on this heap.  Used by user do-all
+ * kernels written against dsoa_device.cuh. */
+int dsoa_enumerate(dsoa_heap* h, int type, const uint32_t** R_dev,
+                   const uint64_t** occ_dev, const uint32_t** r_dev);
+
+/* Number of live objects of `type` (popcounts of the slot bitmaps of the
+ * blocks in the type's allocated-block bitmap).  Synchronous: waits for the
+ * heap's stream.  Not allowed during stream capture. */
+int dsoa_count(dsoa_heap* h, int type, uint64_t* out_host);
+
+/* Same, written to device memory `out_dev` (uint64); graph-capturable. */
+int dsoa_count_async(dsoa_heap* h, int type, uint64_t* out_dev);
+
+/* Number of free blocks (popcount of the free-block bitmap) to `out_dev`
+ * (uint64); graph-capturable.  Used for admission control. */
+int dsoa_free_blocks_async(dsoa_heap* h, uint64_t* out_dev);
+
+/* Read and clear the sticky device error word (DSOA_DEV_* bits).  Synchronous. */
+int dsoa_get_error(dsoa_heap* h, int* bits_out);
+
+/* Check the allocator invariants at quiescence (Sec. 3.4, App. A.4
+ * "container consistency"): writes DSOA_CHECK_COUNT counters to out_host, all
+ * zero when the heap is consistent.  Synchronous. */
+#define DSOA_CHECK_HIER 0          /* upper bit != (lower container != 0)          */
+#define DSOA_CHECK_FREE_XOR 1      /* block neither free nor allocated, or both    */
+#define DSOA_CHECK_MULTI_TYPE 2    /* block in two types' allocated bitmaps        */
+#define DSOA_CHECK_ACTIVE_SUBSET 3 /* active bit without allocated bit             */
+#define DSOA_CHECK_TYPE 4          /* allocated[T] block whose type id is not T    */
+#define DSOA_CHECK_FREE_WORD 5     /* free block whose slot word is not all-taken  */
+#define DSOA_CHECK_EMPTY_ALLOC 6   /* allocated block with no object               */
+#define DSOA_CHECK_ACTIVE_EXACT 7  /* active != (allocated and not full)           */
+#define DSOA_CHECK_TAIL_BITS 8     /* bits beyond M set                            */
+#define DSOA_CHECK_COUNT 9
+int dsoa_check(dsoa_heap* h, uint64_t* out_host);
+
+/* Copy the raw allocator state to host memory (synchronous), for external
+ * checkers: slot words (M x u64, 1 = free slot), block types (M x u32), then
+ * every hierarchical bitmap (free, then allocated[T], active[T] per type; each
+ * bitmap is its levels from level 0 upward, bitmap_words u64 in total).
+ * *bytes_needed receives the size; pass out_host = NULL to query it. */
+int dsoa_export_state(dsoa_heap* h, void* out_host, size_t capacity, size_t* bytes_needed,
+                      uint64_t* bitmap_words);
+
+/* Device-side view of the heap for user kernels built with dsoa_device.cuh:
+ * copies the struct dsoa_ctx (size ctx_bytes must match) to ctx_out_host. */
+int dsoa_get_ctx(dsoa_heap* h, void* ctx_out_host, size_t ctx_bytes);
+
+/* Stream capture of the heap's stream into a CUDA graph, for step loops. */
+int dsoa_graph_begin(dsoa_heap* h);
+int dsoa_graph_end(dsoa_heap* h, dsoa_graph** out);
+int dsoa_graph_launch(dsoa_graph* g, void* stream);
+int dsoa_graph_destroy(dsoa_graph* g);
+
+/* Launch shape of do-all and scan kernels (0 keeps the current value):
+ * threads per CTA of the do-all (multiple of 64), CTAs per SM of the persistent
+ * do-all grid, slots handled per thread by vectorised methods (1, 2 or 4), and
+ * allocated-bitmap level-1 words per CTA of the compaction kernel. */
+int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
+                    int slots_per_thread, int scan_tiles_per_cta);
+
+/* Ablation switches of Sec. 6.4 (Fig. 10c): DSOA_FLAG_NO_COALESCE (1) turns
+ * off allocation request coalescing, DSOA_FLAG_NO_ROTATE (2) turns off bitmap
+ * rotation.  Takes effect for launches issued after the call. */
+int dsoa_set_flags(dsoa_heap* h, uint32_t flags);
+
+/* Number of kernels this heap has launched so far (host-side counter). */
+int dsoa_launch_count(dsoa_heap* h, uint64_t* out_host);
+
+/* Destroy the heap (synchronous); frees library-allocated device memory. */
+int dsoa_heap_destroy(dsoa_heap* h);
+
+/* Human-readable name of an error code. */
+const char* dsoa_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,126 @@
+/*
+ * dsoa_apps.h -- built-in constructors, do-all methods and plain kernels of the
+ * workloads, addressed by id through dsoa_parallel_new / dsoa_parallel_do /
+ * dsoa_run_kernel (dsoa.h).  Each id takes one argument struct, copied by value
+ * at launch (args_bytes must equal its sizeof).  Device pointers inside the
+ * structs are caller-owned and must stay valid until the work has run.
+ *
+ * Workloads (Table 1 of the paper; rules as stated per section below):
+ *   microbench  one type {int32 id, float x, int64 tag}
+ *   game of life  Cell per site + Alive agent per live cell, B3/S23 torus
+ *   wa-tor      Fish / Shark agents on a torus with per-cell occupancy
+ *   traffic     Nagel-Schreckenberg cars on batched rings
+ */
+#ifndef DSOA_APPS_H
+#define DSOA_APPS_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------- microbench (type fields: 0 id i32, 1 x f32, 2 tag u64) ---------- */
+#define DSOA_C_MICRO 100              /* ctor i: id = id_base + i, x = 0, tag = sm2(seed,id) */
+#define DSOA_M_MICRO_SCALE 101        /* x = x * 1.5f + (float)id, 128-bit vectorised       */
+#define DSOA_M_MICRO_SCALE_SCALAR 102 /* same, one slot per thread (generic do-all kernel)  */
+#define DSOA_M_MICRO_DELETE 103       /* delete this where sm3(seed, id, round) is odd     */
+#define DSOA_M_MICRO_GATHER 104       /* x_out[id] = x, live_out[id] = 1                   */
+#define DSOA_M_MICRO_STATS 105        /* accumulate dsoa_micro_stats                        */
+#define DSOA_M_MICRO_SCALE_TMA 106    /* same as SCALE, columns staged by bulk async copies */
+typedef struct {
+    uint64_t seed;       /* SplitMix64 key                                   */
+    uint32_t id_base;    /* constructor: first id                            */
+    uint32_t round;      /* delete: round index                              */
+    float* x_out;        /* gather: [n_ids] (device)                         */
+    uint8_t* live_out;   /* gather: [n_ids] (device)                         */
+    uint64_t n_ids;      /* gather: bound of id                              */
+    void* stats;         /* stats: dsoa_micro_stats* (device, pre-zeroed)    */
+} dsoa_micro_args;
+typedef struct {
+    unsigned long long live, sum_id, sum_tag, xor_tag;
+    double sum_x;
+} dsoa_micro_stats;
+
+/* ---------------- instances of the grid workloads (game of life, wa-tor) ----------- */
+/* One entry per instance slot; the table lives in device memory.  Objects keep
+ * (inst, cell) so that one launch serves every instance of a batch. */
+#define DSOA_INST_IDLE 0u    /* slot unused / finished: methods leave it alone     */
+#define DSOA_INST_RUN 1u     /* stepping                                           */
+#define DSOA_INST_KILL 2u    /* KILL methods delete its objects                    */
+typedef struct {
+    uint64_t* cellmap;   /* [w*h] game of life: Cell handle; wa-tor: agent handle  */
+    uint8_t* occ;        /* [w*h] game of life: READ output; wa-tor: 0/1/2 grid    */
+    uint32_t* claim;     /* [w*h] wa-tor: move claims, all 0xFFFFFFFF between steps */
+    uint64_t seed;       /* Philox key of the instance                             */
+    uint32_t w, h;       /* torus size                                             */
+    uint32_t t;          /* the instance's own step index                          */
+    uint32_t state;      /* DSOA_INST_*                                            */
+} dsoa_inst;
+
+/* ---------------- game of life: Cell {0 inst u32, 1 cell u32, 2 count u32, 3 alive u8};
+ *                  Alive {0 inst u32, 1 cell u32} ------------------------------------ */
+#define DSOA_C_GOL_CELL 200      /* ctor i = cell of instance `target`; initial state from
+                                    `init` (nullable) or Philox(seed; 0xFFFFFFFF, i, 0, 0)
+                                    < 2^30; creates the Alive agent of a live cell        */
+#define DSOA_M_GOL_SPREAD 201    /* Alive: add 1 to the 8 neighbours' counts              */
+#define DSOA_M_GOL_REAP 202      /* Alive: die (delete this) unless count is 2 or 3       */
+#define DSOA_M_GOL_DECIDE 203    /* Cell: dead with count 3 -> new Alive; count = 0       */
+#define DSOA_M_GOL_READ 204      /* Cell: occ[cell] = alive                               */
+#define DSOA_M_GOL_KILL 205      /* Cell or Alive of a KILL instance: delete this         */
+#define DSOA_K_GOL_ADVANCE 250   /* n = n_inst: t += 1 for RUN instances                  */
+typedef struct {
+    dsoa_inst* inst;     /* [n_inst] device table                                   */
+    const uint8_t* init; /* ctor: nullable [w*h] of `target`                        */
+    uint32_t n_inst;
+    uint32_t target;     /* ctor: instance slot being populated                     */
+    int32_t cell_type, alive_type;
+} dsoa_gol_args;
+
+/* ---------------- wa-tor: Fish {0 inst, 1 cell, 2 age, 3 target};
+ *                  Shark {0 inst, 1 cell, 2 age, 3 energy, 4 target, 5 eat} (u32) ---- */
+#define DSOA_M_WATOR_FISH_CHOOSE 301   /* pick an empty neighbour, atomicMin claim       */
+#define DSOA_M_WATOR_FISH_MOVE 302     /* winners move; breeding age 3 leaves a newborn  */
+#define DSOA_M_WATOR_SHARK_CHOOSE 303  /* prefer a fish neighbour, else an empty one     */
+#define DSOA_M_WATOR_SHARK_MOVE 304    /* eat (energy 3) or lose 1; breed at 10; starve  */
+#define DSOA_M_WATOR_KILL 305          /* agent of a KILL instance: delete this          */
+#define DSOA_K_WATOR_INIT 350          /* n = w*h of `target`: agents from `init` (nullable,
+                                          0/1/2) or Philox(seed; 0xFFFFFFFF, c, 0, 0) vs
+                                          0.30 / 0.35 thresholds                          */
+#define DSOA_K_WATOR_ADVANCE 351       /* n = n_inst: t += 1 for RUN instances            */
+typedef struct {
+    dsoa_inst* inst;
+    const uint8_t* init;
+    uint32_t n_inst;
+    uint32_t target;
+    int32_t fish_type, shark_type;
+} dsoa_wator_args;
+
+/* ---------------- traffic: Car {0 ring u32, 1 pos u32, 2 v u32} --------------------- */
+#define DSOA_M_TRAFFIC_MOVE 401    /* accelerate, brake to gap, random slow-down, move,
+                                      leave at the off-ramp L/2 with prob ramp_thr/2^32 */
+#define DSOA_M_TRAFFIC_READ 402    /* vel_out[base+pos] = v                              */
+#define DSOA_K_TRAFFIC_INIT 450    /* n = total cells: cars from `init_occ` (nullable) or
+                                      Philox(seed; 0xFFFFFFFF, j, ring, 0) < thr          */
+#define DSOA_K_TRAFFIC_CLEAR 451   /* n = total cells: next occupancy buffer = 0         */
+#define DSOA_K_TRAFFIC_ONRAMP 452  /* n = rings: new car at an empty cell 0              */
+#define DSOA_K_TRAFFIC_ADVANCE 453 /* n = 1: t += 1                                      */
+typedef struct {
+    uint8_t* occ0;               /* [total] occupancy, even steps read occ0           */
+    uint8_t* occ1;               /* [total] occupancy, odd steps read occ1            */
+    uint8_t* vel_out;            /* [total] READ output (pre-zeroed)                   */
+    const uint64_t* ring_base;   /* [n_rings+1] first cell of each ring               */
+    const uint32_t* ring_thr;    /* [n_rings] initial density threshold               */
+    const uint8_t* init_occ;     /* nullable [total]                                   */
+    const uint8_t* init_v;       /* nullable [total]                                   */
+    uint32_t* t_dev;             /* [1] step index                                     */
+    uint64_t seed;
+    uint32_t n_rings;
+    uint32_t slow_thr;           /* 858993459 = floor(0.2 * 2^32)                      */
+    uint32_t ramp_thr;           /* 214748364 = floor(0.05 * 2^32)                     */
+    int32_t car_type;
+} dsoa_traffic_args;
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,420 @@
+/*
+ * dsoa_device.cuh -- device side of the GB300 SMMO runtime (header only).
+ *
+ * The lock-free allocator of DynaSOAr (Springer & Masuhara, ECOOP 2019,
+ * Sec. 3-4 and App. A) for sm_103a, usable from any CUDA kernel:
+ *
+ *   dsoa_new(ctx, type)       -> handle or 0          Alg. 1 (+ Sec. 4.2 coalescing)
+ *   dsoa_delete(ctx, handle)                          Alg. 2
+ *   dsoa_field<F>(ctx, h, i)  -> F&  (SOA column)      Sec. 3.3, App. B
+ *
+ * Heap layout (one GPU, frozen at the first allocation):
+ *   data[M * block_bytes]  per block 64 slots in SOA: column i of type T at
+ *                          byte col_off[T][i], 64 * field_bytes long, 128 B
+ *                          aligned (Sec. 2.2 clustered layout)
+ *   slot[M]   u64 per block, bit s = 1 iff slot s is FREE.  The paper keeps
+ *             1 = allocated; the complement lets a reservation be one
+ *             atomicAnd and a free one atomicOr.  Every rule of Alg. 7-10 is
+ *             restated in this polarity below.
+ *   btype[M]  u32 block type id
+ *   bm        hierarchical bitmaps (Sec. 4.1): free-block, and per type the
+ *             allocated-block and active-block bitmaps; each is its levels,
+ *             level 0 first, ceil(n/64) u64 containers per level.
+ *
+ * Every spin of the paper (set/clear "retry until changed", the allocation
+ * retry loop, invalidation retries) is bounded; on the bound the thread sets
+ * DSOA_DEV_SPIN in the sticky error word and gives up.  Nothing traps.
+ */
+#ifndef DSOA_DEVICE_CUH
+#define DSOA_DEVICE_CUH
+
+#include <stdint.h>
+
+#include "dsoa.h"
+
+#define DSOA_MAX_LEVELS 6
+#define DSOA_ALL ((unsigned long long)~0ull)
+
+/* Bounds of every retry loop (legal workloads stay far below them; a thread
+ * that reaches one sets DSOA_DEV_SPIN and gives up, so no kernel can hang):
+ * one blocking bitmap op or invalidation waits at most ~16 ms, one
+ * allocation makes at most DSOA_ALLOC_ROUNDS block selections, each with at
+ * most DSOA_TAKE_ATTEMPTS find-and-clear attempts on the free-block bitmap. */
+#ifndef DSOA_SPIN_LIMIT
+#define DSOA_SPIN_LIMIT (1u << 16)
+#endif
+#ifndef DSOA_ALLOC_ROUNDS
+#define DSOA_ALLOC_ROUNDS (1u << 12)
+#endif
+#ifndef DSOA_TAKE_ATTEMPTS
+#define DSOA_TAKE_ATTEMPTS 256u
+#endif
+#ifndef DSOA_LOOKUP_ATTEMPTS
+#define DSOA_LOOKUP_ATTEMPTS 5            /* active-block lookups before slow path  */
+#endif
+
+/* Device view of a heap.  Plain data, passed to kernels by value. */
+struct dsoa_ctx {
+    char* data;                          /* block b at data + b * block_bytes      */
+    unsigned long long* slot;            /* [M] free-slot bitmaps                  */
+    uint32_t* btype;                     /* [M] block type ids                     */
+    unsigned long long* bm;              /* all hierarchical bitmaps               */
+    int* err;                            /* sticky DSOA_DEV_* bits                 */
+    uint64_t M;                          /* number of blocks                       */
+    uint64_t bm_stride;                  /* u64 words per hierarchical bitmap      */
+    uint64_t lvl_off[DSOA_MAX_LEVELS];   /* word offset of level l in a bitmap     */
+    uint64_t lvl_words[DSOA_MAX_LEVELS]; /* containers at level l                  */
+    uint32_t nlevels;
+    uint32_t block_bytes;
+    uint32_t ntypes;
+    uint32_t seed;                       /* rotation seed of this launch           */
+    uint32_t flags;                      /* DSOA_FLAG_*                            */
+    uint16_t col_off[DSOA_MAX_TYPES][DSOA_MAX_FIELDS];
+};
+
+#define DSOA_FLAG_NO_COALESCE 1u          /* ablation: one request per leader       */
+#define DSOA_FLAG_NO_ROTATE 2u            /* ablation: plain find-first-set         */
+
+/* bitmap ids inside ctx.bm */
+__host__ __device__ __forceinline__ uint32_t dsoa_bm_free() { return 0u; }
+__host__ __device__ __forceinline__ uint32_t dsoa_bm_alloc(uint32_t t) { return 1u + 2u * t; }
+__host__ __device__ __forceinline__ uint32_t dsoa_bm_active(uint32_t t) { return 2u + 2u * t; }
+
+/* ---- handles (Sec. 3.3 object pointers, App. B address computation) ---- */
+__host__ __device__ __forceinline__ dsoa_obj dsoa_make_handle(uint32_t t, uint64_t bid, uint32_t s) {
+    return ((uint64_t)(t + 1u) << 56) | (bid << 6) | (uint64_t)s;
+}
+__host__ __device__ __forceinline__ uint32_t dsoa_h_type(dsoa_obj h) { return (uint32_t)(h >> 56) - 1u; }
+__host__ __device__ __forceinline__ uint64_t dsoa_h_block(dsoa_obj h) { return (h >> 6) & ((1ull << 50) - 1ull); }
+__host__ __device__ __forceinline__ uint32_t dsoa_h_slot(dsoa_obj h) { return (uint32_t)(h & 63u); }
+
+#ifdef __CUDACC__
+
+/* ---- memory-model helpers: bitmap words are read at device scope, never
+ * through the non-coherent L1 (App. A: "volatile or atomic") ---- */
+__device__ __forceinline__ unsigned long long dsoa_ld(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t dsoa_ld32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void dsoa_st(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void dsoa_st32(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t dsoa_lane() {
+    uint32_t l;
+    asm("mov.u32 %0, %%laneid;" : "=r"(l));
+    return l;
+}
+__device__ __forceinline__ void dsoa_raise(const dsoa_ctx& c, int bits) { atomicOr(c.err, bits); }
+
+/* One wait step of a bounded spin; false once the bound is reached (error set). */
+__device__ __forceinline__ bool dsoa_backoff(const dsoa_ctx& c, uint32_t& spins) {
+    if (++spins >= DSOA_SPIN_LIMIT) { dsoa_raise(c, DSOA_DEV_SPIN); return false; }
+    if (spins > 8) __nanosleep(spins < 64 ? 32u : 256u);
+    return true;
+}
+
+__device__ __forceinline__ uint32_t dsoa_hash(uint32_t x) {
+    /* integer finaliser (xor-shift / multiply, "lowbias32" constants) */
+    x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ unsigned long long dsoa_rotr(unsigned long long w, uint32_t r) {
+    r &= 63u;
+    return r ? (w >> r) | (w << (64u - r)) : w;
+}
+__device__ __forceinline__ unsigned long long dsoa_rotl(unsigned long long w, uint32_t r) {
+    r &= 63u;
+    return r ? (w << r) | (w >> (64u - r)) : w;
+}
+/* position of the (n+1)-th lowest set bit of w (n < popc(w)), Sec. 4.3 */
+__device__ __forceinline__ uint32_t dsoa_nth_set(unsigned long long w, uint32_t n) {
+    const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+    const uint32_t plo = __popc(lo);
+    if (n < plo) return __fns(lo, 0u, (int)n + 1);
+    return 32u + __fns(hi, 0u, (int)(n - plo) + 1);
+}
+/* mask of the lowest k set bits of w */
+__device__ __forceinline__ unsigned long long dsoa_lowest_k(unsigned long long w, uint32_t k) {
+    if ((uint32_t)__popcll(w) <= k) return w;
+    if (k == 0) return 0ull;
+    const uint32_t p = dsoa_nth_set(w, k - 1u);
+    return p == 63u ? w : (w & ((2ull << p) - 1ull));
+}
+
+__device__ __forceinline__ unsigned long long* dsoa_level(const dsoa_ctx& c, uint32_t b, uint32_t l) {
+    return c.bm + (uint64_t)b * c.bm_stride + c.lvl_off[l];
+}
+
+/* ------------------------------------------------------------------------
+ * Hierarchical bitmap operations (Sec. 4.1, Alg. 3-4, App. A.4).
+ * clear/set at level l; `blocking` = the paper's clear(pos)/set(pos) that
+ * retries until this thread changed the bit; otherwise the try_ variant.
+ * A thread that empties a container (clear-last) or fills an empty one
+ * (set-first) propagates to the next level with the blocking variant.
+ * Returns whether this thread changed the level-l bit.
+ * ------------------------------------------------------------------------ */
+__device__ inline bool dsoa_bm_clear(const dsoa_ctx& c, uint32_t b, uint64_t pos,
+                                     bool blocking, uint32_t l = 0) {
+    bool first = true, changed = false;
+    for (; l < c.nlevels; ++l) {
+        unsigned long long* w = dsoa_level(c, b, l) + (pos >> 6);
+        const unsigned long long m = 1ull << (pos & 63u);
+        unsigned long long prev;
+        uint32_t spins = 0;
+        for (;;) {
+            prev = atomicAnd(w, ~m);
+            if (prev & m) break;
+            if (!blocking) return false;
+            if (!dsoa_backoff(c, spins)) return changed;
+        }
+        if (first) { changed = true; first = false; }
+        if (prev != m) break;          /* container still has set bits */
+        pos >>= 6;
+        blocking = true;
+    }
+    return changed;
+}
+
+__device__ inline bool dsoa_bm_set(const dsoa_ctx& c, uint32_t b, uint64_t pos, uint32_t l = 0) {
+    bool first = true, changed = false;
+    for (; l < c.nlevels; ++l) {
+        unsigned long long* w = dsoa_level(c, b, l) + (pos >> 6);
+        const unsigned long long m = 1ull << (pos & 63u);
+        unsigned long long prev;
+        uint32_t spins = 0;
+        for (;;) {
+            prev = atomicOr(w, m);
+            if (!(prev & m)) break;
+            if (!dsoa_backoff(c, spins)) return changed;
+        }
+        if (first) { changed = true; first = false; }
+        if (prev != 0ull) break;       /* container was already non-empty */
+        pos >>= 6;
+    }
+    return changed;
+}
+
+/* try_find_set (Alg. 4) with bitmap rotation (Sec. 4.2): top-down; at every
+ * level the container is rotated by a hash-derived amount before ffs, so
+ * different warps start at different bits.  -1 = FAIL (possibly spurious
+ * while levels are transiently inconsistent). */
+__device__ inline int64_t dsoa_bm_find(const dsoa_ctx& c, uint32_t b, uint32_t h) {
+    uint64_t idx = 0;
+    const bool rot = !(c.flags & DSOA_FLAG_NO_ROTATE);
+    for (int l = (int)c.nlevels - 1; l >= 0; --l) {
+        const unsigned long long w = dsoa_ld(dsoa_level(c, b, (uint32_t)l) + idx);
+        if (!w) return -1;
+        const uint32_t r = rot ? ((h >> ((uint32_t)l * 5u)) ^ (h >> 27)) & 63u : 0u;
+        const uint32_t bit = ((uint32_t)__ffsll((long long)dsoa_rotr(w, r)) - 1u + r) & 63u;
+        idx = idx * 64u + bit;
+    }
+    return (int64_t)idx;
+}
+
+/* clear() = find-and-clear an arbitrary set bit (Sec. 4.1.2).  -1 when the
+ * bitmap is empty at the top (OOM for the free-block bitmap), -2 when
+ * DSOA_TAKE_ATTEMPTS attempts lost every race (the caller retries). */
+__device__ inline int64_t dsoa_bm_take(const dsoa_ctx& c, uint32_t b, uint32_t h) {
+    for (uint32_t a = 0; a < DSOA_TAKE_ATTEMPTS; ++a) {
+        const int64_t pos = dsoa_bm_find(c, b, dsoa_hash(h + a * 0x9E3779B9u));
+        if (pos >= 0) {
+            if (dsoa_bm_clear(c, b, (uint64_t)pos, false)) return pos;
+        } else if (dsoa_ld(dsoa_level(c, b, c.nlevels - 1)) == 0ull) {
+            return -1;
+        }
+        if (a > 8) __nanosleep(64u);
+    }
+    return -2;
+}
+
+/* ------------------------------------------------------------------------
+ * Block operations (App. A.1-A.2), free-slot polarity.
+ * ------------------------------------------------------------------------ */
+
+/* initialize_block<T> (Alg. 9): type first, fence, then all 64 slots free. */
+__device__ inline void dsoa_block_init(const dsoa_ctx& c, uint64_t bid, uint32_t t) {
+    dsoa_st32(&c.btype[bid], t);
+    __threadfence();
+    dsoa_st(&c.slot[bid], DSOA_ALL);
+}
+
+/* invalidate + delete an emptied block (Alg. 2 lines 7-11 with Alg. 10):
+ * take every slot with one atomicAnd(0).  Success iff all 64 were free; then
+ * the block leaves active[t] and allocated[t] and returns to the free bitmap.
+ * Otherwise give back exactly the slots taken (atomicOr(before)); if another
+ * thread freed a slot meanwhile it saw a "first free" and will set the active
+ * bit, so the deferred deactivation is done here; retry if the block is empty
+ * again. */
+__device__ inline void dsoa_block_invalidate(const dsoa_ctx& c, uint64_t bid) {
+    for (uint32_t it = 0; it < DSOA_SPIN_LIMIT; ++it) {
+        const unsigned long long before = atomicAnd(&c.slot[bid], 0ull);
+        if (before == DSOA_ALL) {
+            const uint32_t t = dsoa_ld32(&c.btype[bid]);
+            dsoa_bm_clear(c, dsoa_bm_active(t), bid, true);
+            dsoa_bm_clear(c, dsoa_bm_alloc(t), bid, true);
+            dsoa_bm_set(c, dsoa_bm_free(), bid);
+            return;
+        }
+        if (before == 0ull) return;    /* nothing taken: someone else owns it */
+        const unsigned long long rb = atomicOr(&c.slot[bid], before);
+        if (rb != 0ull) {
+            const uint32_t t = dsoa_ld32(&c.btype[bid]);
+            dsoa_bm_clear(c, dsoa_bm_active(t), bid, true);
+        }
+        if ((rb | before) != DSOA_ALL) return;
+    }
+    dsoa_raise(c, DSOA_DEV_SPIN);
+}
+
+/* Block::deallocate for a set of slots (Alg. 8, multi-slot form used by
+ * request coalescing and by rollback).  `t` is the block's type. */
+__device__ inline void dsoa_block_release(const dsoa_ctx& c, uint32_t t, uint64_t bid,
+                                          unsigned long long bits) {
+    const unsigned long long before = atomicOr(&c.slot[bid], bits);
+    if (before & bits) {
+        dsoa_raise(c, DSOA_DEV_DOUBLE_FREE);
+        bits &= ~before;
+        if (!bits) return;
+    }
+    if (before == 0ull) dsoa_bm_set(c, dsoa_bm_active(t), bid);            /* FIRST */
+    if ((before | bits) == DSOA_ALL) dsoa_block_invalidate(c, bid);          /* EMPTY */
+}
+
+/* Leader part of allocate<T> (Alg. 1 with request coalescing, Sec. 4.2):
+ * reserve up to `want` slots of type t in ONE block.  Block selection tries
+ * the active bitmap DSOA_LOOKUP_ATTEMPTS times with rotated starts, else takes
+ * a free block (slow path).  A reservation is one atomicAnd of the chosen
+ * slot bits; the thread whose reservation empties the free-slot word marks
+ * the block inactive; a type change is rolled back.  Returns the reserved
+ * slot mask (0 on OOM or spin bound) and the block in *bid_out. */
+__device__ inline unsigned long long dsoa_leader_reserve(const dsoa_ctx& c, uint32_t t, uint32_t want,
+                                                         uint32_t h, uint64_t* bid_out) {
+    const uint32_t act = dsoa_bm_active(t);
+    const bool rot = !(c.flags & DSOA_FLAG_NO_ROTATE);
+    for (uint32_t round = 0; round < DSOA_ALLOC_ROUNDS; ++round) {
+        int64_t bid = -1;
+        for (uint32_t a = 0; a < DSOA_LOOKUP_ATTEMPTS && bid < 0; ++a)
+            bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
+        if (bid < 0) {
+            bid = dsoa_bm_take(c, dsoa_bm_free(), h ^ round);
+            if (bid == -2) continue;
+            if (bid < 0) { dsoa_raise(c, DSOA_DEV_OOM); return 0ull; }
+            dsoa_block_init(c, (uint64_t)bid, t);
+            dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid);
+            dsoa_bm_set(c, act, (uint64_t)bid);
+        }
+        const unsigned long long w = dsoa_ld(&c.slot[bid]);
+        if (!w) continue;
+        const uint32_t r = rot ? (dsoa_hash(h + round) & 63u) : 0u;
+        const unsigned long long mask = dsoa_rotl(dsoa_lowest_k(dsoa_rotr(w, r), want), r);
+        const unsigned long long before = atomicAnd(&c.slot[bid], ~mask);
+        const unsigned long long got = before & mask;
+        if (!got) continue;
+        __threadfence();   /* pairs with the fence of dsoa_block_init */
+        const uint32_t bt = dsoa_ld32(&c.btype[bid]);
+        if ((before & ~mask) == 0ull) dsoa_bm_clear(c, dsoa_bm_active(bt), (uint64_t)bid, true);
+        if (bt != t) {                 /* block replaced by another type: roll back */
+            dsoa_block_release(c, bt, (uint64_t)bid, got);
+            continue;
+        }
+        *bid_out = (uint64_t)bid;
+        return got;
+    }
+    dsoa_raise(c, DSOA_DEV_SPIN);
+    return 0ull;
+}
+
+/* new(d_allocator) T (Sec. 2.1; Alg. 1): callable from any kernel, any
+ * divergence.  Same-type requests of a warp are coalesced (__match_any_sync):
+ * the lowest lane of each group reserves slots for the whole group, block by
+ * block, and lane k of the group takes the k-th reserved slot.  Returns the
+ * handle, or 0 if the heap is out of blocks (DSOA_DEV_OOM set). */
+__device__ inline dsoa_obj dsoa_new(const dsoa_ctx& c, uint32_t t) {
+    const uint32_t lane = dsoa_lane();
+    const uint32_t active = __activemask();
+    const uint32_t peers = (c.flags & DSOA_FLAG_NO_COALESCE) ? (1u << lane) : __match_any_sync(active, t);
+    const uint32_t leader = (uint32_t)__ffs((int)peers) - 1u;
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    const uint32_t want = (uint32_t)__popc(peers);
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t h0 = dsoa_hash(gwarp * 0x85EBCA6Bu ^ c.seed ^ (lane << 26));
+    dsoa_obj out = 0;
+    uint32_t served = 0;
+    for (uint32_t round = 0; served < want; ++round) {
+        unsigned long long got = 0ull;
+        uint64_t bid = 0;
+        if (lane == leader) got = dsoa_leader_reserve(c, t, want - served, h0 + round * 0x632BE5ABu, &bid);
+        got = __shfl_sync(peers, got, (int)leader);
+        bid = __shfl_sync(peers, bid, (int)leader);
+        const uint32_t k = (uint32_t)__popcll(got);
+        if (k == 0) break;
+        if (rank >= served && rank < served + k)
+            out = dsoa_make_handle(t, bid, dsoa_nth_set(got, rank - served));
+        served += k;
+    }
+    return out;
+}
+
+/* destroy(d_allocator, ptr) (Sec. 2.1; Alg. 2): frees of the same block in a
+ * warp are combined into one atomicOr by the group's lowest lane. */
+__device__ inline void dsoa_delete(const dsoa_ctx& c, dsoa_obj h) {
+    const uint32_t active = __activemask();
+    const bool ok = h != 0 && dsoa_h_type(h) < c.ntypes && dsoa_h_block(h) < c.M;
+    if (h != 0 && !ok) dsoa_raise(c, DSOA_DEV_BAD_HANDLE);
+    const unsigned long long key = ok ? (h >> 6) : ~0ull;
+    const uint32_t lane = dsoa_lane();
+    const uint32_t peers = (c.flags & DSOA_FLAG_NO_COALESCE) ? (1u << lane) : __match_any_sync(active, key);
+    const unsigned long long bit = ok ? (1ull << dsoa_h_slot(h)) : 0ull;
+    const uint32_t lo = __reduce_or_sync(peers, (uint32_t)bit);
+    const uint32_t hi = __reduce_or_sync(peers, (uint32_t)(bit >> 32));
+    if (ok && lane == (uint32_t)__ffs((int)peers) - 1u)
+        dsoa_block_release(c, dsoa_h_type(h), dsoa_h_block(h), ((unsigned long long)hi << 32) | lo);
+}
+
+/* ---- field access (Sec. 3.3 / App. B, without pointer tagging) ---- */
+__device__ __forceinline__ char* dsoa_block_data(const dsoa_ctx& c, uint64_t bid) {
+    return c.data + bid * (uint64_t)c.block_bytes;
+}
+template <typename F>
+__device__ __forceinline__ F* dsoa_column(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t field) {
+    return reinterpret_cast<F*>(dsoa_block_data(c, bid) + c.col_off[t][field]);
+}
+template <typename F>
+__device__ __forceinline__ F& dsoa_field(const dsoa_ctx& c, dsoa_obj h, uint32_t field) {
+    return dsoa_column<F>(c, dsoa_h_type(h), dsoa_h_block(h), field)[dsoa_h_slot(h)];
+}
+
+/* ------------------------------------------------------------------------
+ * Parallel do-all kernel (Sec. 3.7, Fig. 6-7): 64 consecutive threads per
+ * block of R; thread tid serves slot tid % 64 of blocks R[(tid + k n) / 64].
+ * Persistent: the grid is sized to the GPU and reads r from device memory,
+ * so the launch is independent of r (graph-capturable).  M must provide
+ *   static __device__ void run(const dsoa_ctx&, uint32_t type, uint64_t bid,
+ *                              uint32_t slot, const Args&);
+ * ------------------------------------------------------------------------ */
+template <class M>
+__global__ void dsoa_doall_kernel(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+                                  const unsigned long long* __restrict__ occ,
+                                  const uint32_t* __restrict__ r_dev, typename M::Args args) {
+    const uint64_t n = (uint64_t)gridDim.x * blockDim.x;      /* multiple of 64 */
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t s = (uint32_t)(tid & 63u);
+    const uint64_t total = (uint64_t)(*r_dev) * 64u;
+    for (uint64_t g = tid; g < total; g += n) {
+        const uint64_t i = g >> 6;
+        const unsigned long long o = __ldg(&occ[i]);
+        if ((o >> s) & 1ull) M::run(c, t, (uint64_t)__ldg(&R[i]), s, args);
+    }
+}
+
+#endif /* __CUDACC__ */
+#endif /* DSOA_DEVICE_CUH */

@@ -75,7 +75,7 @@ def _load():
             lib.orc_gol_run.restype = i32
             lib.orc_wator_run.argtypes = [u32, u32, P, u64, u32, u32, u64, P, P]
             lib.orc_wator_run.restype = i32
-            lib.orc_traffic_run.argtypes = [u32, P, P, u64, u32, u32, u32, P, P, u64,
+            lib.orc_traffic_run.argtypes = [u32, u32, P, P, u64, u32, u32, u32, P, P, u64,
                                             P, P, P]
             lib.orc_traffic_run.restype = i32
             _lib = lib
@@ -153,8 +153,10 @@ RAMP_THR = 214748364     # floor(0.05 * 2^32)
 
 
 def traffic_run(L, thr, steps: int, seed: int = 0, slow_thr: int = SLOW_THR,
-                ramp_thr: int = RAMP_THR, init_occ=None, init_v=None, order_seed: int = 0):
-    """Batched Nagel-Schreckenberg rings.  Returns (occ[sum L], v[sum L], cars[(steps+1), n])."""
+                ramp_thr: int = RAMP_THR, init_occ=None, init_v=None, order_seed: int = 0,
+                first_ring: int = 0):
+    """Batched Nagel-Schreckenberg rings.  Returns (occ[sum L], v[sum L], cars[(steps+1), n]).
+    ``first_ring`` is the batch index of ring 0 (to replay one ring of a batch alone)."""
     Ls = np.ascontiguousarray(np.asarray(L, dtype=np.uint32))
     ths = np.ascontiguousarray(np.asarray(thr, dtype=np.uint32))
     n = Ls.size
@@ -164,7 +166,7 @@ def traffic_run(L, thr, steps: int, seed: int = 0, slow_thr: int = SLOW_THR,
     occ = np.zeros(total, dtype=np.uint8)
     v = np.zeros(total, dtype=np.uint8)
     cars = np.zeros((steps + 1, n), dtype=np.uint32)
-    rc = _load().orc_traffic_run(n, _ptr(Ls), _ptr(ths), seed, steps, slow_thr, ramp_thr,
+    rc = _load().orc_traffic_run(n, first_ring, _ptr(Ls), _ptr(ths), seed, steps, slow_thr, ramp_thr,
                                  _ptr(io), _ptr(iv), order_seed, _ptr(occ), _ptr(v), _ptr(cars))
     if rc != 0:
         raise RuntimeError("oracle traffic failed")

@@ -519,7 +519,7 @@ int orc_wator_run(uint32_t w, uint32_t h, const uint8_t* init, uint64_t seed,
 #define NS_VMAX 5u
 typedef struct { uint32_t inst, pos, v; } ns_car;
 
-int orc_traffic_run(uint32_t n_inst, const uint32_t* L, const uint32_t* thr,
+int orc_traffic_run(uint32_t n_inst, uint32_t first_ring, const uint32_t* L, const uint32_t* thr,
                     uint64_t seed, uint32_t steps, uint32_t slow_thr,
                     uint32_t ramp_thr, const uint8_t* init_occ,
                     const uint8_t* init_v, uint64_t order_seed,
@@ -543,7 +543,7 @@ int orc_traffic_run(uint32_t n_inst, const uint32_t* L, const uint32_t* thr,
     for (uint32_t i = 0; i < n_inst && rc == 0; ++i) {
         for (uint32_t j = 0; j < L[i]; ++j) {
             int present = init_occ ? (init_occ[off[i] + j] != 0)
-                                   : (philox_w0(seed, 0xFFFFFFFFu, j, i, 0) < thr[i]);
+                                   : (philox_w0(seed, 0xFFFFFFFFu, j, first_ring + i, 0) < thr[i]);
             if (!present) continue;
             uint32_t k = store_new(&st);
             if (k == UINT32_MAX) { rc = -1; break; }
@@ -567,10 +567,10 @@ int orc_traffic_run(uint32_t n_inst, const uint32_t* L, const uint32_t* thr,
             uint32_t gap = 0;
             while (gap < v && !cur[off[i] + (car->pos + gap + 1) % len]) gap++;
             if (gap < v) v = gap;
-            if (v > 0 && philox_w0(seed, t, car->pos, i, 1) < slow_thr) v -= 1;
+            if (v > 0 && philox_w0(seed, t, car->pos, first_ring + i, 1) < slow_thr) v -= 1;
             uint32_t np = (car->pos + v) % len;
             uint32_t ramp_off = len / 2;
-            if (np == ramp_off && philox_w0(seed, t, ramp_off, i, 2) < ramp_thr) {
+            if (np == ramp_off && philox_w0(seed, t, ramp_off, first_ring + i, 2) < ramp_thr) {
                 store_delete(&st, snap[j]);
                 cars[i]--;
                 continue;
@@ -582,7 +582,7 @@ int orc_traffic_run(uint32_t n_inst, const uint32_t* L, const uint32_t* thr,
         free(snap);
         /* on-ramp: one possible arrival per ring at cell 0 */
         for (uint32_t i = 0; i < n_inst; ++i) {
-            if (nxt[off[i]] == 0 && philox_w0(seed, t, 0, i, 3) < ramp_thr) {
+            if (nxt[off[i]] == 0 && philox_w0(seed, t, 0, first_ring + i, 3) < ramp_thr) {
                 uint32_t k = store_new(&st);
                 if (k == UINT32_MAX) { rc = -1; break; }
                 ns_car* car = (ns_car*)store_get(&st, k);

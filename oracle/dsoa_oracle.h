@@ -88,8 +88,10 @@ int orc_wator_run(uint32_t w, uint32_t h, const uint8_t* init, uint64_t seed,
  * are drawn from `seed`.  slow_thr / ramp_thr: u32 thresholds of the random
  * slow-down and of the ramp events (0.2 and 0.05 in the configured workload).
  * out_occ / out_v: sum(L) bytes (final occupancy and speed per cell).
- * cars_per_step: nullable (steps+1)*n_inst counts.  Returns 0 or -1. */
-int orc_traffic_run(uint32_t n_inst, const uint32_t* L, const uint32_t* thr,
+ * cars_per_step: nullable (steps+1)*n_inst counts.  first_ring is the batch
+ * index of ring 0 in the Philox counters, so that one ring of a batch can be
+ * replayed alone.  Returns 0 or -1. */
+int orc_traffic_run(uint32_t n_inst, uint32_t first_ring, const uint32_t* L, const uint32_t* thr,
                     uint64_t seed, uint32_t steps, uint32_t slow_thr,
                     uint32_t ramp_thr, const uint8_t* init_occ,
                     const uint8_t* init_v, uint64_t order_seed,

@@ -1,0 +1,675 @@
+// heap.cu -- heap lifecycle, layout, enumeration (bitmap scan + compaction),
+// counting, invariant checking and CUDA-graph capture of the SMMO runtime.
+//
+// Paper map: heap of M equal blocks (Sec. 3), block bitmaps (Sec. 3.4),
+// hierarchical bitmaps (Sec. 4.1), indices()/compaction into R (Sec. 3.7,
+// Sec. 4.1.5, Fig. 7), fragmentation accounting (Sec. 6.4).
+#include <algorithm>
+#include <cstdio>
+#include <new>
+
+#include "dsoa_internal.cuh"
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+constexpr int kSmallWords = 64;  // small device scalars: err, r, done, ...
+
+uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    uint64_t M = 0, tiles = 0, bm_stride = 0;
+    uint32_t nlevels = 0;
+    uint64_t lvl_off[DSOA_MAX_LEVELS] = {0}, lvl_words[DSOA_MAX_LEVELS] = {0};
+    uint64_t off_data = 0, off_slot = 0, off_btype = 0, off_bm = 0, off_R = 0, off_Rocc = 0,
+             off_tcnt = 0, off_toff = 0, off_small = 0, total = 0;
+};
+
+bool make_layout(uint64_t M, uint32_t block_bytes, int nbm, Layout* L) {
+    if (M == 0) return false;
+    L->M = M;
+    uint64_t words = (M + 63) / 64;
+    uint32_t nl = 0;
+    uint64_t off = 0;
+    for (;;) {
+        if (nl >= DSOA_MAX_LEVELS) return false;
+        L->lvl_off[nl] = off;
+        L->lvl_words[nl] = words;
+        off += words;
+        ++nl;
+        if (words == 1) break;
+        words = (words + 63) / 64;
+    }
+    L->nlevels = nl;
+    L->bm_stride = align_up(off, kAlign / 8);
+    L->tiles = nl >= 2 ? L->lvl_words[1] : 1;
+    uint64_t p = 0;
+    L->off_data = p;  p = align_up(p + M * block_bytes, kAlign);
+    L->off_slot = p;  p = align_up(p + M * 8, kAlign);
+    L->off_btype = p; p = align_up(p + M * 4, kAlign);
+    L->off_bm = p;    p = align_up(p + (uint64_t)nbm * L->bm_stride * 8, kAlign);
+    L->off_R = p;     p = align_up(p + M * 4, kAlign);
+    L->off_Rocc = p;  p = align_up(p + M * 8, kAlign);
+    L->off_tcnt = p;  p = align_up(p + L->tiles * 4, kAlign);
+    L->off_toff = p;  p = align_up(p + L->tiles * 4, kAlign);
+    L->off_small = p; p = align_up(p + kSmallWords * 8, kAlign);
+    L->total = p;
+    return true;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Consistent "every block free" state of the free-block bitmap: bit i of level
+// l is set iff i < (number of bits at level l).
+__global__ void k_init_free(dsoa_ctx c) {
+    uint64_t total = 0;
+    for (uint32_t l = 0; l < c.nlevels; ++l) total += c.lvl_words[l];
+    unsigned long long* bm = c.bm;  // bitmap 0 = free
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t i = g;
+        uint32_t l = 0;
+        while (i >= c.lvl_words[l]) { i -= c.lvl_words[l]; ++l; }
+        const uint64_t nbits = l == 0 ? c.M : c.lvl_words[l - 1];
+        const uint64_t lo = i * 64, hi = std::min<uint64_t>(lo + 64, nbits);
+        const uint64_t k = hi - lo;
+        bm[c.lvl_off[l] + i] = k >= 64 ? DSOA_ALL : ((1ull << k) - 1ull);
+    }
+}
+
+// Enumeration, kernel 1 (Alg. 5 "indices", counting half): one warp per
+// level-1 container ("tile" of 64 level-0 containers = 4096 blocks).  Only
+// level-0 containers whose level-1 bit is set are read (hierarchical skip,
+// Sec. 4.1.5).  The last CTA to finish turns the tile counts into exclusive
+// offsets (prefix sum, Fig. 7) and writes r.
+__global__ void k_tile_count(dsoa_ctx c, uint32_t b, uint64_t tiles, uint32_t* __restrict__ tcnt,
+                             uint32_t* __restrict__ toff, uint32_t* __restrict__ r_dev,
+                             uint32_t* __restrict__ done) {
+    const uint32_t lane = threadIdx.x & 31u, wpc = blockDim.x >> 5;
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, b, 1) : nullptr;
+    const uint64_t w0 = c.lvl_words[0];
+    for (uint64_t t = (uint64_t)blockIdx.x * wpc + (threadIdx.x >> 5); t < tiles;
+         t += (uint64_t)gridDim.x * wpc) {
+        const unsigned long long sel = L1 ? L1[t] : 1ull;
+        uint32_t cnt = 0;
+        const uint64_t a = t * 64 + lane, bb = a + 32;
+        if (((sel >> lane) & 1ull) && a < w0) cnt += __popcll(L0[a]);
+        if (((sel >> (lane + 32)) & 1ull) && bb < w0) cnt += __popcll(L0[bb]);
+        cnt = warp_sum(cnt);
+        if (lane == 0) tcnt[t] = cnt;
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // exclusive scan of tcnt[0..tiles) by this CTA
+    __shared__ uint32_t part[1024];
+    const uint64_t per = (tiles + blockDim.x - 1) / blockDim.x;
+    const uint64_t lo = threadIdx.x * per, hi = std::min<uint64_t>(lo + per, tiles);
+    uint32_t s = 0;
+    for (uint64_t i = lo; i < hi; ++i) s += __ldcg(&tcnt[i]);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (uint32_t i = 0; i < blockDim.x; ++i) { const uint32_t v = part[i]; part[i] = run; run += v; }
+        *r_dev = run;
+        *done = 0u;
+    }
+    __syncthreads();
+    uint32_t run = part[threadIdx.x];
+    for (uint64_t i = lo; i < hi; ++i) { toff[i] = run; run += __ldcg(&tcnt[i]); }
+}
+
+// Enumeration, kernel 2 (compaction + iteration-bitmap snapshot, Sec. 3.1 and
+// Fig. 7): 64 threads per tile; thread j owns level-0 container 64t+j; a
+// CTA-local prefix sum gives each set bit its rank; block ids are staged in
+// shared memory and written out coalesced together with the snapshot of the
+// block's occupied slots (the complement of its free-slot word).
+template <int TPC>
+__global__ void __launch_bounds__(64 * TPC) k_compact(dsoa_ctx c, uint32_t b, uint64_t tiles,
+                                                      const uint32_t* __restrict__ toff,
+                                                      uint32_t* __restrict__ R,
+                                                      unsigned long long* __restrict__ Rocc) {
+    __shared__ uint32_t list[TPC][4096];
+    __shared__ uint32_t wsum[TPC][2];
+    const uint32_t tl = threadIdx.x >> 6, j = threadIdx.x & 63u, lane = threadIdx.x & 31u;
+    const uint64_t t = (uint64_t)blockIdx.x * TPC + tl;
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    unsigned long long w = 0ull;
+    if (t < tiles) {
+        const unsigned long long sel = c.nlevels >= 2 ? dsoa_level(c, b, 1)[t] : 1ull;
+        const uint64_t wi = t * 64 + j;
+        if (((sel >> j) & 1ull) && wi < c.lvl_words[0]) w = L0[wi];
+    }
+    const uint32_t cnt = __popcll(w);
+    uint32_t incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+    }
+    if (lane == 31) wsum[tl][j >> 5] = incl;
+    __syncthreads();
+    const uint32_t excl = incl - cnt + ((j >= 32) ? wsum[tl][0] : 0u);
+    const uint32_t tile_total = wsum[tl][0] + wsum[tl][1];
+    const uint64_t bid0 = (t * 64 + j) * 64;
+    uint32_t k = excl;
+    for (unsigned long long x = w; x; x &= x - 1ull) list[tl][k++] = (uint32_t)(bid0 + (uint32_t)(__ffsll((long long)x) - 1));
+    __syncthreads();
+    if (t >= tiles) return;
+    const uint32_t base = toff[t];
+    for (uint32_t i = j; i < tile_total; i += 64) {
+        const uint32_t bid = list[tl][i];
+        R[base + i] = bid;
+        Rocc[base + i] = ~c.slot[bid];
+    }
+}
+
+// Live objects of one type: warp per tile; for every non-empty level-0
+// container the warp reads the 64 slot words coalesced.
+__global__ void k_count(dsoa_ctx c, uint32_t b, uint64_t tiles, unsigned long long* out) {
+    const uint32_t lane = threadIdx.x & 31u, wpc = blockDim.x >> 5;
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, b, 1) : nullptr;
+    uint32_t cnt = 0;
+    for (uint64_t t = (uint64_t)blockIdx.x * wpc + (threadIdx.x >> 5); t < tiles;
+         t += (uint64_t)gridDim.x * wpc) {
+        unsigned long long sel = L1 ? L1[t] : 1ull;
+        for (; sel; sel &= sel - 1ull) {
+            const uint64_t wi = t * 64 + (uint64_t)(__ffsll((long long)sel) - 1);
+            if (wi >= c.lvl_words[0]) break;
+            const unsigned long long w = L0[wi];
+            const uint64_t bid = wi * 64 + lane;
+            if ((w >> lane) & 1ull) cnt += __popcll(~c.slot[bid]);
+            if ((w >> (lane + 32)) & 1ull) cnt += __popcll(~c.slot[bid + 32]);
+        }
+    }
+    cnt = warp_sum(cnt);
+    if (lane == 0 && cnt) atomicAdd(out, (unsigned long long)cnt);
+}
+
+__global__ void k_popc_level0(dsoa_ctx c, uint32_t b, unsigned long long* out) {
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    uint32_t cnt = 0;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.lvl_words[0];
+         i += (uint64_t)gridDim.x * blockDim.x)
+        cnt += __popcll(L0[i]);
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31u) == 0 && cnt) atomicAdd(out, (unsigned long long)cnt);
+}
+
+__device__ __forceinline__ bool bit_at(const unsigned long long* L, uint64_t i) {
+    return (L[i >> 6] >> (i & 63u)) & 1ull;
+}
+
+// Invariant checker (Sec. 3.4 bitmap semantics, App. A.4 consistency).
+__global__ void k_check(dsoa_ctx c, unsigned long long* v) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nbm = 1u + 2u * c.ntypes;
+    unsigned long long loc[DSOA_CHECK_COUNT] = {0};
+    // per-block state
+    for (uint64_t bid = tid; bid < c.M; bid += stride) {
+        const bool f = bit_at(dsoa_level(c, dsoa_bm_free(), 0), bid);
+        uint32_t nalloc = 0, talloc = 0;
+        for (uint32_t t = 0; t < c.ntypes; ++t) {
+            const bool a = bit_at(dsoa_level(c, dsoa_bm_alloc(t), 0), bid);
+            const bool act = bit_at(dsoa_level(c, dsoa_bm_active(t), 0), bid);
+            if (a) { ++nalloc; talloc = t; }
+            if (act && !a) loc[DSOA_CHECK_ACTIVE_SUBSET]++;
+        }
+        const unsigned long long w = c.slot[bid];
+        if (nalloc > 1) loc[DSOA_CHECK_MULTI_TYPE]++;
+        if (f == (nalloc > 0)) loc[DSOA_CHECK_FREE_XOR]++;
+        if (f && w != 0ull) loc[DSOA_CHECK_FREE_WORD]++;
+        if (nalloc == 1) {
+            if (c.btype[bid] != talloc) loc[DSOA_CHECK_TYPE]++;
+            if (w == DSOA_ALL) loc[DSOA_CHECK_EMPTY_ALLOC]++;
+            const bool act = bit_at(dsoa_level(c, dsoa_bm_active(talloc), 0), bid);
+            if (act != (w != 0ull)) loc[DSOA_CHECK_ACTIVE_EXACT]++;
+        }
+    }
+    // hierarchy consistency and tail bits, every bitmap and level
+    for (uint32_t b = 0; b < nbm; ++b) {
+        for (uint32_t l = 0; l < c.nlevels; ++l) {
+            const unsigned long long* Ll = dsoa_level(c, b, l);
+            const uint64_t nbits = l == 0 ? c.M : c.lvl_words[l - 1];
+            for (uint64_t i = tid; i < c.lvl_words[l]; i += stride) {
+                const unsigned long long w = Ll[i];
+                const uint64_t lo = i * 64;
+                if (lo + 64 > nbits) {
+                    const uint64_t k = nbits - lo;
+                    if (w & ~((1ull << k) - 1ull)) loc[DSOA_CHECK_TAIL_BITS]++;
+                }
+                if (l > 0) {
+                    const unsigned long long* Lb = dsoa_level(c, b, l - 1);
+                    for (uint32_t k = 0; k < 64 && lo + k < nbits; ++k) {
+                        const bool up = (w >> k) & 1ull;
+                        if (up != (Lb[lo + k] != 0ull)) loc[DSOA_CHECK_HIER]++;
+                    }
+                }
+            }
+        }
+    }
+    for (int i = 0; i < DSOA_CHECK_COUNT; ++i)
+        if (loc[i]) atomicAdd(&v[i], loc[i]);
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
+    return st != cudaStreamCaptureStatusNone;
+}
+
+int init_heap(dsoa_heap* h, void* base, size_t bytes, bool owns, void* stream) {
+    h->base = base;
+    h->bytes = bytes;
+    h->owns = owns;
+    h->stream = (cudaStream_t)stream;
+    DSOA_CUDA_TRY(cudaGetDevice(&h->device));
+    DSOA_CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    std::memset(&h->ctx, 0, sizeof(h->ctx));
+    return DSOA_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+// helpers used by the application translation units
+// ------------------------------------------------------------------------
+int dsoa_check_launch(dsoa_heap* h) {
+    h->launches++;
+    return cudaGetLastError() == cudaSuccess ? DSOA_OK : DSOA_ERR_CUDA;
+}
+
+dsoa_ctx dsoa_launch_ctx(dsoa_heap* h) {
+    dsoa_ctx c = h->ctx;
+    c.seed = 0x9E3779B9u * (++h->launch_seq);
+    return c;
+}
+
+unsigned dsoa_doall_grid(dsoa_heap* h) {
+    return (unsigned)std::max(1, h->num_sms * h->doall_ctas_per_sm);
+}
+
+unsigned dsoa_new_grid(dsoa_heap* h, uint64_t n, int tpb) {
+    const uint64_t need = (n + tpb - 1) / tpb;
+    const uint64_t cap = (uint64_t)h->num_sms * (2048 / tpb);
+    return (unsigned)std::max<uint64_t>(1, std::min(need, cap));
+}
+
+int dsoa_ensure_frozen(dsoa_heap* h) {
+    if (!h) return DSOA_ERR_INVALID_ARG;
+    if (h->frozen) return DSOA_OK;
+    return dsoa_heap_freeze(h);
+}
+
+int dsoa_enumerate_internal(dsoa_heap* h, int type) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+    const uint32_t b = dsoa_bm_alloc((uint32_t)type);
+    const int tpb = 256;
+    const uint64_t warps = h->tiles;
+    const unsigned g1 = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 7) / 8, (uint64_t)h->num_sms * 8));
+    k_tile_count<<<g1, tpb, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_cnt, h->tile_off, h->r_dev, h->done);
+    rc = dsoa_check_launch(h);
+    if (rc) return rc;
+    switch (h->scan_tiles_per_cta) {
+        case 2:
+            k_compact<2><<<(unsigned)((h->tiles + 1) / 2), 128, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_off, h->R, h->Rocc);
+            break;
+        default:
+            k_compact<1><<<(unsigned)h->tiles, 64, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_off, h->R, h->Rocc);
+            break;
+    }
+    return dsoa_check_launch(h);
+}
+
+// ------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------
+extern "C" {
+
+int dsoa_heap_create(size_t bytes, void* stream, dsoa_heap** out) {
+    if (!out || bytes < 4096) return DSOA_ERR_INVALID_ARG;
+    *out = nullptr;
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return DSOA_ERR_CUDA; }
+    dsoa_heap* h = new (std::nothrow) dsoa_heap();
+    if (!h) { cudaFree(p); return DSOA_ERR_OOM; }
+    int rc = init_heap(h, p, bytes, true, stream);
+    if (rc) { cudaFree(p); delete h; return rc; }
+    *out = h;
+    return DSOA_OK;
+}
+
+int dsoa_heap_create_from(void* dev_ptr, size_t bytes, void* stream, dsoa_heap** out) {
+    if (!out || !dev_ptr || bytes < 4096 || ((uintptr_t)dev_ptr % kAlign) != 0) return DSOA_ERR_INVALID_ARG;
+    *out = nullptr;
+    dsoa_heap* h = new (std::nothrow) dsoa_heap();
+    if (!h) return DSOA_ERR_OOM;
+    int rc = init_heap(h, dev_ptr, bytes, false, stream);
+    if (rc) { delete h; return rc; }
+    *out = h;
+    return DSOA_OK;
+}
+
+int dsoa_register_type(dsoa_heap* h, const uint32_t* field_bytes, int nfields, int* type_out) {
+    if (!h || !field_bytes || !type_out || nfields < 1 || nfields > DSOA_MAX_FIELDS) return DSOA_ERR_INVALID_ARG;
+    if (h->frozen) return DSOA_ERR_FROZEN;
+    if (h->ntypes >= DSOA_MAX_TYPES) return DSOA_ERR_TOO_MANY_TYPES;
+    dsoa_type_info ti;
+    std::memset(&ti, 0, sizeof(ti));
+    ti.nfields = nfields;
+    uint32_t off = 0;
+    for (int i = 0; i < nfields; ++i) {
+        const uint32_t fb = field_bytes[i];
+        if (fb != 1 && fb != 2 && fb != 4 && fb != 8 && fb != 16) return DSOA_ERR_INVALID_ARG;
+        ti.field_bytes[i] = fb;
+        ti.col_off[i] = off;
+        off += (uint32_t)align_up((uint64_t)DSOA_SLOTS * fb, 128);
+    }
+    ti.data_bytes = off;
+    h->types[h->ntypes] = ti;
+    *type_out = h->ntypes++;
+    return DSOA_OK;
+}
+
+int dsoa_heap_freeze(dsoa_heap* h) {
+    if (!h) return DSOA_ERR_INVALID_ARG;
+    if (h->frozen) return DSOA_OK;
+    if (h->ntypes == 0) return DSOA_ERR_INVALID_ARG;
+    if (capturing(h->stream)) return DSOA_ERR_CAPTURE;
+    uint32_t block_bytes = 128;
+    for (int t = 0; t < h->ntypes; ++t) block_bytes = std::max(block_bytes, h->types[t].data_bytes);
+    const int nbm = 1 + 2 * h->ntypes;
+    // largest M whose layout fits in the byte budget
+    uint64_t lo = 0, hi = h->bytes / block_bytes + 1;
+    Layout L;
+    while (lo + 1 < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (make_layout(mid, block_bytes, nbm, &L) && L.total <= h->bytes) lo = mid; else hi = mid;
+    }
+    if (lo == 0 || lo > (1ull << 32) - 1 || !make_layout(lo, block_bytes, nbm, &L)) return DSOA_ERR_OOM;
+    char* base = (char*)h->base;
+    dsoa_ctx& c = h->ctx;
+    std::memset(&c, 0, sizeof(c));
+    c.data = base + L.off_data;
+    c.slot = (unsigned long long*)(base + L.off_slot);
+    c.btype = (uint32_t*)(base + L.off_btype);
+    c.bm = (unsigned long long*)(base + L.off_bm);
+    uint64_t* small = (uint64_t*)(base + L.off_small);
+    c.err = (int*)(small + 0);
+    h->r_dev = (uint32_t*)(small + 1);
+    h->done = (uint32_t*)(small + 2);
+    h->scratch64 = (unsigned long long*)(small + 16);
+    c.M = L.M;
+    c.bm_stride = L.bm_stride;
+    for (int l = 0; l < DSOA_MAX_LEVELS; ++l) { c.lvl_off[l] = L.lvl_off[l]; c.lvl_words[l] = L.lvl_words[l]; }
+    c.nlevels = L.nlevels;
+    c.block_bytes = block_bytes;
+    c.ntypes = (uint32_t)h->ntypes;
+    for (int t = 0; t < h->ntypes; ++t)
+        for (int f = 0; f < h->types[t].nfields; ++f) c.col_off[t][f] = (uint16_t)h->types[t].col_off[f];
+    h->tiles = L.tiles;
+    h->R = (uint32_t*)(base + L.off_R);
+    h->Rocc = (unsigned long long*)(base + L.off_Rocc);
+    h->tile_cnt = (uint32_t*)(base + L.off_tcnt);
+    h->tile_off = (uint32_t*)(base + L.off_toff);
+    h->meta_bytes = L.total - L.M * block_bytes;
+    DSOA_CUDA_TRY(cudaMemsetAsync(c.slot, 0, L.M * 8, h->stream));            // all slots taken
+    DSOA_CUDA_TRY(cudaMemsetAsync(c.btype, 0xFF, L.M * 4, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(c.bm, 0, (uint64_t)nbm * L.bm_stride * 8, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(small, 0, kSmallWords * 8, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(h->R, 0, L.M * 4, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(h->Rocc, 0, L.M * 8, h->stream));
+    k_init_free<<<std::max(1, h->num_sms * 4), 256, 0, h->stream>>>(c);
+    int rc = dsoa_check_launch(h);
+    if (rc) return rc;
+    h->frozen = true;
+    return DSOA_OK;
+}
+
+int dsoa_heap_info(dsoa_heap* h, uint64_t* num_blocks, uint32_t* block_bytes, uint32_t* num_levels,
+                   uint64_t* metadata_bytes) {
+    if (!h) return DSOA_ERR_INVALID_ARG;
+    if (!h->frozen) return DSOA_ERR_NOT_FROZEN;
+    if (num_blocks) *num_blocks = h->ctx.M;
+    if (block_bytes) *block_bytes = h->ctx.block_bytes;
+    if (num_levels) *num_levels = h->ctx.nlevels;
+    if (metadata_bytes) *metadata_bytes = h->meta_bytes;
+    return DSOA_OK;
+}
+
+int dsoa_field_offset(dsoa_heap* h, int type, int field, uint32_t* offset_out) {
+    if (!h || !offset_out || type < 0 || type >= h->ntypes || field < 0 || field >= h->types[type].nfields)
+        return DSOA_ERR_INVALID_ARG;
+    *offset_out = h->types[type].col_off[field];
+    return DSOA_OK;
+}
+
+int dsoa_parallel_new(dsoa_heap* h, int type, uint64_t n, int ctor_id, const void* args, size_t nb) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+    if (ctor_id >= 100 && ctor_id < 200) return dsoa_micro_new(h, type, n, ctor_id, args, nb);
+    if (ctor_id >= 200 && ctor_id < 300) return dsoa_gol_new(h, type, n, ctor_id, args, nb);
+    return DSOA_ERR_UNKNOWN_METHOD;
+}
+
+int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args, size_t nb) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+    if (method_id >= 100 && method_id < 200) return dsoa_micro_do(h, type, method_id, args, nb);
+    if (method_id >= 200 && method_id < 300) return dsoa_gol_do(h, type, method_id, args, nb);
+    if (method_id >= 300 && method_id < 400) return dsoa_wator_do(h, type, method_id, args, nb);
+    if (method_id >= 400 && method_id < 500) return dsoa_traffic_do(h, type, method_id, args, nb);
+    return DSOA_ERR_UNKNOWN_METHOD;
+}
+
+int dsoa_run_kernel(dsoa_heap* h, int kernel_id, uint64_t n, const void* args, size_t nb) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (kernel_id >= 200 && kernel_id < 300) return dsoa_gol_kernel(h, kernel_id, n, args, nb);
+    if (kernel_id >= 300 && kernel_id < 400) return dsoa_wator_kernel(h, kernel_id, n, args, nb);
+    if (kernel_id >= 400 && kernel_id < 500) return dsoa_traffic_kernel(h, kernel_id, n, args, nb);
+    return DSOA_ERR_UNKNOWN_METHOD;
+}
+
+int dsoa_enumerate(dsoa_heap* h, int type, const uint32_t** R_dev, const uint64_t** occ_dev,
+                   const uint32_t** r_dev) {
+    int rc = dsoa_enumerate_internal(h, type);
+    if (rc) return rc;
+    if (R_dev) *R_dev = h->R;
+    if (occ_dev) *occ_dev = (const uint64_t*)h->Rocc;
+    if (r_dev) *r_dev = h->r_dev;
+    return DSOA_OK;
+}
+
+int dsoa_count_async(dsoa_heap* h, int type, uint64_t* out_dev) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (type < 0 || type >= h->ntypes || !out_dev) return DSOA_ERR_INVALID_ARG;
+    DSOA_CUDA_TRY(cudaMemsetAsync(out_dev, 0, 8, h->stream));
+    const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((h->tiles + 7) / 8, (uint64_t)h->num_sms * 8));
+    k_count<<<g, 256, 0, h->stream>>>(h->ctx, dsoa_bm_alloc((uint32_t)type), h->tiles, (unsigned long long*)out_dev);
+    return dsoa_check_launch(h);
+}
+
+int dsoa_count(dsoa_heap* h, int type, uint64_t* out_host) {
+    if (!h || !out_host) return DSOA_ERR_INVALID_ARG;
+    if (capturing(h->stream)) return DSOA_ERR_CAPTURE;
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    rc = dsoa_count_async(h, type, (uint64_t*)h->scratch64);
+    if (rc) return rc;
+    DSOA_CUDA_TRY(cudaMemcpyAsync(out_host, h->scratch64, 8, cudaMemcpyDeviceToHost, h->stream));
+    DSOA_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DSOA_OK;
+}
+
+int dsoa_free_blocks_async(dsoa_heap* h, uint64_t* out_dev) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (!out_dev) return DSOA_ERR_INVALID_ARG;
+    DSOA_CUDA_TRY(cudaMemsetAsync(out_dev, 0, 8, h->stream));
+    const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((h->ctx.lvl_words[0] + 255) / 256, (uint64_t)h->num_sms * 8));
+    k_popc_level0<<<g, 256, 0, h->stream>>>(h->ctx, dsoa_bm_free(), (unsigned long long*)out_dev);
+    return dsoa_check_launch(h);
+}
+
+int dsoa_get_error(dsoa_heap* h, int* bits_out) {
+    if (!h || !bits_out) return DSOA_ERR_INVALID_ARG;
+    *bits_out = 0;
+    if (!h->frozen) return DSOA_OK;
+    if (capturing(h->stream)) return DSOA_ERR_CAPTURE;
+    DSOA_CUDA_TRY(cudaMemcpyAsync(bits_out, h->ctx.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(h->ctx.err, 0, sizeof(int), h->stream));
+    DSOA_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DSOA_OK;
+}
+
+int dsoa_check(dsoa_heap* h, uint64_t* out_host) {
+    if (!h || !out_host) return DSOA_ERR_INVALID_ARG;
+    if (capturing(h->stream)) return DSOA_ERR_CAPTURE;
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    DSOA_CUDA_TRY(cudaMemsetAsync(h->scratch64, 0, DSOA_CHECK_COUNT * 8, h->stream));
+    k_check<<<std::max(1, h->num_sms * 4), 256, 0, h->stream>>>(h->ctx, h->scratch64);
+    rc = dsoa_check_launch(h);
+    if (rc) return rc;
+    DSOA_CUDA_TRY(cudaMemcpyAsync(out_host, h->scratch64, DSOA_CHECK_COUNT * 8, cudaMemcpyDeviceToHost, h->stream));
+    DSOA_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DSOA_OK;
+}
+
+int dsoa_export_state(dsoa_heap* h, void* out_host, size_t capacity, size_t* bytes_needed,
+                      uint64_t* bitmap_words) {
+    if (!h) return DSOA_ERR_INVALID_ARG;
+    if (!h->frozen) return DSOA_ERR_NOT_FROZEN;
+    const uint64_t M = h->ctx.M, nbm = 1 + 2 * (uint64_t)h->ntypes;
+    const size_t need = M * 8 + M * 4 + nbm * h->ctx.bm_stride * 8;
+    if (bytes_needed) *bytes_needed = need;
+    if (bitmap_words) *bitmap_words = h->ctx.bm_stride;
+    if (!out_host) return DSOA_OK;
+    if (capacity < need) return DSOA_ERR_INVALID_ARG;
+    if (capturing(h->stream)) return DSOA_ERR_CAPTURE;
+    char* o = (char*)out_host;
+    DSOA_CUDA_TRY(cudaMemcpyAsync(o, h->ctx.slot, M * 8, cudaMemcpyDeviceToHost, h->stream));
+    DSOA_CUDA_TRY(cudaMemcpyAsync(o + M * 8, h->ctx.btype, M * 4, cudaMemcpyDeviceToHost, h->stream));
+    DSOA_CUDA_TRY(cudaMemcpyAsync(o + M * 12, h->ctx.bm, nbm * h->ctx.bm_stride * 8, cudaMemcpyDeviceToHost, h->stream));
+    DSOA_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DSOA_OK;
+}
+
+int dsoa_get_ctx(dsoa_heap* h, void* out, size_t nb) {
+    if (!h || !out || nb != sizeof(dsoa_ctx)) return DSOA_ERR_INVALID_ARG;
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    std::memcpy(out, &h->ctx, sizeof(dsoa_ctx));
+    return DSOA_OK;
+}
+
+int dsoa_graph_begin(dsoa_heap* h) {
+    if (!h || h->stream == nullptr) return DSOA_ERR_INVALID_ARG;  // legacy stream cannot be captured
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    DSOA_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    return DSOA_OK;
+}
+
+int dsoa_graph_end(dsoa_heap* h, dsoa_graph** out) {
+    if (!h || !out) return DSOA_ERR_INVALID_ARG;
+    *out = nullptr;
+    dsoa_graph* g = new (std::nothrow) dsoa_graph();
+    if (!g) return DSOA_ERR_OOM;
+    if (cudaStreamEndCapture(h->stream, &g->graph) != cudaSuccess) { delete g; return DSOA_ERR_CUDA; }
+    if (cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
+        cudaGraphDestroy(g->graph);
+        delete g;
+        return DSOA_ERR_CUDA;
+    }
+    *out = g;
+    return DSOA_OK;
+}
+
+int dsoa_graph_launch(dsoa_graph* g, void* stream) {
+    if (!g) return DSOA_ERR_INVALID_ARG;
+    DSOA_CUDA_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return DSOA_OK;
+}
+
+int dsoa_graph_destroy(dsoa_graph* g) {
+    if (!g) return DSOA_ERR_INVALID_ARG;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return DSOA_OK;
+}
+
+int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread, int scan_tiles) {
+    if (!h) return DSOA_ERR_INVALID_ARG;
+    if (tpb) {
+        if (tpb < 64 || tpb > 1024 || tpb % 64) return DSOA_ERR_INVALID_ARG;
+        h->doall_tpb = tpb;
+    }
+    if (ctas_per_sm) {
+        if (ctas_per_sm < 1 || ctas_per_sm > 32) return DSOA_ERR_INVALID_ARG;
+        h->doall_ctas_per_sm = ctas_per_sm;
+    }
+    if (slots_per_thread) {
+        if (slots_per_thread != 1 && slots_per_thread != 2 && slots_per_thread != 4) return DSOA_ERR_INVALID_ARG;
+        h->slots_per_thread = slots_per_thread;
+    }
+    if (scan_tiles) {
+        if (scan_tiles != 1 && scan_tiles != 2) return DSOA_ERR_INVALID_ARG;
+        h->scan_tiles_per_cta = scan_tiles;
+    }
+    return DSOA_OK;
+}
+
+int dsoa_set_flags(dsoa_heap* h, uint32_t flags) {
+    if (!h) return DSOA_ERR_INVALID_ARG;
+    h->ctx.flags = flags;
+    return DSOA_OK;
+}
+
+int dsoa_launch_count(dsoa_heap* h, uint64_t* out) {
+    if (!h || !out) return DSOA_ERR_INVALID_ARG;
+    *out = h->launches;
+    return DSOA_OK;
+}
+
+int dsoa_heap_destroy(dsoa_heap* h) {
+    if (!h) return DSOA_ERR_INVALID_ARG;
+    cudaStreamSynchronize(h->stream);
+    if (h->owns && h->base) cudaFree(h->base);
+    delete h;
+    return DSOA_OK;
+}
+
+const char* dsoa_error_string(int code) {
+    switch (code) {
+        case DSOA_OK: return "ok";
+        case DSOA_ERR_INVALID_ARG: return "invalid argument";
+        case DSOA_ERR_FROZEN: return "heap layout already frozen";
+        case DSOA_ERR_TOO_MANY_TYPES: return "too many types";
+        case DSOA_ERR_OOM: return "heap too small";
+        case DSOA_ERR_CUDA: return "CUDA runtime error";
+        case DSOA_ERR_NOT_FROZEN: return "heap layout not frozen";
+        case DSOA_ERR_UNKNOWN_METHOD: return "unknown built-in method, constructor or kernel";
+        case DSOA_ERR_CAPTURE: return "synchronous call during stream capture";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// wator.cu -- Wa-Tor predator-prey as an SMMO application (Table 1 "wa-tor";
+// Dewdney 1984).  Fish {0 inst, 1 cell, 2 age, 3 target} and Shark {0 inst,
+// 1 cell, 2 age, 3 energy, 4 target, 5 eat} agents on a torus with a per-cell
+// occupancy grid (0 empty, 1 fish, 2 shark), an agent-handle map and a claim
+// word per cell.  One step is four do-alls:
+//   Fish.choose   pick an empty N/E/S/W neighbour with Philox(seed; t, c, 1, 0),
+//                 claim it with atomicMin(source cell)
+//   Fish.move     age + 1; the lowest claimant moves; a mover of age >= 3
+//                 leaves a newborn fish and restarts its age
+//   Shark.choose  prefer fish neighbours, else empty ones, Philox(seed; t, c, 2, 0)
+//   Shark.move    age + 1; a winner eats (deletes the Fish object: cross-type
+//                 delete) and refills energy to 3, else loses 1; breeds at 10;
+//                 a shark at energy 0 deletes itself
+// Every decision depends only on cell indices and the step index, so the
+// result does not depend on thread scheduling or object placement.
+#include "dsoa_internal.cuh"
+#include "rng.cuh"
+
+namespace {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kFishBreed = 3u, kSharkBreed = 10u, kSharkEnergy = 3u;
+constexpr uint32_t kFishThr = 1288490188u;   // floor(0.30 * 2^32)
+constexpr uint32_t kSharkThr = 1503238553u;  // floor(0.35 * 2^32): fish or shark
+
+__device__ __forceinline__ void neighbours(uint32_t c, uint32_t w, uint32_t h, uint32_t nb[4]) {
+    const uint32_t x = c % w, y = c / w;
+    nb[0] = ((y + h - 1u) % h) * w + x;  // N
+    nb[1] = y * w + (x + 1u) % w;        // E
+    nb[2] = ((y + 1u) % h) * w + x;      // S
+    nb[3] = y * w + (x + w - 1u) % w;    // W
+}
+
+struct FishChoose {
+    using Args = dsoa_wator_args;
+    static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
+        const dsoa_inst I = a.inst[dsoa_column<uint32_t>(c, t, bid, 0)[s]];
+        if (I.state != DSOA_INST_RUN) return;
+        const uint32_t cell = dsoa_column<uint32_t>(c, t, bid, 1)[s];
+        uint32_t nb[4], cand[4], k = 0;
+        neighbours(cell, I.w, I.h, nb);
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+            if (I.occ[nb[d]] == 0) cand[k++] = nb[d];
+        uint32_t tg = kNone;
+        if (k) {
+            tg = cand[dsoa_philox_w0(I.seed, I.t, cell, 1u, 0u) % k];
+            atomicMin(&I.claim[tg], cell);
+        }
+        dsoa_column<uint32_t>(c, t, bid, 3)[s] = tg;
+    }
+};
+
+struct FishMove {
+    using Args = dsoa_wator_args;
+    static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
+        const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        const dsoa_inst I = a.inst[k];
+        if (I.state != DSOA_INST_RUN) return;
+        uint32_t* cellp = dsoa_column<uint32_t>(c, t, bid, 1) + s;
+        uint32_t* agep = dsoa_column<uint32_t>(c, t, bid, 2) + s;
+        const uint32_t tg = dsoa_column<uint32_t>(c, t, bid, 3)[s];
+        const uint32_t age = *agep + 1u;
+        *agep = age;
+        const uint32_t old = *cellp;
+        if (tg == kNone || I.claim[tg] != old) return;
+        I.claim[tg] = kNone;
+        I.occ[tg] = 1;
+        I.cellmap[tg] = dsoa_make_handle(t, bid, s);
+        *cellp = tg;
+        dsoa_obj nf = 0;
+        if (age >= kFishBreed) {
+            *agep = 0u;
+            nf = dsoa_new(c, t);
+            if (nf) {
+                dsoa_field<uint32_t>(c, nf, 0) = k;
+                dsoa_field<uint32_t>(c, nf, 1) = old;
+                dsoa_field<uint32_t>(c, nf, 2) = 0u;
+                dsoa_field<uint32_t>(c, nf, 3) = kNone;
+            }
+        }
+        I.occ[old] = nf ? 1 : 0;
+        I.cellmap[old] = nf;
+    }
+};
+
+struct SharkChoose {
+    using Args = dsoa_wator_args;
+    static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
+        const dsoa_inst I = a.inst[dsoa_column<uint32_t>(c, t, bid, 0)[s]];
+        if (I.state != DSOA_INST_RUN) return;
+        const uint32_t cell = dsoa_column<uint32_t>(c, t, bid, 1)[s];
+        uint32_t nb[4], cand[4], k = 0;
+        neighbours(cell, I.w, I.h, nb);
+        uint8_t o[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) o[d] = I.occ[nb[d]];
+#pragma unroll
+        for (int d = 0; d < 4; ++d)
+            if (o[d] == 1) cand[k++] = nb[d];
+        const uint32_t eat = k ? 1u : 0u;
+        if (!k) {
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+                if (o[d] == 0) cand[k++] = nb[d];
+        }
+        uint32_t tg = kNone;
+        if (k) {
+            tg = cand[dsoa_philox_w0(I.seed, I.t, cell, 2u, 0u) % k];
+            atomicMin(&I.claim[tg], cell);
+        }
+        dsoa_column<uint32_t>(c, t, bid, 4)[s] = tg;
+        dsoa_column<uint32_t>(c, t, bid, 5)[s] = eat;
+    }
+};
+
+struct SharkMove {
+    using Args = dsoa_wator_args;
+    static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
+        const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        const dsoa_inst I = a.inst[k];
+        if (I.state != DSOA_INST_RUN) return;
+        uint32_t* cellp = dsoa_column<uint32_t>(c, t, bid, 1) + s;
+        uint32_t* agep = dsoa_column<uint32_t>(c, t, bid, 2) + s;
+        uint32_t* enp = dsoa_column<uint32_t>(c, t, bid, 3) + s;
+        const uint32_t tg = dsoa_column<uint32_t>(c, t, bid, 4)[s];
+        const dsoa_obj me = dsoa_make_handle(t, bid, s);
+        const uint32_t age = *agep + 1u;
+        *agep = age;
+        uint32_t energy = *enp;
+        uint32_t cell = *cellp;
+        if (tg != kNone && I.claim[tg] == cell) {
+            const uint32_t old = cell;
+            I.claim[tg] = kNone;
+            if (dsoa_column<uint32_t>(c, t, bid, 5)[s]) {
+                dsoa_delete(c, I.cellmap[tg]);
+                energy = kSharkEnergy;
+            } else {
+                energy -= 1u;
+            }
+            I.occ[tg] = 2;
+            I.cellmap[tg] = me;
+            cell = tg;
+            *cellp = tg;
+            dsoa_obj ns = 0;
+            if (age >= kSharkBreed) {
+                *agep = 0u;
+                ns = dsoa_new(c, t);
+                if (ns) {
+                    dsoa_field<uint32_t>(c, ns, 0) = k;
+                    dsoa_field<uint32_t>(c, ns, 1) = old;
+                    dsoa_field<uint32_t>(c, ns, 2) = 0u;
+                    dsoa_field<uint32_t>(c, ns, 3) = kSharkEnergy;
+                    dsoa_field<uint32_t>(c, ns, 4) = kNone;
+                    dsoa_field<uint32_t>(c, ns, 5) = 0u;
+                }
+            }
+            I.occ[old] = ns ? 2 : 0;
+            I.cellmap[old] = ns;
+        } else {
+            energy -= 1u;
+        }
+        *enp = energy;
+        if (energy == 0u) {
+            I.occ[cell] = 0;
+            I.cellmap[cell] = 0;
+            dsoa_delete(c, me);
+        }
+    }
+};
+
+struct Kill {
+    using Args = dsoa_wator_args;
+    static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
+        const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (a.inst[k].state == DSOA_INST_KILL) dsoa_delete(c, dsoa_make_handle(t, bid, s));
+    }
+};
+
+// Agents of instance `target` from an explicit grid or from Philox draws.
+__global__ void k_init(dsoa_ctx c, dsoa_wator_args a, uint64_t n) {
+    const dsoa_inst I = a.inst[a.target];
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t cell = (uint32_t)i;
+        uint32_t kind;
+        if (a.init) {
+            kind = a.init[cell];
+        } else {
+            const uint32_t u = dsoa_philox_w0(I.seed, 0xFFFFFFFFu, cell, 0u, 0u);
+            kind = u < kFishThr ? 1u : (u < kSharkThr ? 2u : 0u);
+        }
+        dsoa_obj o = 0;
+        if (kind == 1u || kind == 2u) {
+            o = dsoa_new(c, (uint32_t)(kind == 1u ? a.fish_type : a.shark_type));
+            if (o) {
+                dsoa_field<uint32_t>(c, o, 0) = a.target;
+                dsoa_field<uint32_t>(c, o, 1) = cell;
+                dsoa_field<uint32_t>(c, o, 2) = 0u;
+                if (kind == 1u) {
+                    dsoa_field<uint32_t>(c, o, 3) = kNone;
+                } else {
+                    dsoa_field<uint32_t>(c, o, 3) = kSharkEnergy;
+                    dsoa_field<uint32_t>(c, o, 4) = kNone;
+                    dsoa_field<uint32_t>(c, o, 5) = 0u;
+                }
+            }
+        }
+        I.occ[cell] = o ? (uint8_t)kind : 0;
+        I.cellmap[cell] = o;
+        I.claim[cell] = kNone;
+    }
+}
+
+__global__ void k_advance(dsoa_inst* inst, uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && inst[i].state == DSOA_INST_RUN) inst[i].t += 1u;
+}
+
+}  // namespace
+
+int dsoa_wator_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) {
+    dsoa_wator_args args;
+    int rc = dsoa_copy_args(&args, a, nb);
+    if (rc) return rc;
+    if (!args.inst) return DSOA_ERR_INVALID_ARG;
+    const bool fish = type == args.fish_type, shark = type == args.shark_type;
+    switch (method) {
+        case DSOA_M_WATOR_FISH_CHOOSE: return fish ? dsoa_run_doall<FishChoose>(h, type, args) : DSOA_ERR_INVALID_ARG;
+        case DSOA_M_WATOR_FISH_MOVE: return fish ? dsoa_run_doall<FishMove>(h, type, args) : DSOA_ERR_INVALID_ARG;
+        case DSOA_M_WATOR_SHARK_CHOOSE: return shark ? dsoa_run_doall<SharkChoose>(h, type, args) : DSOA_ERR_INVALID_ARG;
+        case DSOA_M_WATOR_SHARK_MOVE: return shark ? dsoa_run_doall<SharkMove>(h, type, args) : DSOA_ERR_INVALID_ARG;
+        case DSOA_M_WATOR_KILL: return (fish || shark) ? dsoa_run_doall<Kill>(h, type, args) : DSOA_ERR_INVALID_ARG;
+        default: return DSOA_ERR_UNKNOWN_METHOD;
+    }
+}
+
+int dsoa_wator_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_t nb) {
+    dsoa_wator_args args;
+    int rc = dsoa_copy_args(&args, a, nb);
+    if (rc) return rc;
+    if (!args.inst) return DSOA_ERR_INVALID_ARG;
+    if (n == 0) return DSOA_OK;
+    switch (kernel) {
+        case DSOA_K_WATOR_INIT: {
+            if (args.target >= args.n_inst || args.fish_type < 0 || args.fish_type >= h->ntypes ||
+                args.shark_type < 0 || args.shark_type >= h->ntypes)
+                return DSOA_ERR_INVALID_ARG;
+            const int tpb = 256;
+            k_init<<<dsoa_new_grid(h, n, tpb), tpb, 0, h->stream>>>(dsoa_launch_ctx(h), args, n);
+            return dsoa_check_launch(h);
+        }
+        case DSOA_K_WATOR_ADVANCE:
+            if (n > args.n_inst) return DSOA_ERR_INVALID_ARG;
+            k_advance<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(args.inst, (uint32_t)n);
+            return dsoa_check_launch(h);
+        default: return DSOA_ERR_UNKNOWN_METHOD;
+    }
+}

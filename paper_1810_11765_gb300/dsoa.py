@@ -1,0 +1,306 @@
+"""Python binding of the C ABI in ``include/dsoa.h`` and ``include/dsoa_apps.h``.
+
+Argument marshalling only: every step of the allocator and the do-all runs in the
+CUDA kernels of ``_lib/libdsoa.so``.  There is no CPU fallback; loading fails with
+an error when the library has not been built (``paper_1810_11765_gb300.build``).
+PyTorch supplies device memory (tensors) and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DSOA_OK = 0
+ERRORS = {-1: "invalid argument", -2: "heap layout already frozen", -3: "too many types",
+          -4: "heap too small", -5: "CUDA runtime error", -6: "heap layout not frozen",
+          -7: "unknown built-in method", -8: "synchronous call during stream capture"}
+
+DEV_OOM, DEV_SPIN, DEV_DOUBLE_FREE, DEV_BAD_HANDLE = 1, 2, 4, 8
+FLAG_NO_COALESCE, FLAG_NO_ROTATE = 1, 2
+CHECK_NAMES = ["hier", "free_xor", "multi_type", "active_subset", "type", "free_word",
+               "empty_alloc", "active_exact", "tail_bits"]
+
+# built-in ids (dsoa_apps.h)
+C_MICRO, M_MICRO_SCALE, M_MICRO_SCALE_SCALAR, M_MICRO_DELETE = 100, 101, 102, 103
+M_MICRO_GATHER, M_MICRO_STATS, M_MICRO_SCALE_TMA = 104, 105, 106
+C_GOL_CELL, M_GOL_SPREAD, M_GOL_REAP, M_GOL_DECIDE, M_GOL_READ, M_GOL_KILL = 200, 201, 202, 203, 204, 205
+K_GOL_ADVANCE = 250
+M_WATOR_FISH_CHOOSE, M_WATOR_FISH_MOVE, M_WATOR_SHARK_CHOOSE, M_WATOR_SHARK_MOVE = 301, 302, 303, 304
+M_WATOR_KILL, K_WATOR_INIT, K_WATOR_ADVANCE = 305, 350, 351
+M_TRAFFIC_MOVE, M_TRAFFIC_READ = 401, 402
+K_TRAFFIC_INIT, K_TRAFFIC_CLEAR, K_TRAFFIC_ONRAMP, K_TRAFFIC_ADVANCE = 450, 451, 452, 453
+
+INST_IDLE, INST_RUN, INST_KILL = 0, 1, 2
+
+P = ctypes.c_void_p
+u8p = ctypes.c_void_p
+
+
+class MicroArgs(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("id_base", ctypes.c_uint32), ("round", ctypes.c_uint32),
+                ("x_out", P), ("live_out", P), ("n_ids", ctypes.c_uint64), ("stats", P)]
+
+
+class MicroStats(ctypes.Structure):
+    _fields_ = [("live", ctypes.c_uint64), ("sum_id", ctypes.c_uint64), ("sum_tag", ctypes.c_uint64),
+                ("xor_tag", ctypes.c_uint64), ("sum_x", ctypes.c_double)]
+
+
+class Inst(ctypes.Structure):
+    _fields_ = [("cellmap", P), ("occ", P), ("claim", P), ("seed", ctypes.c_uint64),
+                ("w", ctypes.c_uint32), ("h", ctypes.c_uint32), ("t", ctypes.c_uint32),
+                ("state", ctypes.c_uint32)]
+
+
+class GolArgs(ctypes.Structure):
+    _fields_ = [("inst", P), ("init", P), ("n_inst", ctypes.c_uint32), ("target", ctypes.c_uint32),
+                ("cell_type", ctypes.c_int32), ("alive_type", ctypes.c_int32)]
+
+
+class WatorArgs(ctypes.Structure):
+    _fields_ = [("inst", P), ("init", P), ("n_inst", ctypes.c_uint32), ("target", ctypes.c_uint32),
+                ("fish_type", ctypes.c_int32), ("shark_type", ctypes.c_int32)]
+
+
+class TrafficArgs(ctypes.Structure):
+    _fields_ = [("occ0", P), ("occ1", P), ("vel_out", P), ("ring_base", P), ("ring_thr", P),
+                ("init_occ", P), ("init_v", P), ("t_dev", P), ("seed", ctypes.c_uint64),
+                ("n_rings", ctypes.c_uint32), ("slow_thr", ctypes.c_uint32),
+                ("ramp_thr", ctypes.c_uint32), ("car_type", ctypes.c_int32)]
+
+
+# exported names of include/dsoa.h, in declaration order
+ABI_FUNCTIONS = [
+    "dsoa_heap_create", "dsoa_heap_create_from", "dsoa_register_type", "dsoa_heap_freeze",
+    "dsoa_heap_info", "dsoa_field_offset", "dsoa_parallel_new", "dsoa_parallel_do",
+    "dsoa_run_kernel", "dsoa_enumerate", "dsoa_count", "dsoa_count_async",
+    "dsoa_free_blocks_async", "dsoa_get_error", "dsoa_check", "dsoa_export_state",
+    "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
+    "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_launch_count",
+    "dsoa_heap_destroy", "dsoa_error_string",
+]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libdsoa.so (no implicit build, no fallback)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise ImportError(f"{p} is missing: build it with paper_1810_11765_gb300.build.build()")
+    L = ctypes.CDLL(p)
+    vp, sz, i32, u32, u64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+    sig = {
+        "dsoa_heap_create": [sz, vp, vp], "dsoa_heap_create_from": [vp, sz, vp, vp],
+        "dsoa_register_type": [vp, vp, i32, vp], "dsoa_heap_freeze": [vp],
+        "dsoa_heap_info": [vp, vp, vp, vp, vp], "dsoa_field_offset": [vp, i32, i32, vp],
+        "dsoa_parallel_new": [vp, i32, u64, i32, vp, sz], "dsoa_parallel_do": [vp, i32, i32, vp, sz],
+        "dsoa_run_kernel": [vp, i32, u64, vp, sz], "dsoa_enumerate": [vp, i32, vp, vp, vp],
+        "dsoa_count": [vp, i32, vp], "dsoa_count_async": [vp, i32, vp],
+        "dsoa_free_blocks_async": [vp, vp], "dsoa_get_error": [vp, vp], "dsoa_check": [vp, vp],
+        "dsoa_export_state": [vp, vp, sz, vp, vp], "dsoa_get_ctx": [vp, vp, sz],
+        "dsoa_graph_begin": [vp], "dsoa_graph_end": [vp, vp], "dsoa_graph_launch": [vp, vp],
+        "dsoa_graph_destroy": [vp], "dsoa_set_launch": [vp, i32, i32, i32, i32],
+        "dsoa_set_flags": [vp, u32], "dsoa_launch_count": [vp, vp], "dsoa_heap_destroy": [vp],
+        "dsoa_error_string": [i32],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "dsoa_error_string" else i32
+    if path is None:
+        _lib = L
+    return L
+
+
+class DsoaError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({code})")
+        self.code = code
+
+
+def _ok(rc, what):
+    if rc != DSOA_OK:
+        raise DsoaError(rc, what)
+
+
+def _addr(x) -> int | None:
+    """Device / host address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(type(x))
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+class Graph:
+    def __init__(self, handle):
+        self._h = handle
+
+    def launch(self, stream=None):
+        _ok(load().dsoa_graph_launch(self._h, _stream_ptr(stream)), "dsoa_graph_launch")
+
+    def close(self):
+        if self._h:
+            load().dsoa_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Heap:
+    """A device heap of 64-slot SOA blocks (dsoa_heap)."""
+
+    def __init__(self, nbytes: int | None = None, stream=None, buffer=None):
+        L = load()
+        self._h = ctypes.c_void_p()
+        self.stream = stream
+        sp = _stream_ptr(stream)
+        self._buffer = buffer
+        if buffer is not None:
+            _ok(L.dsoa_heap_create_from(_addr(buffer), buffer.numel() * buffer.element_size(), sp,
+                                        ctypes.byref(self._h)), "dsoa_heap_create_from")
+        else:
+            _ok(L.dsoa_heap_create(int(nbytes), sp, ctypes.byref(self._h)), "dsoa_heap_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def register_type(self, field_bytes) -> int:
+        fb = (ctypes.c_uint32 * len(field_bytes))(*field_bytes)
+        t = ctypes.c_int()
+        _ok(load().dsoa_register_type(self._h, fb, len(field_bytes), ctypes.byref(t)), "dsoa_register_type")
+        return t.value
+
+    def freeze(self):
+        _ok(load().dsoa_heap_freeze(self._h), "dsoa_heap_freeze")
+
+    def info(self) -> dict:
+        M, bb, nl, meta = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+        _ok(load().dsoa_heap_info(self._h, ctypes.byref(M), ctypes.byref(bb), ctypes.byref(nl),
+                                  ctypes.byref(meta)), "dsoa_heap_info")
+        return {"num_blocks": M.value, "block_bytes": bb.value, "num_levels": nl.value,
+                "metadata_bytes": meta.value}
+
+    def field_offset(self, t: int, f: int) -> int:
+        o = ctypes.c_uint32()
+        _ok(load().dsoa_field_offset(self._h, t, f, ctypes.byref(o)), "dsoa_field_offset")
+        return o.value
+
+    def parallel_new(self, t: int, n: int, ctor: int, args):
+        _ok(load().dsoa_parallel_new(self._h, t, n, ctor, ctypes.byref(args), ctypes.sizeof(args)),
+            "dsoa_parallel_new")
+
+    def parallel_do(self, t: int, method: int, args):
+        _ok(load().dsoa_parallel_do(self._h, t, method, ctypes.byref(args), ctypes.sizeof(args)),
+            "dsoa_parallel_do")
+
+    def run_kernel(self, kernel: int, n: int, args):
+        _ok(load().dsoa_run_kernel(self._h, kernel, n, ctypes.byref(args), ctypes.sizeof(args)),
+            "dsoa_run_kernel")
+
+    def enumerate(self, t: int):
+        R, occ, r = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _ok(load().dsoa_enumerate(self._h, t, ctypes.byref(R), ctypes.byref(occ), ctypes.byref(r)),
+            "dsoa_enumerate")
+        return R.value, occ.value, r.value
+
+    def count(self, t: int) -> int:
+        out = ctypes.c_uint64()
+        _ok(load().dsoa_count(self._h, t, ctypes.byref(out)), "dsoa_count")
+        return out.value
+
+    def count_async(self, t: int, out_dev):
+        _ok(load().dsoa_count_async(self._h, t, _addr(out_dev)), "dsoa_count_async")
+
+    def free_blocks_async(self, out_dev):
+        _ok(load().dsoa_free_blocks_async(self._h, _addr(out_dev)), "dsoa_free_blocks_async")
+
+    def get_error(self) -> int:
+        e = ctypes.c_int()
+        _ok(load().dsoa_get_error(self._h, ctypes.byref(e)), "dsoa_get_error")
+        return e.value
+
+    def check(self) -> dict:
+        out = (ctypes.c_uint64 * len(CHECK_NAMES))()
+        _ok(load().dsoa_check(self._h, out), "dsoa_check")
+        return {n: int(out[i]) for i, n in enumerate(CHECK_NAMES)}
+
+    def export_state(self) -> dict:
+        need, words = ctypes.c_size_t(), ctypes.c_uint64()
+        L = load()
+        _ok(L.dsoa_export_state(self._h, None, 0, ctypes.byref(need), ctypes.byref(words)), "dsoa_export_state")
+        buf = np.empty(need.value, dtype=np.uint8)
+        _ok(L.dsoa_export_state(self._h, buf.ctypes.data, need.value, ctypes.byref(need), ctypes.byref(words)),
+            "dsoa_export_state")
+        M = self.info()["num_blocks"]
+        slot = buf[:M * 8].view(np.uint64)
+        btype = buf[M * 8:M * 12].view(np.uint32)
+        bm = buf[M * 12:].view(np.uint64).reshape(-1, words.value)
+        return {"slot": slot, "btype": btype, "bitmaps": bm}
+
+    def set_launch(self, tpb=0, ctas_per_sm=0, slots_per_thread=0, scan_tiles=0):
+        _ok(load().dsoa_set_launch(self._h, tpb, ctas_per_sm, slots_per_thread, scan_tiles), "dsoa_set_launch")
+
+    def set_flags(self, flags: int):
+        _ok(load().dsoa_set_flags(self._h, flags), "dsoa_set_flags")
+
+    @property
+    def launches(self) -> int:
+        out = ctypes.c_uint64()
+        _ok(load().dsoa_launch_count(self._h, ctypes.byref(out)), "dsoa_launch_count")
+        return out.value
+
+    def graph_begin(self):
+        _ok(load().dsoa_graph_begin(self._h), "dsoa_graph_begin")
+
+    def graph_end(self) -> Graph:
+        g = ctypes.c_void_p()
+        _ok(load().dsoa_graph_end(self._h, ctypes.byref(g)), "dsoa_graph_end")
+        return Graph(g)
+
+    def close(self):
+        if self._h:
+            load().dsoa_heap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,192 @@
+"""GPU parity of the allocator + do-all microbench against the oracle.
+
+Bar: live counts, integer sums and per-object x bit-exact; the fp64 sum of x within
+1e-6 relative (the configured tolerance for the fp32 field); allocator invariants
+clean at quiescence, checked by the library's device checker and by the independent
+host checker of gpu_common.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import gpu_ready, host_check
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x5EED0001
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ready():
+    gpu_ready()
+
+
+def make(heap_bytes=64 << 20, n=1 << 18, **launch):
+    from paper_1810_11765_gb300.apps import Micro
+    m = Micro(heap_bytes, SEED, n)
+    if launch:
+        m.heap.set_launch(**launch)
+    return m
+
+
+def assert_clean(m):
+    assert m.heap.get_error() == 0
+    dev = m.heap.check()
+    assert all(v == 0 for v in dev.values()), dev
+    host = host_check(m.heap, 1)
+    assert all(v == 0 for v in host["violations"].values()), host
+    return host
+
+
+def compare_round(g, o):
+    assert g["live"] == o["live"]
+    assert g["sum_id"] == o["sum_id"] % 2**64
+    assert g["sum_tag"] == o["sum_tag"]
+    assert g["xor_tag"] == o["xor_tag"]
+    assert abs(g["sum_x"] - o["sum_x"]) <= 1e-6 * max(abs(o["sum_x"]), 1.0)
+
+
+def test_full_config_parity():
+    """2^18 new per round, 10 rounds, 64 MiB heap: the configured microbench."""
+    n, rounds = 1 << 18, 10
+    ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
+    m = make()
+    for r in range(rounds):
+        m.new(r)
+        if r == 0:
+            # no slot handed out twice: n distinct ids land in n distinct slots
+            assert m.heap.count(m.type) == n
+            _, live0 = m.gather(n)
+            assert live0.sum() == n
+        m.scale()
+        m.delete(r)
+        compare_round(m.stats(), ref[r])
+        host = assert_clean(m)
+        assert host["live"][0] == ref[r]["live"]
+        assert m.heap.count(m.type) == ref[r]["live"]
+    x, live = m.gather(n * rounds)
+    assert np.array_equal(live, live_ref)
+    sel = live_ref.astype(bool)
+    assert np.array_equal(x[sel].view(np.uint32), x_ref[sel].view(np.uint32))
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 1000, 4097, 70001])
+def test_ragged_sizes(n):
+    rounds = 3
+    ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
+    m = make(heap_bytes=32 << 20, n=n)
+    for r in range(rounds):
+        m.round(r)
+        compare_round(m.stats(), ref[r])
+        assert_clean(m)
+    x, live = m.gather(n * rounds)
+    assert np.array_equal(live, live_ref)
+    assert np.array_equal(x[live_ref.astype(bool)], x_ref[live_ref.astype(bool)])
+
+
+@pytest.mark.parametrize("method", ["scalar", "spt1", "spt2", "spt4"])
+def test_scale_variants_agree(method):
+    from paper_1810_11765_gb300 import dsoa as D
+    n, rounds = 50000, 4
+    ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
+    spt = {"scalar": 4, "spt1": 1, "spt2": 2, "spt4": 4}[method]
+    m = make(heap_bytes=16 << 20, n=n, slots_per_thread=spt)
+    meth = D.M_MICRO_SCALE_SCALAR if method == "scalar" else D.M_MICRO_SCALE
+    for r in range(rounds):
+        m.round(r, method=meth)
+    x, live = m.gather(n * rounds)
+    assert np.array_equal(live, live_ref)
+    assert np.array_equal(x[live_ref.astype(bool)], x_ref[live_ref.astype(bool)])
+    assert_clean(m)
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_ablations_keep_semantics(flags):
+    """NoCoal / NoShift / both (Sec. 6.4) change placement, not results."""
+    n, rounds = 20000, 3
+    ref, _, _ = oracle.micro_run(SEED, n, rounds)
+    m = make(heap_bytes=16 << 20, n=n)
+    m.heap.set_flags(flags)
+    for r in range(rounds):
+        m.round(r)
+        compare_round(m.stats(), ref[r])
+        assert_clean(m)
+
+
+@pytest.mark.parametrize("tpb,ctas,scan", [(64, 1, 1), (128, 4, 2), (512, 2, 1), (1024, 2, 2)])
+def test_launch_shapes_keep_semantics(tpb, ctas, scan):
+    n, rounds = 30000, 3
+    ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
+    m = make(heap_bytes=16 << 20, n=n, tpb=tpb, ctas_per_sm=ctas, scan_tiles=scan)
+    for r in range(rounds):
+        m.round(r)
+        compare_round(m.stats(), ref[r])
+    x, live = m.gather(n * rounds)
+    assert np.array_equal(live, live_ref)
+    assert np.array_equal(x[live_ref.astype(bool)], x_ref[live_ref.astype(bool)])
+
+
+def test_empty_heap_operations():
+    m = make(heap_bytes=4 << 20, n=0)
+    assert m.heap.count(m.type) == 0
+    m.scale()
+    m.delete(0)
+    s = m.stats()
+    assert s["live"] == 0 and s["sum_x"] == 0.0
+    assert_clean(m)
+
+
+def test_out_of_memory_is_reported_not_hung():
+    """A heap with room for a few blocks: allocation beyond it returns null handles
+    and sets DSOA_DEV_OOM; the kernel completes and the heap stays consistent."""
+    from paper_1810_11765_gb300 import dsoa as D
+    m = make(heap_bytes=64 << 10, n=10000)
+    M = m.heap.info()["num_blocks"]
+    m.new(0)
+    err = m.heap.get_error()
+    assert err & D.DEV_OOM
+    assert not err & (D.DEV_SPIN | D.DEV_DOUBLE_FREE | D.DEV_BAD_HANDLE)
+    live = m.heap.count(m.type)
+    assert 0 < live <= 64 * M
+    assert live >= 0.75 * 64 * M       # most of the heap is used before OOM
+    host = host_check(m.heap, 1)
+    assert host["live"][0] == live
+    assert all(v == 0 for v in host["violations"].values()), host
+
+
+def test_heap_from_torch_buffer():
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import Micro
+    buf = torch.empty(8 << 20, dtype=torch.uint8, device="cuda")
+    heap = D.Heap(buffer=buf)
+    m = Micro(0, SEED, 5000, heap=heap)
+    ref, _, _ = oracle.micro_run(SEED, 5000, 2)
+    for r in range(2):
+        m.round(r)
+        compare_round(m.stats(), ref[r])
+    heap.close()
+
+
+def test_graph_capture_replays_rounds():
+    """A captured round (new / scale / delete) replays with its argument values
+    baked in; replaying the round graph of round r reproduces round r."""
+    import torch
+    from paper_1810_11765_gb300.apps import Micro
+    n, rounds = 40000, 5
+    ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        m = Micro(16 << 20, SEED, n, stream=s)
+        graphs = []
+        for r in range(rounds):
+            m.heap.graph_begin()
+            m.round(r)
+            graphs.append(m.heap.graph_end())
+        for r in range(rounds):
+            graphs[r].launch(s)
+        s.synchronize()
+        compare_round(m.stats(), ref[-1])
+        x, live = m.gather(n * rounds)
+    assert np.array_equal(live, live_ref)
+    assert np.array_equal(x[live_ref.astype(bool)], x_ref[live_ref.astype(bool)])

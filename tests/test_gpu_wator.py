@@ -1,0 +1,80 @@
+"""GPU parity of Wa-Tor (Fish / Shark agents, claims by lowest source index).
+
+Bar: bit-exact grids and populations per step against the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import gpu_ready, host_check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ready():
+    gpu_ready()
+
+
+def world(heap_bytes=64 << 20, capacity=1):
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import WatorWorld
+    heap = D.Heap(heap_bytes)
+    w = WatorWorld(heap, capacity)
+    heap.freeze()
+    return heap, w
+
+
+def test_hand_cases():
+    heap, w = world(4 << 20, capacity=3)
+    a = w.add(3, 1, 5, init=np.array([[2, 1, 0]], np.uint8))
+    b = w.add(3, 1, 5, init=np.array([[1, 0, 1]], np.uint8))
+    w.step()
+    assert w.read(a).tolist() == [[0, 0, 2]]
+    assert w.read(b).tolist() == [[0, 1, 1]]
+    assert heap.get_error() == 0
+
+
+@pytest.mark.parametrize("W,H,steps,seed", [(4, 4, 30, 1), (5, 5, 40, 2), (64, 48, 60, 3), (200, 100, 80, 4)])
+def test_random_grids_per_step(W, H, steps, seed):
+    heap, w = world(32 << 20)
+    s = w.add(W, H, seed)
+    g0, _ = oracle.wator_run(W, H, 0, seed=seed)
+    assert np.array_equal(w.read(s), g0)
+    _, st = oracle.wator_run(W, H, steps, seed=seed)
+    for k in range(steps):
+        w.step()
+        assert w.counts() == (st[k]["fish"], st[k]["sharks"]), k
+    ref, _ = oracle.wator_run(W, H, steps, seed=seed)
+    assert np.array_equal(w.read(s), ref)
+    assert heap.get_error() == 0
+    host = host_check(heap, 2)
+    assert all(v == 0 for v in host["violations"].values()), host
+
+
+def test_full_config_1024_500():
+    """1024 x 1024 torus, 30 % fish / 5 % sharks, 500 steps (the configured workload)."""
+    from paper_1810_11765_gb300 import inputs
+    cfg = inputs.WatorConfig()
+    ref, st = oracle.wator_run(cfg.width, cfg.height, cfg.steps, seed=cfg.seed)
+    heap, w = world(256 << 20)
+    s = w.add(cfg.width, cfg.height, cfg.seed)
+    for k in range(cfg.steps):
+        w.step()
+        if k % 50 == 49 or k < 5:
+            assert w.counts() == (st[k]["fish"], st[k]["sharks"]), k
+    assert np.array_equal(w.read(s), ref)
+    assert heap.get_error() == 0
+    assert all(v == 0 for v in heap.check().values())
+
+
+def test_batched_instances_match_alone():
+    heap, w = world(64 << 20, capacity=3)
+    specs = [(50, 40, 31), (128, 64, 32), (17, 90, 33)]
+    slots = [w.add(a, b, sd) for a, b, sd in specs]
+    for _ in range(40):
+        w.step()
+    for slot, (a, b, sd) in zip(slots, specs):
+        ref, _ = oracle.wator_run(a, b, 40, seed=sd)
+        assert np.array_equal(w.read(slot), ref)
+    assert heap.get_error() == 0

@@ -117,3 +117,16 @@ def test_order_independence():
     b = oracle.traffic_run(L, thr, 40, seed=3, order_seed=17)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def test_rings_are_independent_of_the_batch():
+    # replaying ring k of a batch alone (first_ring = k) reproduces its state
+    L = [300, 513, 1000]
+    thr = [int(0.1 * 2**32), int(0.2 * 2**32), int(0.3 * 2**32)]
+    o, v, cars = oracle.traffic_run(L, thr, 60, seed=8)
+    base = np.concatenate([[0], np.cumsum(L)])
+    for k in range(3):
+        ok, vk, ck = oracle.traffic_run([L[k]], [thr[k]], 60, seed=8, first_ring=k)
+        assert np.array_equal(ok, o[base[k]:base[k + 1]])
+        assert np.array_equal(vk, v[base[k]:base[k + 1]])
+        assert np.array_equal(ck[:, 0], cars[:, k])
