@@ -1,0 +1,488 @@
+"""Benchmark of the GB300 SMMO runtime (allocator + do-all).
+
+Headline: Wa-Tor 1024x1024 torus (30 % fish / 5 % sharks), app steps/s with each
+step captured as a CUDA graph around the persistent do-all kernels, next to the same
+steps launched plainly.  One step = 4 do-alls (each: hierarchical bitmap scan +
+prefix-sum compaction + do-all kernel) with allocations (births) and frees (eaten
+fish, starved sharks), i.e. every step of the hot path.  L2 is flushed (a 256 MiB
+write) between timed steps, outside the timed region.
+
+Secondary figures in the same JSON line: the do-all kernel's HBM GB/s on >L2 object
+sets (2^26 objects, full and 50 % holes), alloc+free ops/s (allocation storm then
+delete-all), heap utilisation (fill a fixed heap until OOM), per-kernel roofline of
+the dominant step kernel, the end-to-end figure through host buffers, and the
+oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dsoa|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "app steps/s (graph+persistent vs plain); alloc+free ops/s; do-all HBM GB/s"
+WORKLOAD = "wa-tor 1024x1024 torus, 30% fish / 5% sharks, 500 steps"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=490)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="dsoa", choices=["dsoa", "reference"])
+    p.add_argument("--skip-secondary", action="store_true", help="headline legs only")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- dist
+class Dist:
+    def __init__(self, n):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            import torch
+            torch.cuda.set_device(self.local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- legs
+def ev():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
+
+
+def wator_world(seed, heap_bytes=512 << 20, launch=None):
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import WatorWorld
+    heap = D.Heap(heap_bytes)
+    w = WatorWorld(heap)
+    heap.freeze()
+    if launch:
+        heap.set_launch(**launch)
+    return heap, w
+
+
+def run_wator(seed, warmup, steps, mode, flush, launch=None):
+    """Returns (per-step ms list, final grid, launches per step)."""
+    import torch
+    heap, w = wator_world(seed, launch=launch)
+    slot = w.add(1024, 1024, seed)
+    g = None
+    if mode == "graph":
+        heap.graph_begin()
+        w.step()
+        g = heap.graph_end()
+    step = (lambda: g.launch()) if g else w.step
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = heap.launches
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record()
+        step()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    per_step_launches = (heap.launches - l0) / steps if mode == "plain" else None
+    torch.cuda.synchronize()
+    grid = w.read(slot)
+    fish, sharks = w.counts()
+    err = heap.get_error()
+    if g:
+        g.close()
+    heap.close()
+    return times, grid, per_step_launches, (fish, sharks), err
+
+
+WATOR_KERNELS = [  # (type attr, method, algorithmic bytes per agent)
+    ("fish_type", "M_WATOR_FISH_CHOOSE", 24),
+    ("fish_type", "M_WATOR_FISH_MOVE", 20),
+    ("shark_type", "M_WATOR_SHARK_CHOOSE", 28),
+    ("shark_type", "M_WATOR_SHARK_MOVE", 32),
+]
+
+
+def wator_kernel_profile(seed, warmup, steps, flush):
+    """Per-kernel CUDA-event durations of one plain Wa-Tor step, kernel by kernel."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    heap, w = wator_world(seed)
+    w.add(1024, 1024, seed)
+    for _ in range(warmup):
+        w.step()
+    acc = {}
+    a = w.args()
+    for _ in range(steps):
+        fish, sharks = w.counts()
+        flush.zero_()
+        for tattr, meth, bpa in WATOR_KERNELS:
+            t = getattr(w, tattr)
+            e0, e1, e2 = ev(), ev(), ev()
+            e0.record()
+            heap.enumerate(t)
+            e1.record()
+            heap.parallel_do_enumerated(t, getattr(D, meth), a)
+            e2.record()
+            e2.synchronize()
+            n_agents = fish if tattr == "fish_type" else sharks
+            r = acc.setdefault(meth, {"ms": [], "bytes": [], "enum_ms": []})
+            r["ms"].append(e1.elapsed_time(e2))
+            r["enum_ms"].append(e0.elapsed_time(e1))
+            r["bytes"].append(n_agents * bpa + (n_agents / 64.0) * 12)
+        heap.run_kernel(D.K_WATOR_ADVANCE, 1, a)
+    torch.cuda.synchronize()
+    heap.close()
+    return acc
+
+
+def doall_sweep(log2n, holes, flush, iters=10):
+    """do-all HBM GB/s of the 128-bit vectorised SOA kernel (x = x*1.5f + id)."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import Micro
+    n = 1 << log2n
+    m = Micro(int(n * 16 * 1.3) + (64 << 20), 0x5EED0001, n)
+    m.new(0)
+    if holes:
+        m.delete(0)
+    live = m.heap.count(m.type)
+    m.heap.enumerate(m.type)
+    args = m.args()
+    times = []
+    for _ in range(iters):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record()
+        m.heap.parallel_do_enumerated(m.type, D.M_MICRO_SCALE, args)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    err = m.heap.get_error()
+    m.heap.close()
+    del m
+    torch.cuda.empty_cache()
+    ms = statistics.median(times)
+    return {"objects": live, "ms": ms, "alg_bytes": live * 12, "gbs": live * 12 / ms / 1e6, "err": err}
+
+
+def alloc_free_storm(log2n, flush, iters=3):
+    """parallel_new of 2^log2n objects into an empty heap, then delete-all."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import Micro
+    n = 1 << log2n
+    m = Micro(int(n * 16 * 2.2) + (64 << 20), 0x5EED0001, n)
+    res = []
+    for _ in range(iters):
+        flush.zero_()
+        a, b, c = ev(), ev(), ev()
+        a.record()
+        m.new(0)
+        b.record()
+        m.heap.parallel_do(m.type, D.M_MICRO_DELETE_ALL, m.args())
+        c.record()
+        c.synchronize()
+        res.append((a.elapsed_time(b), b.elapsed_time(c)))
+    left = m.heap.count(m.type)
+    err = m.heap.get_error()
+    m.heap.close()
+    torch.cuda.empty_cache()
+    new_ms = statistics.median(r[0] for r in res)
+    del_ms = statistics.median(r[1] for r in res)
+    return {"objects": n, "new_ms": new_ms, "delete_ms": del_ms,
+            "ops_per_s": 2 * n / ((new_ms + del_ms) / 1e3), "left": left, "err": err}
+
+
+def heap_utilisation(heap_bytes=1 << 30):
+    """Fill a fixed heap with 16-byte objects until allocation fails (Sec. 6.5)."""
+    import torch
+    from paper_1810_11765_gb300.apps import Micro
+    m = Micro(heap_bytes, 0x5EED0001, 1 << 20)
+    cap = m.heap.info()["num_blocks"] * 64
+    rnd = 0
+    while True:
+        m.new(rnd)
+        rnd += 1
+        if m.heap.get_error() or rnd * (1 << 20) > cap + (1 << 20):
+            break
+    live = m.heap.count(m.type)
+    m.heap.close()
+    torch.cuda.empty_cache()
+    return {"heap_bytes": heap_bytes, "objects": live, "object_bytes": 16,
+            "utilisation": live * 16 / heap_bytes}
+
+
+def e2e_wator(seed, warmup, steps, flush):
+    """Whole job through the public API with host buffers: initial grid uploaded
+    from pinned host memory, K graph steps, per-step populations read back to
+    pinned host memory, final grid read back."""
+    import numpy as np
+    import torch
+    heap, w = wator_world(seed)
+    s0 = w.add(1024, 1024, seed)
+    host_grid = torch.from_numpy(w.read(s0).copy()).pin_memory()
+    heap.close()
+    heap, w = wator_world(seed)
+    counts_dev = torch.zeros(2 * steps, dtype=torch.int64, device="cuda")
+    counts_host = torch.zeros(2 * steps, dtype=torch.int64).pin_memory()
+    out_host = torch.zeros(1024 * 1024, dtype=torch.uint8).pin_memory()
+    torch.cuda.synchronize()
+    flush.zero_()
+    a, b = ev(), ev()
+    a.record()
+    dev_grid = host_grid.to("cuda", non_blocking=True)
+    slot = w.add(1024, 1024, seed, init=dev_grid.view(-1))
+    heap.graph_begin()
+    w.step()
+    g = heap.graph_end()
+    for k in range(steps):
+        g.launch()
+        heap.count_async(w.fish_type, counts_dev[2 * k:2 * k + 1])
+        heap.count_async(w.shark_type, counts_dev[2 * k + 1:2 * k + 2])
+        counts_host[2 * k:2 * k + 2].copy_(counts_dev[2 * k:2 * k + 2], non_blocking=True)
+    out_host.copy_(w.bufs[slot][1], non_blocking=True)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    g.close()
+    heap.close()
+    h2d = 1024 * 1024
+    return {"value": steps / (ms / 1e3), "unit": "steps/s",
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 16 + 1024 * 1024 / steps,
+            "ms": ms, "final_fish": int(counts_host[-2]), "final_sharks": int(counts_host[-1])}
+
+
+def cpu_baseline(seed, sample_steps=100):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.wator_run(1024, 1024, sample_steps, seed=seed)
+    dt = time.perf_counter() - t0
+    return {"value": sample_steps / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {sample_steps} steps of the same 1024x1024 wa-tor run (seed {seed:#x}), "
+                      "single-threaded sequential oracle incl. its initialisation"}
+
+
+# ----------------------------------------------------------------------------- arms
+def reference_arm(args):
+    """The oracle as the reference arm, on the same workload and metric."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    import oracle
+    from paper_1810_11765_gb300 import inputs
+    seed = inputs.WatorConfig().seed
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.wator_run(1024, 1024, args.warmup, seed=seed)
+    t1 = time.perf_counter()
+    oracle.wator_run(1024, 1024, args.warmup + args.steps, seed=seed)
+    t2 = time.perf_counter()
+    dt = max((t2 - t1) - (t1 - t0), 1e-9)
+    v = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "seed": seed, "mode": "sequential CPU oracle"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "steps/s",
+                             "sample": f"{args.steps} steps after {args.warmup} warm-up steps of the "
+                                       "1024x1024 wa-tor run (difference of two runs)"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def dsoa_arm(args):
+    import numpy as np
+    import torch
+    from paper_1810_11765_gb300 import build, inputs
+    dist = Dist(args.gpus)
+    dev = dist.local if dist.world > 1 else 0
+    torch.cuda.set_device(dev)
+    build.build()
+    cfg = inputs.WatorConfig()
+    seed = cfg.seed + 7919 * dist.rank          # one independent replica per rank
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    hbm_peak, peak_kind = peaks()
+
+    from paper_1810_11765_gb300 import autotune
+    launch = autotune.best_wator_launch(seed)
+
+    # --- headline: graph + persistent do-all, L2 flushed between timed steps
+    clocks = ClockSampler(dev)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_graph, grid_g, _, pop_g, err_g = run_wator(seed, args.warmup, args.steps, "graph", flush, launch)
+    clk = clocks.stop()
+    dist.barrier()
+    ms_graph = dist.max(sum(t_graph))
+    t_plain, grid_p, launches_per_step, pop_p, err_p = run_wator(seed, args.warmup, args.steps, "plain",
+                                                                 flush, launch)
+    ms_plain = dist.max(sum(t_plain))
+    same = bool(np.array_equal(grid_g, grid_p)) and pop_g == pop_p and err_g == 0 and err_p == 0
+    value = dist.world * args.steps / (ms_graph / 1e3)
+    plain_value = dist.world * args.steps / (ms_plain / 1e3)
+
+    out = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": dist.world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "seed": cfg.seed, "mode": "graph+persistent do-all",
+                      "l2": "flushed (256 MiB write) between timed steps, outside the timed region",
+                      "parallelism": f"replicas x{dist.world}", "launch": launch},
+           "plain_steps_per_s": plain_value, "graph_steps_per_s": value,
+           "graph_vs_plain": ms_plain / ms_graph, "graph_equals_plain": same,
+           "populations_after": {"fish": pop_g[0], "sharks": pop_g[1],
+                                 "steps": args.warmup + args.steps},
+           "gpu_launches": int(round(launches_per_step * args.steps)) if launches_per_step else None,
+           "clocks": clk}
+
+    if dist.rank == 0 and not args.skip_secondary:
+        # --- dominant kernel of the step, with its roofline
+        prof = wator_kernel_profile(seed, 20, 20, flush)
+        tot = {k: sum(v["ms"]) for k, v in prof.items()}
+        dom = max(tot, key=tot.get)
+        d = prof[dom]
+        avg_ms = statistics.mean(d["ms"])
+        alg = statistics.mean(d["bytes"])
+        ach = alg / (avg_ms / 1e3) / 1e9
+        out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                           "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                           "peak_kind": peak_kind, "avg_launch_ms": avg_ms, "alg_bytes_per_launch": alg}
+        out["step_kernels_ms"] = {k: {"method": statistics.mean(v["ms"]),
+                                      "enumeration": statistics.mean(v["enum_ms"])} for k, v in prof.items()}
+        # --- do-all HBM sweep (spec kernel), > L2 working sets
+        sweep = {}
+        for lg, holes in ((26, False), (26, True), (24, False)):
+            r = doall_sweep(lg, holes, flush)
+            sweep[f"2^{lg}{'_holes' if holes else ''}"] = r
+        best = sweep["2^26"]
+        out["doall_hbm_gbs"] = best["gbs"]
+        out["doall_roofline"] = {"kernel": "k_micro_scale_vec<4,2>", "bound": "hbm", "achieved": best["gbs"],
+                                 "peak": hbm_peak, "unit": "GB/s", "frac": best["gbs"] / hbm_peak,
+                                 "traffic": None, "peak_kind": peak_kind,
+                                 "alg_bytes_per_launch": best["alg_bytes"], "avg_launch_ms": best["ms"]}
+        out["doall_sweep"] = sweep
+        # --- alloc + free
+        storm = alloc_free_storm(24, flush)
+        out["alloc_free_ops_per_s"] = storm["ops_per_s"]
+        out["alloc_free"] = storm
+        out["heap_utilisation"] = heap_utilisation()
+        # --- end to end through host buffers
+        out["e2e"] = e2e_wator(seed, args.warmup, args.steps, flush)
+        # --- oracle on the host cores
+        out["cpu_baseline"] = cpu_baseline(seed)
+    dist.barrier()
+    if dist.rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return dsoa_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

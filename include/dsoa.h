@@ -97,6 +97,14 @@ int dsoa_parallel_new(dsoa_heap* h, int type, uint64_t n, int ctor_id,
 int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args_host,
                      size_t args_bytes);
 
+/* The method kernel of dsoa_parallel_do alone, over the snapshot and block
+ * list of the latest enumeration of `type` (dsoa_enumerate or a previous
+ * dsoa_parallel_do of the same type).  Valid only while no object of `type`
+ * was created or deleted since that enumeration, except by methods run this
+ * way on the same snapshot.  Used to time or to repeat the do-all kernel. */
+int dsoa_parallel_do_enumerated(dsoa_heap* h, int type, int method_id, const void* args_host,
+                                size_t args_bytes);
+
 /* Run built-in plain kernel `kernel_id` (dsoa_apps.h) with n logical threads:
  * an ordinary CUDA kernel that may call device new/delete (Sec. 2.1, "new and
  * destroy are device functions callable from GPU code"). */

@@ -27,6 +27,7 @@ extern "C" {
 #define DSOA_M_MICRO_GATHER 104       /* x_out[id] = x, live_out[id] = 1                   */
 #define DSOA_M_MICRO_STATS 105        /* accumulate dsoa_micro_stats                        */
 #define DSOA_M_MICRO_SCALE_TMA 106    /* same as SCALE, columns staged by bulk async copies */
+#define DSOA_M_MICRO_DELETE_ALL 107   /* delete this (every object of the snapshot)         */
 typedef struct {
     uint64_t seed;       /* SplitMix64 key                                   */
     uint32_t id_base;    /* constructor: first id                            */

@@ -394,25 +394,33 @@ __device__ __forceinline__ F& dsoa_field(const dsoa_ctx& c, dsoa_obj h, uint32_t
 }
 
 /* ------------------------------------------------------------------------
- * Parallel do-all kernel (Sec. 3.7, Fig. 6-7): 64 consecutive threads per
- * block of R; thread tid serves slot tid % 64 of blocks R[(tid + k n) / 64].
+ * Parallel do-all kernel (Sec. 3.7, Fig. 6-7).  With G = 1 (the paper's
+ * assignment) 64 consecutive threads serve one block of R: thread tid serves
+ * slot tid % 64 of blocks R[(tid + k n) / 64].  With G = 2 one warp serves a
+ * block, lane l taking slots l and l + 32 (two coalesced 128-byte rows).
  * Persistent: the grid is sized to the GPU and reads r from device memory,
- * so the launch is independent of r (graph-capturable).  M must provide
+ * so the launch does not depend on r (graph-capturable).  M provides
  *   static __device__ void run(const dsoa_ctx&, uint32_t type, uint64_t bid,
  *                              uint32_t slot, const Args&);
  * ------------------------------------------------------------------------ */
-template <class M>
+template <class M, int G = 1>
 __global__ void dsoa_doall_kernel(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                   const unsigned long long* __restrict__ occ,
                                   const uint32_t* __restrict__ r_dev, typename M::Args args) {
+    constexpr uint32_t TPB = 64u / G;                          /* threads per block */
     const uint64_t n = (uint64_t)gridDim.x * blockDim.x;      /* multiple of 64 */
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t s = (uint32_t)(tid & 63u);
-    const uint64_t total = (uint64_t)(*r_dev) * 64u;
+    const uint32_t s0 = (uint32_t)(tid % TPB);
+    const uint64_t total = (uint64_t)(*r_dev) * TPB;
     for (uint64_t g = tid; g < total; g += n) {
-        const uint64_t i = g >> 6;
+        const uint64_t i = g / TPB;
         const unsigned long long o = __ldg(&occ[i]);
-        if ((o >> s) & 1ull) M::run(c, t, (uint64_t)__ldg(&R[i]), s, args);
+        const uint64_t bid = (uint64_t)__ldg(&R[i]);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const uint32_t s = s0 + (uint32_t)k * TPB;
+            if ((o >> s) & 1ull) M::run(c, t, bid, s, args);
+        }
     }
 }
 

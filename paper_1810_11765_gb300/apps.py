@@ -22,6 +22,15 @@ def _dev_u8(n, device):
     return torch.zeros(max(int(n), 1), dtype=torch.uint8, device=device)
 
 
+def _grid_on_device(init, device):
+    """An initial grid as a flat uint8 device tensor (host arrays are copied)."""
+    if init is None:
+        return None
+    if isinstance(init, torch.Tensor):
+        return init.to(device=device, dtype=torch.uint8).contiguous().view(-1)
+    return torch.as_tensor(np.ascontiguousarray(init, dtype=np.uint8).reshape(-1)).to(device)
+
+
 def _upload(dst: torch.Tensor, offset: int, raw: bytes):
     src = torch.frombuffer(bytearray(raw), dtype=torch.uint8)
     dst[offset:offset + len(raw)].copy_(src)
@@ -138,9 +147,7 @@ class GolWorld:
         e.cellmap, e.occ, e.claim, e.seed = cellmap.data_ptr(), occ.data_ptr(), None, seed
         e.w, e.h, e.t, e.state = w, h, 0, D.INST_RUN
         self.table.put(slot)
-        ini = None
-        if init is not None:
-            ini = torch.as_tensor(np.ascontiguousarray(init, dtype=np.uint8).reshape(-1)).to(self.device)
+        ini = _grid_on_device(init, self.device)
         self.heap.parallel_new(self.cell_type, n, D.C_GOL_CELL, self.args(slot, ini))
         if ini is not None:
             self.bufs[slot] = (cellmap, occ, ini)   # keep alive until the kernel ran
@@ -199,9 +206,7 @@ class WatorWorld:
         cellmap = torch.zeros(n, dtype=torch.int64, device=self.device)
         occ = _dev_u8(n, self.device)
         claim = torch.full((n,), -1, dtype=torch.int32, device=self.device)
-        ini = None
-        if init is not None:
-            ini = torch.as_tensor(np.ascontiguousarray(init, dtype=np.uint8).reshape(-1)).to(self.device)
+        ini = _grid_on_device(init, self.device)
         self.bufs[slot] = (cellmap, occ, claim, ini)
         e = self.table.host[slot]
         e.cellmap, e.occ, e.claim, e.seed = cellmap.data_ptr(), occ.data_ptr(), claim.data_ptr(), seed

@@ -1,0 +1,80 @@
+"""Launch-shape autotuner for graph-captured step loops.
+
+Searches do-all threads per CTA, persistent CTAs per SM, slots per thread (one block
+per 64 threads, or one block per warp) and the compaction kernel's tiles per CTA.
+Each candidate runs a fresh world from the same seed, captures one step as a CUDA
+graph and times replays with CUDA events (L2 flushed between replays, as in the
+benchmark).  Results are cached per GPU name and workload in ``_tune/``.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+import statistics
+
+import torch
+
+from . import dsoa as D
+from .apps import WatorWorld
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE_DIR = os.path.join(HERE, "_tune")
+
+CANDIDATES = [dict(tpb=tpb, ctas_per_sm=ctas, slots_per_thread=spt, scan_tiles=scan)
+              for tpb, ctas, spt, scan in itertools.product((128, 256, 512), (2, 4, 8), (1, 2), (1, 2))
+              if tpb * ctas <= 4096]
+
+
+def _cache_path(key: str) -> str:
+    gpu = torch.cuda.get_device_name().replace(" ", "_")
+    return os.path.join(CACHE_DIR, f"{key}-{gpu}.json")
+
+
+def time_wator_step(seed: int, launch: dict, side: int = 1024, warmup: int = 5, reps: int = 15,
+                    flush: torch.Tensor | None = None) -> float:
+    """Median ms of one graph replay of a Wa-Tor step under `launch`."""
+    heap = D.Heap(512 << 20)
+    w = WatorWorld(heap)
+    heap.freeze()
+    heap.set_launch(**launch)
+    w.add(side, side, seed)
+    heap.graph_begin()
+    w.step()
+    g = heap.graph_end()
+    for _ in range(warmup):
+        g.launch()
+    times = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.launch()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    g.close()
+    heap.close()
+    return statistics.median(times)
+
+
+def best_wator_launch(seed: int, use_cache: bool = True, verbose: bool = False) -> dict:
+    path = _cache_path("wator1024")
+    if use_cache and os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)["best"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    results = []
+    for cand in CANDIDATES:
+        ms = time_wator_step(seed, cand, flush=flush)
+        results.append((ms, cand))
+        if verbose:
+            print(f"{ms:.4f} ms  {cand}")
+    results.sort(key=lambda r: r[0])
+    best = results[0][1]
+    os.makedirs(CACHE_DIR, exist_ok=True)
+    with open(path, "w") as f:
+        json.dump({"best": best, "ms": results[0][0],
+                   "all": [{"ms": m, **c} for m, c in results]}, f, indent=1)
+    return best

@@ -47,11 +47,15 @@ struct dsoa_heap {
     // launch shapes
     int doall_tpb = 256;
     int doall_ctas_per_sm = 8;
-    int slots_per_thread = 4;
+    int slots_per_thread = 1;        // generic do-all: 1 (64 threads/block) or 2 (a warp/block);
+                                     // vectorised microbench kernel: 1, 2 or 4
+    int vec_slots_per_thread = 4;    // vectorised kernels: slots per thread (1, 2 or 4)
     int scan_tiles_per_cta = 1;
 
     uint32_t launch_seq = 0;
     uint64_t launches = 0;
+    int enumerated_type = -1;        // type of the block list currently in R
+    bool skip_enumeration = false;   // set by dsoa_parallel_do_enumerated
 };
 
 struct dsoa_graph {
@@ -64,6 +68,7 @@ int dsoa_ensure_frozen(dsoa_heap* h);
 int dsoa_check_launch(dsoa_heap* h);                 // after a kernel launch
 dsoa_ctx dsoa_launch_ctx(dsoa_heap* h);              // ctx with a fresh rotation seed
 int dsoa_enumerate_internal(dsoa_heap* h, int type); // scan + compaction into R / Rocc
+int dsoa_prepare_doall(dsoa_heap* h, int type);      // enumerate unless told to reuse R
 unsigned dsoa_doall_grid(dsoa_heap* h);              // persistent do-all grid
 unsigned dsoa_new_grid(dsoa_heap* h, uint64_t n, int tpb);
 
@@ -87,10 +92,14 @@ int dsoa_traffic_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, siz
 // Launch a do-all of method M over `type` (enumeration + persistent kernel).
 template <class M>
 int dsoa_run_doall(dsoa_heap* h, int type, const typename M::Args& args) {
-    int rc = dsoa_enumerate_internal(h, type);
+    int rc = dsoa_prepare_doall(h, type);
     if (rc) return rc;
-    dsoa_doall_kernel<M><<<dsoa_doall_grid(h), h->doall_tpb, 0, h->stream>>>(
-        dsoa_launch_ctx(h), (uint32_t)type, h->R, h->Rocc, h->r_dev, args);
+    if (h->slots_per_thread >= 2)
+        dsoa_doall_kernel<M, 2><<<dsoa_doall_grid(h), h->doall_tpb, 0, h->stream>>>(
+            dsoa_launch_ctx(h), (uint32_t)type, h->R, h->Rocc, h->r_dev, args);
+    else
+        dsoa_doall_kernel<M, 1><<<dsoa_doall_grid(h), h->doall_tpb, 0, h->stream>>>(
+            dsoa_launch_ctx(h), (uint32_t)type, h->R, h->Rocc, h->r_dev, args);
     return dsoa_check_launch(h);
 }
 

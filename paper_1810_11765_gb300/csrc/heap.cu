@@ -330,7 +330,14 @@ int dsoa_enumerate_internal(dsoa_heap* h, int type) {
             k_compact<1><<<(unsigned)h->tiles, 64, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_off, h->R, h->Rocc);
             break;
     }
-    return dsoa_check_launch(h);
+    rc = dsoa_check_launch(h);
+    if (rc == DSOA_OK) h->enumerated_type = type;
+    return rc;
+}
+
+int dsoa_prepare_doall(dsoa_heap* h, int type) {
+    if (h->skip_enumeration) return h->enumerated_type == type ? DSOA_OK : DSOA_ERR_INVALID_ARG;
+    return dsoa_enumerate_internal(h, type);
 }
 
 // ------------------------------------------------------------------------
@@ -474,6 +481,15 @@ int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args, si
     if (method_id >= 300 && method_id < 400) return dsoa_wator_do(h, type, method_id, args, nb);
     if (method_id >= 400 && method_id < 500) return dsoa_traffic_do(h, type, method_id, args, nb);
     return DSOA_ERR_UNKNOWN_METHOD;
+}
+
+int dsoa_parallel_do_enumerated(dsoa_heap* h, int type, int method_id, const void* args, size_t nb) {
+    if (!h) return DSOA_ERR_INVALID_ARG;
+    if (!h->frozen) return DSOA_ERR_NOT_FROZEN;
+    h->skip_enumeration = true;
+    const int rc = dsoa_parallel_do(h, type, method_id, args, nb);
+    h->skip_enumeration = false;
+    return rc;
 }
 
 int dsoa_run_kernel(dsoa_heap* h, int kernel_id, uint64_t n, const void* args, size_t nb) {
@@ -629,6 +645,7 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
     if (slots_per_thread) {
         if (slots_per_thread != 1 && slots_per_thread != 2 && slots_per_thread != 4) return DSOA_ERR_INVALID_ARG;
         h->slots_per_thread = slots_per_thread;
+        h->vec_slots_per_thread = slots_per_thread;
     }
     if (scan_tiles) {
         if (scan_tiles != 1 && scan_tiles != 2) return DSOA_ERR_INVALID_ARG;

@@ -40,6 +40,13 @@ struct MicroDelete {
     }
 };
 
+struct MicroDeleteAll {
+    using Args = dsoa_micro_args;
+    static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args&) {
+        dsoa_delete(c, dsoa_make_handle(t, bid, s));
+    }
+};
+
 struct MicroGather {
     using Args = dsoa_micro_args;
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
@@ -176,12 +183,12 @@ int dsoa_micro_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
     if (rc) return rc;
     switch (method) {
         case DSOA_M_MICRO_SCALE: {
-            rc = dsoa_enumerate_internal(h, type);
+            rc = dsoa_prepare_doall(h, type);
             if (rc) return rc;
             const dsoa_ctx c = dsoa_launch_ctx(h);
             const unsigned g = dsoa_doall_grid(h);
             const int tpb = h->doall_tpb;
-            switch (h->slots_per_thread) {
+            switch (h->vec_slots_per_thread) {
                 case 1: k_micro_scale_vec<1, 4><<<g, tpb, 0, h->stream>>>(c, type, h->R, h->Rocc, h->r_dev); break;
                 case 2: k_micro_scale_vec<2, 2><<<g, tpb, 0, h->stream>>>(c, type, h->R, h->Rocc, h->r_dev); break;
                 default: k_micro_scale_vec<4, 2><<<g, tpb, 0, h->stream>>>(c, type, h->R, h->Rocc, h->r_dev); break;
@@ -190,12 +197,13 @@ int dsoa_micro_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
         }
         case DSOA_M_MICRO_SCALE_SCALAR: return dsoa_run_doall<MicroScale>(h, type, args);
         case DSOA_M_MICRO_DELETE: return dsoa_run_doall<MicroDelete>(h, type, args);
+        case DSOA_M_MICRO_DELETE_ALL: return dsoa_run_doall<MicroDeleteAll>(h, type, args);
         case DSOA_M_MICRO_GATHER:
             if (!args.x_out || !args.live_out) return DSOA_ERR_INVALID_ARG;
             return dsoa_run_doall<MicroGather>(h, type, args);
         case DSOA_M_MICRO_STATS: {
             if (!args.stats) return DSOA_ERR_INVALID_ARG;
-            rc = dsoa_enumerate_internal(h, type);
+            rc = dsoa_prepare_doall(h, type);
             if (rc) return rc;
             k_micro_stats<<<dsoa_doall_grid(h), 256, 0, h->stream>>>(h->ctx, type, h->R, h->Rocc, h->r_dev,
                                                                    (dsoa_micro_stats*)args.stats);

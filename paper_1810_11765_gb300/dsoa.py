@@ -26,7 +26,7 @@ CHECK_NAMES = ["hier", "free_xor", "multi_type", "active_subset", "type", "free_
 
 # built-in ids (dsoa_apps.h)
 C_MICRO, M_MICRO_SCALE, M_MICRO_SCALE_SCALAR, M_MICRO_DELETE = 100, 101, 102, 103
-M_MICRO_GATHER, M_MICRO_STATS, M_MICRO_SCALE_TMA = 104, 105, 106
+M_MICRO_GATHER, M_MICRO_STATS, M_MICRO_SCALE_TMA, M_MICRO_DELETE_ALL = 104, 105, 106, 107
 C_GOL_CELL, M_GOL_SPREAD, M_GOL_REAP, M_GOL_DECIDE, M_GOL_READ, M_GOL_KILL = 200, 201, 202, 203, 204, 205
 K_GOL_ADVANCE = 250
 M_WATOR_FISH_CHOOSE, M_WATOR_FISH_MOVE, M_WATOR_SHARK_CHOOSE, M_WATOR_SHARK_MOVE = 301, 302, 303, 304
@@ -77,7 +77,7 @@ class TrafficArgs(ctypes.Structure):
 ABI_FUNCTIONS = [
     "dsoa_heap_create", "dsoa_heap_create_from", "dsoa_register_type", "dsoa_heap_freeze",
     "dsoa_heap_info", "dsoa_field_offset", "dsoa_parallel_new", "dsoa_parallel_do",
-    "dsoa_run_kernel", "dsoa_enumerate", "dsoa_count", "dsoa_count_async",
+    "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_enumerate", "dsoa_count", "dsoa_count_async",
     "dsoa_free_blocks_async", "dsoa_get_error", "dsoa_check", "dsoa_export_state",
     "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
     "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_launch_count",
@@ -106,6 +106,7 @@ def load(path: str | None = None):
         "dsoa_register_type": [vp, vp, i32, vp], "dsoa_heap_freeze": [vp],
         "dsoa_heap_info": [vp, vp, vp, vp, vp], "dsoa_field_offset": [vp, i32, i32, vp],
         "dsoa_parallel_new": [vp, i32, u64, i32, vp, sz], "dsoa_parallel_do": [vp, i32, i32, vp, sz],
+        "dsoa_parallel_do_enumerated": [vp, i32, i32, vp, sz],
         "dsoa_run_kernel": [vp, i32, u64, vp, sz], "dsoa_enumerate": [vp, i32, vp, vp, vp],
         "dsoa_count": [vp, i32, vp], "dsoa_count_async": [vp, i32, vp],
         "dsoa_free_blocks_async": [vp, vp], "dsoa_get_error": [vp, vp], "dsoa_check": [vp, vp],
@@ -223,6 +224,10 @@ class Heap:
     def parallel_do(self, t: int, method: int, args):
         _ok(load().dsoa_parallel_do(self._h, t, method, ctypes.byref(args), ctypes.sizeof(args)),
             "dsoa_parallel_do")
+
+    def parallel_do_enumerated(self, t: int, method: int, args):
+        _ok(load().dsoa_parallel_do_enumerated(self._h, t, method, ctypes.byref(args), ctypes.sizeof(args)),
+            "dsoa_parallel_do_enumerated")
 
     def run_kernel(self, kernel: int, n: int, args):
         _ok(load().dsoa_run_kernel(self._h, kernel, n, ctypes.byref(args), ctypes.sizeof(args)),
