@@ -397,6 +397,10 @@ def dsoa_arm(args):
     dev = dist.local if dist.world > 1 else 0
     torch.cuda.set_device(dev)
     build.build()
+    # every heap and torch op of the bench runs on one non-default stream, which
+    # stream capture (CUDA graphs) requires; events are recorded on it too
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     cfg = inputs.WatorConfig()
     seed = cfg.seed + 7919 * dist.rank          # one independent replica per rank
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")

@@ -168,7 +168,7 @@ int dsoa_graph_launch(dsoa_graph* g, void* stream);
 int dsoa_graph_destroy(dsoa_graph* g);
 
 /* Launch shape of do-all and scan kernels (0 keeps the current value):
- * threads per CTA of the do-all (multiple of 64), CTAs per SM of the persistent
+ * threads per CTA of the do-all (multiple of 64, at most 512), CTAs per SM of the persistent
  * do-all grid, slots handled per thread by vectorised methods (1, 2 or 4), and
  * allocated-bitmap level-1 words per CTA of the compaction kernel. */
 int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,

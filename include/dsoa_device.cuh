@@ -49,6 +49,9 @@
 #ifndef DSOA_TAKE_ATTEMPTS
 #define DSOA_TAKE_ATTEMPTS 256u
 #endif
+#ifndef DSOA_OOM_ROUNDS
+#define DSOA_OOM_ROUNDS 16u               /* rounds with an empty free bitmap = OOM */
+#endif
 #ifndef DSOA_LOOKUP_ATTEMPTS
 #define DSOA_LOOKUP_ATTEMPTS 5            /* active-block lookups before slow path  */
 #endif
@@ -300,6 +303,7 @@ __device__ inline unsigned long long dsoa_leader_reserve(const dsoa_ctx& c, uint
                                                          uint32_t h, uint64_t* bid_out) {
     const uint32_t act = dsoa_bm_active(t);
     const bool rot = !(c.flags & DSOA_FLAG_NO_ROTATE);
+    uint32_t empty_free = 0;   /* rounds that found the free-block bitmap empty */
     for (uint32_t round = 0; round < DSOA_ALLOC_ROUNDS; ++round) {
         int64_t bid = -1;
         for (uint32_t a = 0; a < DSOA_LOOKUP_ATTEMPTS && bid < 0; ++a)
@@ -307,7 +311,15 @@ __device__ inline unsigned long long dsoa_leader_reserve(const dsoa_ctx& c, uint
         if (bid < 0) {
             bid = dsoa_bm_take(c, dsoa_bm_free(), h ^ round);
             if (bid == -2) continue;
-            if (bid < 0) { dsoa_raise(c, DSOA_DEV_OOM); return 0ull; }
+            if (bid < 0) {
+                /* No free block.  Blocks that other warps initialised in the
+                 * same burst may still have free slots once their active bits
+                 * are set: look again before reporting OOM (Alg. 1 retries
+                 * forever; here a bounded number of times). */
+                if (++empty_free >= DSOA_OOM_ROUNDS) { dsoa_raise(c, DSOA_DEV_OOM); return 0ull; }
+                __nanosleep(256u);
+                continue;
+            }
             dsoa_block_init(c, (uint64_t)bid, t);
             dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid);
             dsoa_bm_set(c, act, (uint64_t)bid);
@@ -404,7 +416,7 @@ __device__ __forceinline__ F& dsoa_field(const dsoa_ctx& c, dsoa_obj h, uint32_t
  *                              uint32_t slot, const Args&);
  * ------------------------------------------------------------------------ */
 template <class M, int G = 1>
-__global__ void dsoa_doall_kernel(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+__global__ void __launch_bounds__(512) dsoa_doall_kernel(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                   const unsigned long long* __restrict__ occ,
                                   const uint32_t* __restrict__ r_dev, typename M::Args args) {
     constexpr uint32_t TPB = 64u / G;                          /* threads per block */

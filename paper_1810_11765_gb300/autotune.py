@@ -64,13 +64,18 @@ def best_wator_launch(seed: int, use_cache: bool = True, verbose: bool = False) 
     if use_cache and os.path.exists(path):
         with open(path) as f:
             return json.load(f)["best"]
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     results = []
-    for cand in CANDIDATES:
-        ms = time_wator_step(seed, cand, flush=flush)
-        results.append((ms, cand))
-        if verbose:
-            print(f"{ms:.4f} ms  {cand}")
+    # stream capture needs a non-default stream
+    stream = torch.cuda.current_stream()
+    if stream.cuda_stream == 0:
+        stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        for cand in CANDIDATES:
+            ms = time_wator_step(seed, cand, flush=flush)
+            results.append((ms, cand))
+            if verbose:
+                print(f"{ms:.4f} ms  {cand}")
     results.sort(key=lambda r: r[0])
     best = results[0][1]
     os.makedirs(CACHE_DIR, exist_ok=True)

@@ -635,7 +635,7 @@ int dsoa_graph_destroy(dsoa_graph* g) {
 int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread, int scan_tiles) {
     if (!h) return DSOA_ERR_INVALID_ARG;
     if (tpb) {
-        if (tpb < 64 || tpb > 1024 || tpb % 64) return DSOA_ERR_INVALID_ARG;
+        if (tpb < 64 || tpb > 512 || tpb % 64) return DSOA_ERR_INVALID_ARG;
         h->doall_tpb = tpb;
     }
     if (ctas_per_sm) {

@@ -65,7 +65,7 @@ struct MicroGather {
 // in flight per SM; stores of partially occupied vectors fall back to
 // per-element stores so that slots outside the snapshot are never written.
 template <int SPT, int U>
-__global__ void __launch_bounds__(256) k_micro_scale_vec(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+__global__ void __launch_bounds__(512) k_micro_scale_vec(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                                          const unsigned long long* __restrict__ occ,
                                                          const uint32_t* __restrict__ r_dev) {
     constexpr uint32_t TPB = 64 / SPT;
@@ -131,7 +131,7 @@ __device__ __forceinline__ double warp_sumd(double v) {
 
 // Statistics over the snapshot: whole warps read 32 slots of one block each;
 // unoccupied lanes contribute zero; one set of atomics per warp.
-__global__ void __launch_bounds__(256) k_micro_stats(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+__global__ void __launch_bounds__(512) k_micro_stats(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                                      const unsigned long long* __restrict__ occ,
                                                      const uint32_t* __restrict__ r_dev, dsoa_micro_stats* out) {
     const uint64_t n = (uint64_t)gridDim.x * blockDim.x;

@@ -78,3 +78,30 @@ def test_batched_instances_match_alone():
         ref, _ = oracle.wator_run(a, b, 40, seed=sd)
         assert np.array_equal(w.read(slot), ref)
     assert heap.get_error() == 0
+
+
+@pytest.mark.parametrize("launch", [dict(), dict(tpb=128, ctas_per_sm=4, slots_per_thread=2, scan_tiles=2)])
+def test_graph_captured_steps_match_oracle(launch):
+    """One step captured as a CUDA graph and replayed: the step index lives in
+    device memory, so replays advance the simulation exactly like plain steps."""
+    import torch
+    W, H, steps, seed = 128, 96, 60, 41
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        heap, w = world(32 << 20)
+        if launch:
+            heap.set_launch(**launch)
+        slot = w.add(W, H, seed)
+        heap.graph_begin()
+        w.step()
+        g = heap.graph_end()
+        for _ in range(steps):
+            g.launch()
+        s.synchronize()
+        grid = w.read(slot)
+        counts = w.counts()
+    ref, st = oracle.wator_run(W, H, steps, seed=seed)
+    assert np.array_equal(grid, ref)
+    assert counts == (st[-1]["fish"], st[-1]["sharks"])
+    assert heap.get_error() == 0
+    g.close()
