@@ -188,6 +188,39 @@ int dsoa_heap_destroy(dsoa_heap* h);
 /* Human-readable name of an error code. */
 const char* dsoa_error_string(int code);
 
+/* ---- Enumeration without allocation (the paper has no counterpart) ----
+ * For callers that cannot allocate device memory while they run: a host
+ * program whose own allocator owns the GPU's memory under a fixed budget, a
+ * latency-critical loop in which cudaMalloc / cudaFree would synchronise the
+ * device, or code that keeps several enumerations alive in buffers it manages
+ * itself.  Computes what dsoa_enumerate computes -- the blocks of `type` in
+ * increasing order and the occupied-slot mask of each -- into caller-owned
+ * device buffers R_out_dev[capacity] (u32), occ_out_dev[capacity] (u64) and
+ * *r_out_dev (u32, the number of entries written).  capacity must be at least
+ * the heap's block count (dsoa_heap_info), else DSOA_ERR_INVALID_ARG.
+ *
+ * The scan's working memory (per-tile counts and offsets, a completion ticket)
+ * is a fixed array of 2 * DSOA_NOALLOC_MAX_TILES + 64 u32 (about 33 KB) inside
+ * this library, which every GPU that loads the library holds until the
+ * process exits.  The call allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.  Limits and rules:
+ *   - heaps of at most DSOA_NOALLOC_MAX_TILES * 4096 = 16,777,216 blocks; a
+ *     larger heap returns DSOA_ERR_SCRATCH_LIMIT;
+ *   - the heap must be frozen (DSOA_ERR_NOT_FROZEN otherwise; not frozen
+ *     implicitly) and its device must be the current device;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - every call shares the one array, which keeps the last call's contents;
+ *     the ticket is cleared at the start of each call, counts and offsets are
+ *     overwritten.  Calls that overlap on the GPU (two streams, two heaps at
+ *     once) race on the array: serialise them;
+ *   - asynchronous, ordered on the heap's stream. */
+#define DSOA_NOALLOC_MAX_TILES 4096
+#define DSOA_ERR_SCRATCH_LIMIT (-9)   /* heap larger than the fixed scratch allows */
+int dsoa_enumerate_noalloc(dsoa_heap* h, int type, uint32_t* R_out_dev, uint64_t* occ_out_dev,
+                           uint32_t* r_out_dev, uint64_t capacity);
+
 #ifdef __cplusplus
 }
 #endif

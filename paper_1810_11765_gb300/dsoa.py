@@ -17,7 +17,8 @@ from . import build as _build
 DSOA_OK = 0
 ERRORS = {-1: "invalid argument", -2: "heap layout already frozen", -3: "too many types",
           -4: "heap too small", -5: "CUDA runtime error", -6: "heap layout not frozen",
-          -7: "unknown built-in method", -8: "synchronous call during stream capture"}
+          -7: "unknown built-in method", -8: "synchronous call during stream capture",
+          -9: "heap larger than the fixed no-allocation scratch allows"}
 
 DEV_OOM, DEV_SPIN, DEV_DOUBLE_FREE, DEV_BAD_HANDLE = 1, 2, 4, 8
 FLAG_NO_COALESCE, FLAG_NO_ROTATE = 1, 2
@@ -81,7 +82,7 @@ ABI_FUNCTIONS = [
     "dsoa_free_blocks_async", "dsoa_get_error", "dsoa_check", "dsoa_export_state",
     "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
     "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_launch_count",
-    "dsoa_heap_destroy", "dsoa_error_string",
+    "dsoa_heap_destroy", "dsoa_error_string", "dsoa_enumerate_noalloc",
 ]
 
 _lib = None
@@ -115,6 +116,7 @@ def load(path: str | None = None):
         "dsoa_graph_destroy": [vp], "dsoa_set_launch": [vp, i32, i32, i32, i32],
         "dsoa_set_flags": [vp, u32], "dsoa_launch_count": [vp, vp], "dsoa_heap_destroy": [vp],
         "dsoa_error_string": [i32],
+        "dsoa_enumerate_noalloc": [vp, i32, vp, vp, vp, u64],
     }
     for name, args in sig.items():
         f = getattr(L, name)
