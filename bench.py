@@ -192,49 +192,60 @@ def run_wator(seed, warmup, steps, mode, flush, launch=None):
     return times, grid, per_step_launches, (fish, sharks), err
 
 
-WATOR_KERNELS = [  # (type attr, method, algorithmic bytes per agent)
-    ("fish_type", "M_WATOR_FISH_CHOOSE", 24),
-    ("fish_type", "M_WATOR_FISH_MOVE", 20),
-    ("shark_type", "M_WATOR_SHARK_CHOOSE", 28),
-    ("shark_type", "M_WATOR_SHARK_MOVE", 32),
+WATOR_KERNELS = [  # (type attr, method, reuses the previous snapshot, algorithmic bytes per agent)
+    ("fish_type", "M_WATOR_FISH_CHOOSE", False, 24),
+    ("fish_type", "M_WATOR_FISH_MOVE", True, 20),
+    ("shark_type", "M_WATOR_SHARK_CHOOSE", False, 28),
+    ("shark_type", "M_WATOR_SHARK_MOVE", True, 32),
 ]
 
 
 def wator_kernel_profile(seed, warmup, steps, flush):
-    """Per-kernel CUDA-event durations of one plain Wa-Tor step, kernel by kernel."""
+    """CUDA-event duration of each kernel of a plain Wa-Tor step, launched exactly
+    as the step launches it (choose methods: one fused enumeration + do-all
+    kernel; move methods: one do-all kernel on the choose snapshot)."""
     import torch
     from paper_1810_11765_gb300 import dsoa as D
     heap, w = wator_world(seed)
     w.add(1024, 1024, seed)
     for _ in range(warmup):
         w.step()
+    M = heap.info()["num_blocks"]
     acc = {}
     a = w.args()
     for _ in range(steps):
         fish, sharks = w.counts()
         flush.zero_()
-        for tattr, meth, bpa in WATOR_KERNELS:
+        for tattr, meth, reuse, bpa in WATOR_KERNELS:
             t = getattr(w, tattr)
-            e0, e1, e2 = ev(), ev(), ev()
+            e0, e1 = ev(), ev()
             e0.record()
-            heap.enumerate(t)
+            if reuse:
+                heap.parallel_do_enumerated(t, getattr(D, meth), a)
+            else:
+                heap.parallel_do(t, getattr(D, meth), a)
             e1.record()
-            heap.parallel_do_enumerated(t, getattr(D, meth), a)
-            e2.record()
-            e2.synchronize()
+            e1.synchronize()
             n_agents = fish if tattr == "fish_type" else sharks
-            r = acc.setdefault(meth, {"ms": [], "bytes": [], "enum_ms": []})
-            r["ms"].append(e1.elapsed_time(e2))
-            r["enum_ms"].append(e0.elapsed_time(e1))
-            r["bytes"].append(n_agents * bpa + (n_agents / 64.0) * 12)
+            blocks = n_agents / 64.0
+            alg = n_agents * bpa + blocks * 12            # fields + R / snapshot read
+            if not reuse:                                 # enumeration inside the kernel
+                alg += M / 8.0 + blocks * (12 + 8)        # level-0 bitmap, R/snapshot write, slot words
+            r = acc.setdefault(meth, {"ms": [], "bytes": []})
+            r["ms"].append(e0.elapsed_time(e1))
+            r["bytes"].append(alg)
         heap.run_kernel(D.K_WATOR_ADVANCE, 1, a)
     torch.cuda.synchronize()
     heap.close()
     return acc
 
 
-def doall_sweep(log2n, holes, flush, iters=10):
-    """do-all HBM GB/s of the 128-bit vectorised SOA kernel (x = x*1.5f + id)."""
+DOALL_KERNELS = {"vec128": ("M_MICRO_SCALE", "k_micro_scale_vec<4,2>"),
+                 "bulk": ("M_MICRO_SCALE_TMA", "k_micro_scale_bulk<8,4>")}
+
+
+def doall_sweep(log2n, holes, flush, iters=10, kernel="vec128"):
+    """do-all HBM GB/s of an SOA do-all kernel (x = x*1.5f + id)."""
     import torch
     from paper_1810_11765_gb300 import dsoa as D
     from paper_1810_11765_gb300.apps import Micro
@@ -251,7 +262,7 @@ def doall_sweep(log2n, holes, flush, iters=10):
         flush.zero_()
         a, b = ev(), ev()
         a.record()
-        m.heap.parallel_do_enumerated(m.type, D.M_MICRO_SCALE, args)
+        m.heap.parallel_do_enumerated(m.type, getattr(D, DOALL_KERNELS[kernel][0]), args)
         b.record()
         b.synchronize()
         times.append(a.elapsed_time(b))
@@ -348,6 +359,70 @@ def e2e_wator(seed, warmup, steps, flush):
     return {"value": steps / (ms / 1e3), "unit": "steps/s",
             "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 16 + 1024 * 1024 / steps,
             "ms": ms, "final_fish": int(counts_host[-2]), "final_sharks": int(counts_host[-1])}
+
+
+def app_steps(kind, steps, flush, warmup=3):
+    """Steps/s of the other apps, graph-captured step vs plain launches (L2
+    flushed between timed steps)."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D, inputs
+    from paper_1810_11765_gb300.apps import GolWorld, TrafficWorld
+    res = {}
+    for mode in ("plain", "graph"):
+        heap = D.Heap(1 << 30)
+        if kind == "gol":
+            cfg = inputs.GolConfig()
+            w = GolWorld(heap)
+            heap.freeze()
+            w.add(cfg.width, cfg.height, cfg.seed)
+        else:
+            L, thr = inputs.traffic_instances()
+            w = TrafficWorld(heap, L, thr, inputs.SEED_TRAFFIC)
+            heap.freeze()
+            w.init()
+        g = None
+        if mode == "graph":
+            heap.graph_begin()
+            w.step()
+            g = heap.graph_end()
+        step = (lambda: g.launch()) if g else w.step
+        for _ in range(warmup):
+            step()
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record()
+            step()
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        res[f"{mode}_steps_per_s"] = steps / (sum(times) / 1e3)
+        res["device_errors"] = heap.get_error()
+        if g:
+            g.close()
+        heap.close()
+    res["graph_vs_plain"] = res["graph_steps_per_s"] / res["plain_steps_per_s"]
+    res["workload"] = ("game of life 512x512 torus, density 1/4" if kind == "gol"
+                       else "traffic: 64 Nagel-Schreckenberg rings, 2^12..2^20 cells")
+    return res
+
+
+def serving_leg(n_req=24, rates=(50.0, 200.0)):
+    """Continuous batching of game-of-life / wa-tor instances (sides 2^8..2^10 and
+    100..300 steps to bound the run time) at swept Poisson arrival rates."""
+    from paper_1810_11765_gb300 import inputs
+    from paper_1810_11765_gb300.serving import Server
+    out = []
+    for rate in rates:
+        reqs = inputs.serving_requests(n_req, rate_per_s=rate, side_log2_min=8, side_log2_max=10,
+                                       steps_min=100, steps_max=300)
+        srv = Server(8 << 30, capacity=32)
+        _, summary = srv.run(reqs)
+        srv.close()
+        summary.pop("rejected", None)
+        out.append({"rate_per_s": rate, **summary})
+    return out
 
 
 def cpu_baseline(seed, sample_steps=100):
@@ -451,16 +526,17 @@ def dsoa_arm(args):
         out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
                            "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
                            "peak_kind": peak_kind, "avg_launch_ms": avg_ms, "alg_bytes_per_launch": alg}
-        out["step_kernels_ms"] = {k: {"method": statistics.mean(v["ms"]),
-                                      "enumeration": statistics.mean(v["enum_ms"])} for k, v in prof.items()}
+        out["step_kernels_ms"] = {k: statistics.mean(v["ms"]) for k, v in prof.items()}
         # --- do-all HBM sweep (spec kernel), > L2 working sets
         sweep = {}
-        for lg, holes in ((26, False), (26, True), (24, False)):
-            r = doall_sweep(lg, holes, flush)
-            sweep[f"2^{lg}{'_holes' if holes else ''}"] = r
-        best = sweep["2^26"]
+        for kern in DOALL_KERNELS:
+            for lg, holes in ((26, False), (26, True), (24, False)):
+                r = doall_sweep(lg, holes, flush, kernel=kern)
+                sweep[f"{kern}:2^{lg}{'_holes' if holes else ''}"] = r
+        kbest = max(DOALL_KERNELS, key=lambda k: sweep[f"{k}:2^26"]["gbs"])
+        best = sweep[f"{kbest}:2^26"]
         out["doall_hbm_gbs"] = best["gbs"]
-        out["doall_roofline"] = {"kernel": "k_micro_scale_vec<4,2>", "bound": "hbm", "achieved": best["gbs"],
+        out["doall_roofline"] = {"kernel": DOALL_KERNELS[kbest][1], "bound": "hbm", "achieved": best["gbs"],
                                  "peak": hbm_peak, "unit": "GB/s", "frac": best["gbs"] / hbm_peak,
                                  "traffic": None, "peak_kind": peak_kind,
                                  "alg_bytes_per_launch": best["alg_bytes"], "avg_launch_ms": best["ms"]}
@@ -470,6 +546,10 @@ def dsoa_arm(args):
         out["alloc_free_ops_per_s"] = storm["ops_per_s"]
         out["alloc_free"] = storm
         out["heap_utilisation"] = heap_utilisation()
+        # --- other apps (plain vs graph) and serving
+        out["gol_512"] = app_steps("gol", 100, flush)
+        out["traffic_64_rings"] = app_steps("traffic", 50, flush)
+        out["serving"] = serving_leg()
         # --- end to end through host buffers
         out["e2e"] = e2e_wator(seed, args.warmup, args.steps, flush)
         # --- oracle on the host cores

@@ -111,6 +111,15 @@ int dsoa_parallel_do_enumerated(dsoa_heap* h, int type, int method_id, const voi
 int dsoa_run_kernel(dsoa_heap* h, int kernel_id, uint64_t n, const void* args_host,
                     size_t args_bytes);
 
+/* destroy() (Sec. 2.1, Alg. 2) for n handles in device memory, one kernel:
+ * frees of the same block in a warp are combined.  Null handles are skipped;
+ * a handle whose type or block is out of range sets DSOA_DEV_BAD_HANDLE, a slot
+ * that is already free in a block that still exists sets DSOA_DEV_DOUBLE_FREE
+ * (both leave the heap unchanged for that handle).  Freeing a slot of a block
+ * that was already emptied and deleted violates Alg. 8's precondition and is
+ * not detected; every retry loop stays bounded, so it cannot hang. */
+int dsoa_delete_handles(dsoa_heap* h, const dsoa_obj* handles_dev, uint64_t n);
+
 /* Enumerate only (the first two kernels of dsoa_parallel_do): after the call,
  * R_dev[0..*r_dev) lists the blocks of `type` in increasing order and
  * occ_dev[i] their occupied-slot masks.  The three pointers are library-owned
@@ -176,7 +185,10 @@ int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
 
 /* Ablation switches of Sec. 6.4 (Fig. 10c): DSOA_FLAG_NO_COALESCE (1) turns
  * off allocation request coalescing, DSOA_FLAG_NO_ROTATE (2) turns off bitmap
- * rotation.  Takes effect for launches issued after the call. */
+ * rotation, DSOA_FLAG_NO_HINT (4) turns off the per-SM last-block hint and
+ * DSOA_FLAG_UNFUSED (8) runs the enumeration of dsoa_parallel_do as separate
+ * kernels instead of inside one cooperative do-all launch (the last two are
+ * not in the paper).  Takes effect for launches issued after the call. */
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags);
 
 /* Number of kernels this heap has launched so far (host-side counter). */

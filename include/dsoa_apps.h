@@ -28,6 +28,7 @@ extern "C" {
 #define DSOA_M_MICRO_STATS 105        /* accumulate dsoa_micro_stats                        */
 #define DSOA_M_MICRO_SCALE_TMA 106    /* same as SCALE, columns staged by bulk async copies */
 #define DSOA_M_MICRO_DELETE_ALL 107   /* delete this (every object of the snapshot)         */
+#define DSOA_M_MICRO_HANDLES 108      /* handles_out[id] = handle of the object with that id */
 typedef struct {
     uint64_t seed;       /* SplitMix64 key                                   */
     uint32_t id_base;    /* constructor: first id                            */
@@ -36,6 +37,7 @@ typedef struct {
     uint8_t* live_out;   /* gather: [n_ids] (device)                         */
     uint64_t n_ids;      /* gather: bound of id                              */
     void* stats;         /* stats: dsoa_micro_stats* (device, pre-zeroed)    */
+    uint64_t* handles_out; /* handles: [n_ids] (device)                      */
 } dsoa_micro_args;
 typedef struct {
     unsigned long long live, sum_id, sum_tag, xor_tag;

@@ -63,6 +63,10 @@ struct dsoa_ctx {
     uint32_t* btype;                     /* [M] block type ids                     */
     unsigned long long* bm;              /* all hierarchical bitmaps               */
     int* err;                            /* sticky DSOA_DEV_* bits                 */
+    uint32_t* hint;                      /* [DSOA_HINT_SLOTS][ntypes] last block with
+                                            free slots per SM sub-slot (advisory)     */
+    uint32_t* grid_scratch;              /* [DSOA_GRID_SCRATCH] per-CTA aggregates and
+                                            grid-barrier words of the fused do-all    */
     uint64_t M;                          /* number of blocks                       */
     uint64_t bm_stride;                  /* u64 words per hierarchical bitmap      */
     uint64_t lvl_off[DSOA_MAX_LEVELS];   /* word offset of level l in a bitmap     */
@@ -77,6 +81,12 @@ struct dsoa_ctx {
 
 #define DSOA_FLAG_NO_COALESCE 1u          /* ablation: one request per leader       */
 #define DSOA_FLAG_NO_ROTATE 2u            /* ablation: plain find-first-set         */
+#define DSOA_FLAG_NO_HINT 4u              /* ablation: no per-SM block hint         */
+#define DSOA_HINT_SLOTS 1024u             /* 256 SMs x 4 warp groups                */
+#define DSOA_FLAG_UNFUSED 8u              /* enumerate with separate kernels        */
+#define DSOA_FUSED_MAX_CTAS 2048u         /* grid limit of the fused do-all         */
+#define DSOA_GRID_SCRATCH (DSOA_FUSED_MAX_CTAS + 64u)
+#define DSOA_NO_BLOCK 0xFFFFFFFFu
 
 /* bitmap ids inside ctx.bm */
 __host__ __device__ __forceinline__ uint32_t dsoa_bm_free() { return 0u; }
@@ -111,12 +121,24 @@ __device__ __forceinline__ void dsoa_st(unsigned long long* p, unsigned long lon
 __device__ __forceinline__ void dsoa_st32(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+/* atomicAnd with acquire semantics at device scope: loads after it observe
+ * what was written before the release (fence + store) whose value it read. */
+__device__ __forceinline__ unsigned long long dsoa_and_acquire(unsigned long long* p, unsigned long long m) {
+    unsigned long long old;
+    asm volatile("atom.acquire.gpu.global.and.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(m) : "memory");
+    return old;
+}
 __device__ __forceinline__ uint32_t dsoa_lane() {
     uint32_t l;
     asm("mov.u32 %0, %%laneid;" : "=r"(l));
     return l;
 }
 __device__ __forceinline__ void dsoa_raise(const dsoa_ctx& c, int bits) { atomicOr(c.err, bits); }
+__device__ __forceinline__ uint32_t dsoa_smid() {
+    uint32_t s;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
+    return s;
+}
 
 /* One wait step of a bounded spin; false once the bound is reached (error set). */
 __device__ __forceinline__ bool dsoa_backoff(const dsoa_ctx& c, uint32_t& spins) {
@@ -226,7 +248,7 @@ __device__ inline int64_t dsoa_bm_find(const dsoa_ctx& c, uint32_t b, uint32_t h
 /* clear() = find-and-clear an arbitrary set bit (Sec. 4.1.2).  -1 when the
  * bitmap is empty at the top (OOM for the free-block bitmap), -2 when
  * DSOA_TAKE_ATTEMPTS attempts lost every race (the caller retries). */
-__device__ inline int64_t dsoa_bm_take(const dsoa_ctx& c, uint32_t b, uint32_t h) {
+__device__ __noinline__ int64_t dsoa_bm_take(const dsoa_ctx& c, uint32_t b, uint32_t h) {
     for (uint32_t a = 0; a < DSOA_TAKE_ATTEMPTS; ++a) {
         const int64_t pos = dsoa_bm_find(c, b, dsoa_hash(h + a * 0x9E3779B9u));
         if (pos >= 0) {
@@ -257,7 +279,7 @@ __device__ inline void dsoa_block_init(const dsoa_ctx& c, uint64_t bid, uint32_t
  * thread freed a slot meanwhile it saw a "first free" and will set the active
  * bit, so the deferred deactivation is done here; retry if the block is empty
  * again. */
-__device__ inline void dsoa_block_invalidate(const dsoa_ctx& c, uint64_t bid) {
+__device__ __noinline__ void dsoa_block_invalidate(const dsoa_ctx& c, uint64_t bid) {
     for (uint32_t it = 0; it < DSOA_SPIN_LIMIT; ++it) {
         const unsigned long long before = atomicAnd(&c.slot[bid], 0ull);
         if (before == DSOA_ALL) {
@@ -278,18 +300,44 @@ __device__ inline void dsoa_block_invalidate(const dsoa_ctx& c, uint64_t bid) {
     dsoa_raise(c, DSOA_DEV_SPIN);
 }
 
+/* Rare transitions of a block, kept out of line so that the hot paths of
+ * allocation and deallocation stay small in registers. */
+__device__ __noinline__ void dsoa_block_first_free(const dsoa_ctx& c, uint32_t t, uint64_t bid) {
+    dsoa_bm_set(c, dsoa_bm_active(t), bid);                 /* was full: active again */
+}
+__device__ __noinline__ void dsoa_block_deactivate(const dsoa_ctx& c, uint32_t t, uint64_t bid) {
+    dsoa_bm_clear(c, dsoa_bm_active(t), bid, true);         /* now full: inactive */
+}
+
 /* Block::deallocate for a set of slots (Alg. 8, multi-slot form used by
  * request coalescing and by rollback).  `t` is the block's type. */
-__device__ inline void dsoa_block_release(const dsoa_ctx& c, uint32_t t, uint64_t bid,
-                                          unsigned long long bits) {
+__device__ __forceinline__ void dsoa_block_release(const dsoa_ctx& c, uint32_t t, uint64_t bid,
+                                                   unsigned long long bits) {
     const unsigned long long before = atomicOr(&c.slot[bid], bits);
     if (before & bits) {
         dsoa_raise(c, DSOA_DEV_DOUBLE_FREE);
         bits &= ~before;
         if (!bits) return;
     }
-    if (before == 0ull) dsoa_bm_set(c, dsoa_bm_active(t), bid);            /* FIRST */
+    if (before == 0ull) dsoa_block_first_free(c, t, bid);                    /* FIRST */
     if ((before | bits) == DSOA_ALL) dsoa_block_invalidate(c, bid);          /* EMPTY */
+}
+
+/* Slow path of Alg. 1 (lines 3-6): take a free block, initialise it for type
+ * t, enter it into allocated[t] and active[t].  -1 = no free block, -2 = every
+ * attempt lost its race. */
+__device__ __noinline__ int64_t dsoa_block_new(const dsoa_ctx& c, uint32_t t, uint32_t h) {
+    const int64_t bid = dsoa_bm_take(c, dsoa_bm_free(), h);
+    if (bid < 0) return bid;
+    dsoa_block_init(c, (uint64_t)bid, t);
+    dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid);
+    dsoa_bm_set(c, dsoa_bm_active(t), (uint64_t)bid);
+    return bid;
+}
+
+/* Roll back slots reserved in a block whose type changed (Alg. 1, line 14). */
+__device__ __noinline__ void dsoa_rollback(const dsoa_ctx& c, uint32_t bt, uint64_t bid, unsigned long long got) {
+    dsoa_block_release(c, bt, bid, got);
 }
 
 /* Leader part of allocate<T> (Alg. 1 with request coalescing, Sec. 4.2):
@@ -299,17 +347,30 @@ __device__ inline void dsoa_block_release(const dsoa_ctx& c, uint32_t t, uint64_
  * slot bits; the thread whose reservation empties the free-slot word marks
  * the block inactive; a type change is rolled back.  Returns the reserved
  * slot mask (0 on OOM or spin bound) and the block in *bid_out. */
-__device__ inline unsigned long long dsoa_leader_reserve(const dsoa_ctx& c, uint32_t t, uint32_t want,
+__device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx& c, uint32_t t, uint32_t want,
                                                          uint32_t h, uint64_t* bid_out) {
     const uint32_t act = dsoa_bm_active(t);
     const bool rot = !(c.flags & DSOA_FLAG_NO_ROTATE);
+    /* Per-SM hint: the block this SM (warp group) last reserved in while it
+     * still had free slots.  Trying it first skips the top-down bitmap search;
+     * a stale hint is just another "Block Full / Deallocated / Replaced" case
+     * of App. A.3 and is caught by the same checks as a stale try_find_set. */
+    uint32_t* hp = nullptr;
+    if (c.hint && !(c.flags & DSOA_FLAG_NO_HINT)) {
+        const uint32_t slot = (dsoa_smid() * 4u + ((threadIdx.x >> 5) & 3u)) % DSOA_HINT_SLOTS;
+        hp = c.hint + slot * c.ntypes + t;
+    }
     uint32_t empty_free = 0;   /* rounds that found the free-block bitmap empty */
     for (uint32_t round = 0; round < DSOA_ALLOC_ROUNDS; ++round) {
         int64_t bid = -1;
+        if (round == 0 && hp) {
+            const uint32_t hb = *hp;
+            if (hb < c.M) bid = hb;
+        }
         for (uint32_t a = 0; a < DSOA_LOOKUP_ATTEMPTS && bid < 0; ++a)
             bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
         if (bid < 0) {
-            bid = dsoa_bm_take(c, dsoa_bm_free(), h ^ round);
+            bid = dsoa_block_new(c, t, h ^ round);
             if (bid == -2) continue;
             if (bid < 0) {
                 /* No free block.  Blocks that other warps initialised in the
@@ -320,24 +381,28 @@ __device__ inline unsigned long long dsoa_leader_reserve(const dsoa_ctx& c, uint
                 __nanosleep(256u);
                 continue;
             }
-            dsoa_block_init(c, (uint64_t)bid, t);
-            dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid);
-            dsoa_bm_set(c, act, (uint64_t)bid);
         }
         const unsigned long long w = dsoa_ld(&c.slot[bid]);
-        if (!w) continue;
-        const uint32_t r = rot ? (dsoa_hash(h + round) & 63u) : 0u;
-        const unsigned long long mask = dsoa_rotl(dsoa_lowest_k(dsoa_rotr(w, r), want), r);
-        const unsigned long long before = atomicAnd(&c.slot[bid], ~mask);
-        const unsigned long long got = before & mask;
-        if (!got) continue;
-        __threadfence();   /* pairs with the fence of dsoa_block_init */
-        const uint32_t bt = dsoa_ld32(&c.btype[bid]);
-        if ((before & ~mask) == 0ull) dsoa_bm_clear(c, dsoa_bm_active(bt), (uint64_t)bid, true);
-        if (bt != t) {                 /* block replaced by another type: roll back */
-            dsoa_block_release(c, bt, (uint64_t)bid, got);
+        if (!w) {
+            if (hp && *hp == (uint32_t)bid) *hp = DSOA_NO_BLOCK;
             continue;
         }
+        const uint32_t r = rot ? (dsoa_hash(h + round) & 63u) : 0u;
+        const unsigned long long mask = dsoa_rotl(dsoa_lowest_k(dsoa_rotr(w, r), want), r);
+        /* acquire: the type read below sees the type written before the
+         * fence of dsoa_block_init whose slot-word store this RMW follows */
+        const unsigned long long before = dsoa_and_acquire(&c.slot[bid], ~mask);
+        const unsigned long long got = before & mask;
+        if (!got) continue;
+        const uint32_t bt = dsoa_ld32(&c.btype[bid]);
+        const bool full = (before & ~mask) == 0ull;
+        if (full) dsoa_block_deactivate(c, bt, (uint64_t)bid);
+        if (bt != t) {                 /* block replaced by another type: roll back */
+            if (hp && *hp == (uint32_t)bid) *hp = DSOA_NO_BLOCK;
+            dsoa_rollback(c, bt, (uint64_t)bid, got);
+            continue;
+        }
+        if (hp) *hp = full ? DSOA_NO_BLOCK : (uint32_t)bid;
         *bid_out = (uint64_t)bid;
         return got;
     }
@@ -428,6 +493,155 @@ __global__ void __launch_bounds__(512) dsoa_doall_kernel(dsoa_ctx c, uint32_t t,
         const uint64_t i = g / TPB;
         const unsigned long long o = __ldg(&occ[i]);
         const uint64_t bid = (uint64_t)__ldg(&R[i]);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const uint32_t s = s0 + (uint32_t)k * TPB;
+            if ((o >> s) & 1ull) M::run(c, t, bid, s, args);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Fused persistent do-all: enumeration and method in ONE cooperative launch.
+ *   phase 1  CTA b counts the allocated blocks of its contiguous range of
+ *            level-1 tiles (hierarchical skip) -> aggregate agg[b]
+ *   barrier
+ *   phase 2  exclusive prefix of agg below b and the total r; CTA b writes
+ *            R / occupancy snapshot for its tiles (sorted, Fig. 7)
+ *   barrier  (the snapshot is complete before any method runs: objects
+ *            created by the method are never visited, Sec. 3.1)
+ *   phase 3  the do-all loop of dsoa_doall_kernel over R
+ * The grid must be co-resident (cooperative launch).  Barrier waits are
+ * bounded; on the bound every CTA sets DSOA_DEV_SPIN and returns.
+ * ------------------------------------------------------------------------ */
+__device__ inline bool dsoa_grid_sync(const dsoa_ctx& c, uint32_t nblocks) {
+    uint32_t* count = c.grid_scratch + DSOA_FUSED_MAX_CTAS;
+    uint32_t* gen = count + 1;
+    __shared__ uint32_t s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1u;
+        const uint32_t g = dsoa_ld32(gen);
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1u) {
+            dsoa_st32(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            uint32_t spins = 0;
+            while (dsoa_ld32(gen) == g) {
+                if (++spins >= (DSOA_SPIN_LIMIT << 4)) { s_ok = 0u; dsoa_raise(c, DSOA_DEV_SPIN); break; }
+                if (spins > 16) __nanosleep(64u);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_ok != 0u;
+}
+
+template <class M, int G = 1>
+__global__ void __launch_bounds__(512) dsoa_doall_fused_kernel(dsoa_ctx c, uint32_t t, uint32_t* __restrict__ R,
+                                                               unsigned long long* __restrict__ occ,
+                                                               uint32_t* __restrict__ r_dev, typename M::Args args) {
+    __shared__ uint32_t list[4096];
+    __shared__ uint32_t red[32];
+    __shared__ uint32_t wsum[2];
+    const uint32_t b = dsoa_bm_alloc(t);
+    const uint32_t nb = gridDim.x, tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint64_t tiles = c.nlevels >= 2 ? c.lvl_words[1] : 1u;
+    const uint64_t w0 = c.lvl_words[0];
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, b, 1) : nullptr;
+    const uint64_t t_lo = tiles * blockIdx.x / nb, t_hi = tiles * (blockIdx.x + 1) / nb;
+    uint32_t* agg = c.grid_scratch;
+    /* phase 1: count this CTA's tiles (warp per tile) */
+    uint32_t mine = 0;
+    for (uint64_t tt = t_lo + warp; tt < t_hi; tt += nwarps) {
+        const unsigned long long sel = L1 ? L1[tt] : 1ull;
+        const uint64_t a = tt * 64 + lane, a2 = a + 32;
+        uint32_t n = 0;
+        if (((sel >> lane) & 1ull) && a < w0) n += __popcll(L0[a]);
+        if (((sel >> (lane + 32)) & 1ull) && a2 < w0) n += __popcll(L0[a2]);
+        for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+        mine += n;
+    }
+    if (lane == 0) red[warp] = mine;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t sum = 0;
+        for (uint32_t w = 0; w < nwarps; ++w) sum += red[w];
+        dsoa_st32(&agg[blockIdx.x], sum);
+    }
+    if (!dsoa_grid_sync(c, nb)) return;
+    /* phase 2: prefix of the aggregates below this CTA and the total */
+    uint32_t below = 0, total = 0;
+    for (uint32_t i = tid; i < nb; i += blockDim.x) {
+        const uint32_t v = dsoa_ld32(&agg[i]);
+        total += v;
+        if (i < blockIdx.x) below += v;
+    }
+    for (int o = 16; o; o >>= 1) {
+        below += __shfl_xor_sync(0xffffffffu, below, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+    }
+    __syncthreads();
+    if (lane == 0) { red[warp] = below; red[16 + warp] = total; }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t sb = 0, st = 0;
+        for (uint32_t w = 0; w < nwarps; ++w) { sb += red[w]; st += red[16 + w]; }
+        red[0] = sb;
+        red[1] = st;
+    }
+    __syncthreads();
+    uint32_t base = red[0];
+    const uint32_t r = red[1];
+    if (blockIdx.x == 0 && tid == 0) *r_dev = r;
+    /* compaction of this CTA's tiles, one tile at a time */
+    for (uint64_t tt = t_lo; tt < t_hi; ++tt) {
+        unsigned long long w = 0ull;
+        if (tid < 64) {
+            const unsigned long long sel = L1 ? L1[tt] : 1ull;
+            const uint64_t wi = tt * 64 + tid;
+            if (((sel >> tid) & 1ull) && wi < w0) w = L0[wi];
+        }
+        const uint32_t cnt = __popcll(w);
+        uint32_t incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += v;
+        }
+        if (tid < 64 && lane == 31) wsum[tid >> 5] = incl;
+        __syncthreads();
+        const uint32_t tile_total = wsum[0] + wsum[1];
+        if (tid < 64) {
+            uint32_t k = incl - cnt + ((tid >= 32) ? wsum[0] : 0u);
+            const uint64_t bid0 = (tt * 64 + tid) * 64;
+            for (unsigned long long x = w; x; x &= x - 1ull)
+                list[k++] = (uint32_t)(bid0 + (uint32_t)(__ffsll((long long)x) - 1));
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < tile_total; i += blockDim.x) {
+            const uint32_t bid = list[i];
+            R[base + i] = bid;
+            occ[base + i] = ~c.slot[bid];
+        }
+        base += tile_total;
+        __syncthreads();
+    }
+    if (!dsoa_grid_sync(c, nb)) return;
+    /* phase 3: the do-all over the snapshot */
+    constexpr uint32_t TPB = 64u / G;
+    const uint64_t n = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + tid;
+    const uint32_t s0 = (uint32_t)(gtid % TPB);
+    const uint64_t work = (uint64_t)r * TPB;
+    for (uint64_t g = gtid; g < work; g += n) {
+        const uint64_t i = g / TPB;
+        const unsigned long long o = dsoa_ld(&occ[i]);
+        const uint64_t bid = (uint64_t)dsoa_ld32(&R[i]);
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             const uint32_t s = s0 + (uint32_t)k * TPB;

@@ -107,6 +107,13 @@ class Micro:
         return {"live": s.live, "sum_id": s.sum_id, "sum_tag": s.sum_tag, "xor_tag": s.xor_tag,
                 "sum_x": s.sum_x}
 
+    def handles(self, n_ids: int) -> torch.Tensor:
+        """Device tensor of the handle of every live object, indexed by id (0 = dead)."""
+        out = torch.zeros(n_ids, dtype=torch.int64, device=self.device)
+        self.heap.parallel_do(self.type, D.M_MICRO_HANDLES,
+                              self.args(handles_out=out.data_ptr(), n_ids=n_ids))
+        return out
+
     def gather(self, n_ids: int):
         x = torch.zeros(n_ids, dtype=torch.float32, device=self.device)
         live = torch.zeros(n_ids, dtype=torch.uint8, device=self.device)
@@ -154,9 +161,11 @@ class GolWorld:
         return slot
 
     def step(self):
+        """One generation.  Spread neither creates nor deletes Alive objects, so
+        Reap runs on Spread's snapshot without enumerating again."""
         a = self.args()
         self.heap.parallel_do(self.alive_type, D.M_GOL_SPREAD, a)
-        self.heap.parallel_do(self.alive_type, D.M_GOL_REAP, a)
+        self.heap.parallel_do_enumerated(self.alive_type, D.M_GOL_REAP, a)
         self.heap.parallel_do(self.cell_type, D.M_GOL_DECIDE, a)
         self.heap.run_kernel(D.K_GOL_ADVANCE, self.table.capacity, a)
 
@@ -216,11 +225,13 @@ class WatorWorld:
         return slot
 
     def step(self):
+        """One step.  The choose methods neither create nor delete agents of their
+        own type, so each move method runs on its choose method's snapshot."""
         a = self.args()
         self.heap.parallel_do(self.fish_type, D.M_WATOR_FISH_CHOOSE, a)
-        self.heap.parallel_do(self.fish_type, D.M_WATOR_FISH_MOVE, a)
+        self.heap.parallel_do_enumerated(self.fish_type, D.M_WATOR_FISH_MOVE, a)
         self.heap.parallel_do(self.shark_type, D.M_WATOR_SHARK_CHOOSE, a)
-        self.heap.parallel_do(self.shark_type, D.M_WATOR_SHARK_MOVE, a)
+        self.heap.parallel_do_enumerated(self.shark_type, D.M_WATOR_SHARK_MOVE, a)
         self.heap.run_kernel(D.K_WATOR_ADVANCE, self.table.capacity, a)
 
     def read(self, slot: int) -> np.ndarray:

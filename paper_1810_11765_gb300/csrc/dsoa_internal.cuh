@@ -35,9 +35,11 @@ struct dsoa_heap {
     // frozen layout
     dsoa_ctx ctx;
     uint64_t tiles = 0;              // level-1 containers of one bitmap (scan tiles)
-    uint32_t* R = nullptr;           // [M] compacted block list
-    unsigned long long* Rocc = nullptr;  // [M] occupied-slot snapshot per R entry
-    uint32_t* r_dev = nullptr;       // number of valid R entries
+    // per registered type: block list of its last enumeration, the occupancy
+    // snapshot of each listed block, and the list length (device)
+    uint32_t* R[DSOA_MAX_TYPES] = {nullptr};
+    unsigned long long* Rocc[DSOA_MAX_TYPES] = {nullptr};
+    uint32_t* r_dev[DSOA_MAX_TYPES] = {nullptr};
     uint32_t* tile_cnt = nullptr;    // [tiles]
     uint32_t* tile_off = nullptr;    // [tiles]
     uint32_t* done = nullptr;        // last-CTA ticket of the tile-count kernel
@@ -52,9 +54,10 @@ struct dsoa_heap {
     int vec_slots_per_thread = 4;    // vectorised kernels: slots per thread (1, 2 or 4)
     int scan_tiles_per_cta = 1;
 
+    uint32_t flags = 0;              // DSOA_FLAG_* applied to every launch
     uint32_t launch_seq = 0;
     uint64_t launches = 0;
-    int enumerated_type = -1;        // type of the block list currently in R
+    bool enumerated[DSOA_MAX_TYPES] = {false};  // R[t] holds an enumeration of type t
     bool skip_enumeration = false;   // set by dsoa_parallel_do_enumerated
 };
 
@@ -64,6 +67,7 @@ struct dsoa_graph {
 };
 
 // ---- helpers implemented in heap.cu ----
+int dsoa_resident_ctas(const void* kernel, int tpb);   // CTAs of `kernel` per SM (cached)
 int dsoa_ensure_frozen(dsoa_heap* h);
 int dsoa_check_launch(dsoa_heap* h);                 // after a kernel launch
 dsoa_ctx dsoa_launch_ctx(dsoa_heap* h);              // ctx with a fresh rotation seed
@@ -89,17 +93,68 @@ int dsoa_traffic_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, siz
         if (e_ != cudaSuccess) return DSOA_ERR_CUDA;     \
     } while (0)
 
+// Persistent grid of `kernel`: CTAs per SM = min(requested, resident), so that
+// the whole grid is one resident wave (no tail of late CTAs).
+template <typename K>
+unsigned dsoa_persistent_grid(dsoa_heap* h, K* kernel, int tpb) {
+    int per_sm = dsoa_resident_ctas(reinterpret_cast<const void*>(kernel), tpb);
+    if (per_sm > h->doall_ctas_per_sm) per_sm = h->doall_ctas_per_sm;
+    if (per_sm < 1) per_sm = 1;
+    return (unsigned)(per_sm * h->num_sms);
+}
+
+// Cooperative launch (every CTA co-resident) of a kernel that uses grid barriers.
+template <typename... KArgs, typename... Args>
+cudaError_t dsoa_launch_cooperative(void (*kernel)(KArgs...), unsigned grid, unsigned tpb, cudaStream_t s,
+                                    Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tpb);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Fused enumeration + do-all of method M in one cooperative persistent launch.
+template <class M, int G>
+int dsoa_run_doall_fused(dsoa_heap* h, int type, const typename M::Args& args) {
+    const int tpb = h->doall_tpb;
+    auto* k = &dsoa_doall_fused_kernel<M, G>;
+    unsigned grid = dsoa_persistent_grid(h, k, tpb);
+    if (grid > DSOA_FUSED_MAX_CTAS) grid = DSOA_FUSED_MAX_CTAS;
+    const cudaError_t e = dsoa_launch_cooperative(k, grid, (unsigned)tpb, h->stream, dsoa_launch_ctx(h),
+                                                  (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], args);
+    h->launches++;
+    if (e != cudaSuccess) { cudaGetLastError(); return DSOA_ERR_CUDA; }
+    h->enumerated[type] = true;
+    return DSOA_OK;
+}
+
 // Launch a do-all of method M over `type` (enumeration + persistent kernel).
 template <class M>
 int dsoa_run_doall(dsoa_heap* h, int type, const typename M::Args& args) {
+    if (!h->skip_enumeration && !(h->flags & DSOA_FLAG_UNFUSED)) {
+        if (!h->frozen) return DSOA_ERR_NOT_FROZEN;
+        if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+        return h->slots_per_thread >= 2 ? dsoa_run_doall_fused<M, 2>(h, type, args)
+                                        : dsoa_run_doall_fused<M, 1>(h, type, args);
+    }
     int rc = dsoa_prepare_doall(h, type);
     if (rc) return rc;
-    if (h->slots_per_thread >= 2)
-        dsoa_doall_kernel<M, 2><<<dsoa_doall_grid(h), h->doall_tpb, 0, h->stream>>>(
-            dsoa_launch_ctx(h), (uint32_t)type, h->R, h->Rocc, h->r_dev, args);
-    else
-        dsoa_doall_kernel<M, 1><<<dsoa_doall_grid(h), h->doall_tpb, 0, h->stream>>>(
-            dsoa_launch_ctx(h), (uint32_t)type, h->R, h->Rocc, h->r_dev, args);
+    const int tpb = h->doall_tpb;
+    if (h->slots_per_thread >= 2) {
+        auto* k = &dsoa_doall_kernel<M, 2>;
+        k<<<dsoa_persistent_grid(h, k, tpb), tpb, 0, h->stream>>>(
+            dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], args);
+    } else {
+        auto* k = &dsoa_doall_kernel<M, 1>;
+        k<<<dsoa_persistent_grid(h, k, tpb), tpb, 0, h->stream>>>(
+            dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], args);
+    }
     return dsoa_check_launch(h);
 }
 

@@ -6,7 +6,10 @@
 // Sec. 4.1.5, Fig. 7), fragmentation accounting (Sec. 6.4).
 #include <algorithm>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "dsoa_internal.cuh"
 
@@ -22,10 +25,11 @@ struct Layout {
     uint32_t nlevels = 0;
     uint64_t lvl_off[DSOA_MAX_LEVELS] = {0}, lvl_words[DSOA_MAX_LEVELS] = {0};
     uint64_t off_data = 0, off_slot = 0, off_btype = 0, off_bm = 0, off_R = 0, off_Rocc = 0,
-             off_tcnt = 0, off_toff = 0, off_small = 0, total = 0;
+             off_tcnt = 0, off_toff = 0, off_hint = 0, off_grid = 0, off_small = 0, total = 0;
 };
 
-bool make_layout(uint64_t M, uint32_t block_bytes, int nbm, Layout* L) {
+bool make_layout(uint64_t M, uint32_t block_bytes, int ntypes, Layout* L) {
+    const int nbm = 1 + 2 * ntypes;
     if (M == 0) return false;
     L->M = M;
     uint64_t words = (M + 63) / 64;
@@ -48,10 +52,12 @@ bool make_layout(uint64_t M, uint32_t block_bytes, int nbm, Layout* L) {
     L->off_slot = p;  p = align_up(p + M * 8, kAlign);
     L->off_btype = p; p = align_up(p + M * 4, kAlign);
     L->off_bm = p;    p = align_up(p + (uint64_t)nbm * L->bm_stride * 8, kAlign);
-    L->off_R = p;     p = align_up(p + M * 4, kAlign);
-    L->off_Rocc = p;  p = align_up(p + M * 8, kAlign);
+    L->off_R = p;     p = align_up(p + M * 4 * (uint64_t)ntypes, kAlign);
+    L->off_Rocc = p;  p = align_up(p + M * 8 * (uint64_t)ntypes, kAlign);
     L->off_tcnt = p;  p = align_up(p + L->tiles * 4, kAlign);
     L->off_toff = p;  p = align_up(p + L->tiles * 4, kAlign);
+    L->off_hint = p;  p = align_up(p + (uint64_t)DSOA_HINT_SLOTS * (uint64_t)ntypes * 4, kAlign);
+    L->off_grid = p;  p = align_up(p + (uint64_t)DSOA_GRID_SCRATCH * 4, kAlign);
     L->off_small = p; p = align_up(p + kSmallWords * 8, kAlign);
     L->total = p;
     return true;
@@ -262,6 +268,12 @@ __global__ void k_check(dsoa_ctx c, unsigned long long* v) {
         if (loc[i]) atomicAdd(&v[i], loc[i]);
 }
 
+__global__ void k_delete_handles(dsoa_ctx c, const dsoa_obj* __restrict__ hs, uint64_t n) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dsoa_delete(c, hs[i]);
+}
+
 bool capturing(cudaStream_t s) {
     cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &st) != cudaSuccess) return false;
@@ -292,7 +304,26 @@ int dsoa_check_launch(dsoa_heap* h) {
 dsoa_ctx dsoa_launch_ctx(dsoa_heap* h) {
     dsoa_ctx c = h->ctx;
     c.seed = 0x9E3779B9u * (++h->launch_seq);
+    c.flags = h->flags;
     return c;
+}
+
+int dsoa_resident_ctas(const void* kernel, int tpb) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_pair(kernel, tpb * 1024 + dev);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, tpb, 0) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    cache[key] = n;
+    return n;
 }
 
 unsigned dsoa_doall_grid(dsoa_heap* h) {
@@ -319,24 +350,24 @@ int dsoa_enumerate_internal(dsoa_heap* h, int type) {
     const int tpb = 256;
     const uint64_t warps = h->tiles;
     const unsigned g1 = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 7) / 8, (uint64_t)h->num_sms * 8));
-    k_tile_count<<<g1, tpb, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_cnt, h->tile_off, h->r_dev, h->done);
+    k_tile_count<<<g1, tpb, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_cnt, h->tile_off, h->r_dev[type], h->done);
     rc = dsoa_check_launch(h);
     if (rc) return rc;
     switch (h->scan_tiles_per_cta) {
         case 2:
-            k_compact<2><<<(unsigned)((h->tiles + 1) / 2), 128, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_off, h->R, h->Rocc);
+            k_compact<2><<<(unsigned)((h->tiles + 1) / 2), 128, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_off, h->R[type], h->Rocc[type]);
             break;
         default:
-            k_compact<1><<<(unsigned)h->tiles, 64, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_off, h->R, h->Rocc);
+            k_compact<1><<<(unsigned)h->tiles, 64, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_off, h->R[type], h->Rocc[type]);
             break;
     }
     rc = dsoa_check_launch(h);
-    if (rc == DSOA_OK) h->enumerated_type = type;
+    if (rc == DSOA_OK) h->enumerated[type] = true;
     return rc;
 }
 
 int dsoa_prepare_doall(dsoa_heap* h, int type) {
-    if (h->skip_enumeration) return h->enumerated_type == type ? DSOA_OK : DSOA_ERR_INVALID_ARG;
+    if (h->skip_enumeration) return h->enumerated[type] ? DSOA_OK : DSOA_ERR_INVALID_ARG;
     return dsoa_enumerate_internal(h, type);
 }
 
@@ -398,14 +429,15 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     uint32_t block_bytes = 128;
     for (int t = 0; t < h->ntypes; ++t) block_bytes = std::max(block_bytes, h->types[t].data_bytes);
     const int nbm = 1 + 2 * h->ntypes;
+    (void)nbm;
     // largest M whose layout fits in the byte budget
     uint64_t lo = 0, hi = h->bytes / block_bytes + 1;
     Layout L;
     while (lo + 1 < hi) {
         const uint64_t mid = lo + (hi - lo) / 2;
-        if (make_layout(mid, block_bytes, nbm, &L) && L.total <= h->bytes) lo = mid; else hi = mid;
+        if (make_layout(mid, block_bytes, h->ntypes, &L) && L.total <= h->bytes) lo = mid; else hi = mid;
     }
-    if (lo == 0 || lo > (1ull << 32) - 1 || !make_layout(lo, block_bytes, nbm, &L)) return DSOA_ERR_OOM;
+    if (lo == 0 || lo > (1ull << 32) - 1 || !make_layout(lo, block_bytes, h->ntypes, &L)) return DSOA_ERR_OOM;
     char* base = (char*)h->base;
     dsoa_ctx& c = h->ctx;
     std::memset(&c, 0, sizeof(c));
@@ -415,9 +447,10 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     c.bm = (unsigned long long*)(base + L.off_bm);
     uint64_t* small = (uint64_t*)(base + L.off_small);
     c.err = (int*)(small + 0);
-    h->r_dev = (uint32_t*)(small + 1);
-    h->done = (uint32_t*)(small + 2);
-    h->scratch64 = (unsigned long long*)(small + 16);
+    c.hint = (uint32_t*)(base + L.off_hint);
+    c.grid_scratch = (uint32_t*)(base + L.off_grid);
+    h->done = (uint32_t*)(small + 1);
+    h->scratch64 = (unsigned long long*)(small + 32);
     c.M = L.M;
     c.bm_stride = L.bm_stride;
     for (int l = 0; l < DSOA_MAX_LEVELS; ++l) { c.lvl_off[l] = L.lvl_off[l]; c.lvl_words[l] = L.lvl_words[l]; }
@@ -427,8 +460,12 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     for (int t = 0; t < h->ntypes; ++t)
         for (int f = 0; f < h->types[t].nfields; ++f) c.col_off[t][f] = (uint16_t)h->types[t].col_off[f];
     h->tiles = L.tiles;
-    h->R = (uint32_t*)(base + L.off_R);
-    h->Rocc = (unsigned long long*)(base + L.off_Rocc);
+    for (int t = 0; t < h->ntypes; ++t) {
+        h->R[t] = (uint32_t*)(base + L.off_R) + (uint64_t)t * L.M;
+        h->Rocc[t] = (unsigned long long*)(base + L.off_Rocc) + (uint64_t)t * L.M;
+        h->r_dev[t] = (uint32_t*)(small + 8 + t);
+        h->enumerated[t] = false;
+    }
     h->tile_cnt = (uint32_t*)(base + L.off_tcnt);
     h->tile_off = (uint32_t*)(base + L.off_toff);
     h->meta_bytes = L.total - L.M * block_bytes;
@@ -436,8 +473,10 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     DSOA_CUDA_TRY(cudaMemsetAsync(c.btype, 0xFF, L.M * 4, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(c.bm, 0, (uint64_t)nbm * L.bm_stride * 8, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(small, 0, kSmallWords * 8, h->stream));
-    DSOA_CUDA_TRY(cudaMemsetAsync(h->R, 0, L.M * 4, h->stream));
-    DSOA_CUDA_TRY(cudaMemsetAsync(h->Rocc, 0, L.M * 8, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(c.hint, 0xFF, (uint64_t)DSOA_HINT_SLOTS * (uint64_t)h->ntypes * 4, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(c.grid_scratch, 0, (uint64_t)DSOA_GRID_SCRATCH * 4, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(h->R[0], 0, L.M * 4 * (uint64_t)h->ntypes, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(h->Rocc[0], 0, L.M * 8 * (uint64_t)h->ntypes, h->stream));
     k_init_free<<<std::max(1, h->num_sms * 4), 256, 0, h->stream>>>(c);
     int rc = dsoa_check_launch(h);
     if (rc) return rc;
@@ -501,13 +540,22 @@ int dsoa_run_kernel(dsoa_heap* h, int kernel_id, uint64_t n, const void* args, s
     return DSOA_ERR_UNKNOWN_METHOD;
 }
 
+int dsoa_delete_handles(dsoa_heap* h, const dsoa_obj* handles_dev, uint64_t n) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (n == 0) return DSOA_OK;
+    if (!handles_dev) return DSOA_ERR_INVALID_ARG;
+    k_delete_handles<<<dsoa_new_grid(h, n, 256), 256, 0, h->stream>>>(dsoa_launch_ctx(h), handles_dev, n);
+    return dsoa_check_launch(h);
+}
+
 int dsoa_enumerate(dsoa_heap* h, int type, const uint32_t** R_dev, const uint64_t** occ_dev,
                    const uint32_t** r_dev) {
     int rc = dsoa_enumerate_internal(h, type);
     if (rc) return rc;
-    if (R_dev) *R_dev = h->R;
-    if (occ_dev) *occ_dev = (const uint64_t*)h->Rocc;
-    if (r_dev) *r_dev = h->r_dev;
+    if (R_dev) *R_dev = h->R[type];
+    if (occ_dev) *occ_dev = (const uint64_t*)h->Rocc[type];
+    if (r_dev) *r_dev = h->r_dev[type];
     return DSOA_OK;
 }
 
@@ -655,8 +703,9 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
 }
 
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags) {
-    if (!h) return DSOA_ERR_INVALID_ARG;
-    h->ctx.flags = flags;
+    if (!h || (flags & ~(DSOA_FLAG_NO_COALESCE | DSOA_FLAG_NO_ROTATE | DSOA_FLAG_NO_HINT | DSOA_FLAG_UNFUSED)))
+        return DSOA_ERR_INVALID_ARG;
+    h->flags = flags;
     return DSOA_OK;
 }
 

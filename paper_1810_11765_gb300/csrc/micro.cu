@@ -47,6 +47,14 @@ struct MicroDeleteAll {
     }
 };
 
+struct MicroHandles {
+    using Args = dsoa_micro_args;
+    static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
+        const uint32_t id = (uint32_t)dsoa_column<int32_t>(c, t, bid, 0)[s];
+        if (id < a.n_ids) a.handles_out[id] = dsoa_make_handle(t, bid, s);
+    }
+};
+
 struct MicroGather {
     using Args = dsoa_micro_args;
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
@@ -113,6 +121,133 @@ __global__ void __launch_bounds__(512) k_micro_scale_vec(dsoa_ctx c, uint32_t t,
                     if ((nib[u] >> k) & 1u) d[k] = xp[k];
             }
         }
+    }
+}
+
+// ---- bulk-copy staged do-all (Blackwell async copy engine) ----------------
+// The id and x columns of CH consecutive blocks of R (2 x 256 B each) are
+// copied into shared memory by cp.async.bulk, S chunks ahead, completing on a
+// per-stage mbarrier by transaction bytes; 128 threads then update 4 slots
+// each and store x straight to global (16-byte stores; per-slot stores where
+// the snapshot has holes).  Bytes in flight per SM are bounded by shared
+// memory (S x CH x 512 B per CTA), not by registers.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+constexpr uint32_t kBulkWaitLimit = 1u << 26;   // try_wait polls before giving up (error)
+
+template <int CH, int S>
+__global__ void __launch_bounds__(128) k_micro_scale_bulk(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+                                                         const unsigned long long* __restrict__ occ,
+                                                         const uint32_t* __restrict__ r_dev) {
+    __shared__ __align__(128) int32_t s_id[S][CH][64];
+    __shared__ __align__(128) float s_x[S][CH][64];
+    __shared__ __align__(8) uint64_t bar[S];
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t r = *r_dev;
+    const uint32_t nchunks = (r + CH - 1) / CH;
+    const uint32_t off_id = c.col_off[t][0], off_x = c.col_off[t][1];
+    if (tid == 0) {
+        for (int k = 0; k < S; ++k) mbar_init(&bar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // producer: warp 0, lane i copies block i of the chunk
+    auto issue = [&](uint32_t chunk, int stage) {
+        const uint32_t first = chunk * CH;
+        const uint32_t nb = min((uint32_t)CH, r - first);
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive_tx(&bar[stage], nb * 512u);
+        }
+        __syncwarp();
+        if (lane < nb) {
+            const char* blk = c.data + (uint64_t)__ldg(&R[first + lane]) * c.block_bytes;
+            bulk_g2s(&s_id[stage][lane][0], blk + off_id, 256u, &bar[stage]);
+            bulk_g2s(&s_x[stage][lane][0], blk + off_x, 256u, &bar[stage]);
+        }
+    };
+    __shared__ uint32_t s_abort;
+    if (tid == 0) s_abort = 0u;
+    __syncthreads();
+    uint32_t j = 0;
+    if (warp == 0)
+        for (int k = 0; k < S; ++k) {
+            const uint32_t ch = blockIdx.x + (uint32_t)k * gridDim.x;
+            if (ch < nchunks) issue(ch, k);
+        }
+    for (uint32_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++j) {
+        const int stage = (int)(j % S);
+        const uint32_t parity = (j / S) & 1u;
+        bool ready = true;
+        for (uint32_t polls = 0; !mbar_try_wait(&bar[stage], parity);) {
+            if (++polls >= kBulkWaitLimit) { ready = false; break; }
+        }
+        if (!ready) {
+            atomicOr(&s_abort, 1u);
+        } else {
+            const uint32_t first = ch * CH;
+            const uint32_t bi = tid >> 4, q = tid & 15u;       // block in chunk, slot quad
+            if (first + bi < r) {
+                const uint32_t nib = (uint32_t)(__ldg(&occ[first + bi]) >> (q * 4)) & 0xFu;
+                if (nib) {
+                    const int4 id4 = *reinterpret_cast<const int4*>(&s_id[stage][bi][q * 4]);
+                    float4 x4 = *reinterpret_cast<const float4*>(&s_x[stage][bi][q * 4]);
+                    x4.x = micro_update(x4.x, id4.x);
+                    x4.y = micro_update(x4.y, id4.y);
+                    x4.z = micro_update(x4.z, id4.z);
+                    x4.w = micro_update(x4.w, id4.w);
+                    float* dst = reinterpret_cast<float*>(c.data + (uint64_t)__ldg(&R[first + bi]) * c.block_bytes +
+                                                          off_x) + q * 4;
+                    if (nib == 0xFu) {
+                        __stcs(reinterpret_cast<float4*>(dst), x4);
+                    } else {
+                        if (nib & 1u) dst[0] = x4.x;
+                        if (nib & 2u) dst[1] = x4.y;
+                        if (nib & 4u) dst[2] = x4.z;
+                        if (nib & 8u) dst[3] = x4.w;
+                    }
+                }
+            }
+        }
+        __syncthreads();                                   // stage consumed by every thread
+        if (s_abort) {
+            // A copy did not land within the bound: report, then give the copies
+            // still in flight into this CTA's shared memory a bounded time to land
+            // before the CTA exits.  Uniform exit: every thread saw s_abort.
+            if (tid == 0) {
+                dsoa_raise(c, DSOA_DEV_SPIN);
+                for (uint32_t k = 1; k <= (uint32_t)S; ++k) {
+                    const uint32_t jj = j + k - 1;          // uses issued but not consumed
+                    const uint32_t chk = blockIdx.x + jj * gridDim.x;
+                    if (chk >= nchunks) break;
+                    for (uint32_t polls = 0; polls < kBulkWaitLimit; ++polls)
+                        if (mbar_try_wait(&bar[jj % S], (jj / S) & 1u)) break;
+                }
+            }
+            return;
+        }
+        const uint32_t next = ch + (uint32_t)S * gridDim.x;
+        if (warp == 0 && next < nchunks) issue(next, stage);
     }
 }
 
@@ -186,18 +321,28 @@ int dsoa_micro_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
             rc = dsoa_prepare_doall(h, type);
             if (rc) return rc;
             const dsoa_ctx c = dsoa_launch_ctx(h);
-            const unsigned g = dsoa_doall_grid(h);
             const int tpb = h->doall_tpb;
-            switch (h->vec_slots_per_thread) {
-                case 1: k_micro_scale_vec<1, 4><<<g, tpb, 0, h->stream>>>(c, type, h->R, h->Rocc, h->r_dev); break;
-                case 2: k_micro_scale_vec<2, 2><<<g, tpb, 0, h->stream>>>(c, type, h->R, h->Rocc, h->r_dev); break;
-                default: k_micro_scale_vec<4, 2><<<g, tpb, 0, h->stream>>>(c, type, h->R, h->Rocc, h->r_dev); break;
-            }
+            auto* k = &k_micro_scale_vec<4, 2>;
+            if (h->vec_slots_per_thread == 1) k = &k_micro_scale_vec<1, 4>;
+            if (h->vec_slots_per_thread == 2) k = &k_micro_scale_vec<2, 2>;
+            k<<<dsoa_persistent_grid(h, k, tpb), tpb, 0, h->stream>>>(c, type, h->R[type], h->Rocc[type],
+                                                                     h->r_dev[type]);
+            return dsoa_check_launch(h);
+        }
+        case DSOA_M_MICRO_SCALE_TMA: {
+            rc = dsoa_prepare_doall(h, type);
+            if (rc) return rc;
+            auto* k = &k_micro_scale_bulk<8, 4>;
+            k<<<dsoa_persistent_grid(h, k, 128), 128, 0, h->stream>>>(dsoa_launch_ctx(h), type, h->R[type],
+                                                                    h->Rocc[type], h->r_dev[type]);
             return dsoa_check_launch(h);
         }
         case DSOA_M_MICRO_SCALE_SCALAR: return dsoa_run_doall<MicroScale>(h, type, args);
         case DSOA_M_MICRO_DELETE: return dsoa_run_doall<MicroDelete>(h, type, args);
         case DSOA_M_MICRO_DELETE_ALL: return dsoa_run_doall<MicroDeleteAll>(h, type, args);
+        case DSOA_M_MICRO_HANDLES:
+            if (!args.handles_out) return DSOA_ERR_INVALID_ARG;
+            return dsoa_run_doall<MicroHandles>(h, type, args);
         case DSOA_M_MICRO_GATHER:
             if (!args.x_out || !args.live_out) return DSOA_ERR_INVALID_ARG;
             return dsoa_run_doall<MicroGather>(h, type, args);
@@ -205,7 +350,8 @@ int dsoa_micro_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
             if (!args.stats) return DSOA_ERR_INVALID_ARG;
             rc = dsoa_prepare_doall(h, type);
             if (rc) return rc;
-            k_micro_stats<<<dsoa_doall_grid(h), 256, 0, h->stream>>>(h->ctx, type, h->R, h->Rocc, h->r_dev,
+            k_micro_stats<<<dsoa_persistent_grid(h, &k_micro_stats, 256), 256, 0, h->stream>>>(
+                h->ctx, type, h->R[type], h->Rocc[type], h->r_dev[type],
                                                                    (dsoa_micro_stats*)args.stats);
             return dsoa_check_launch(h);
         }

@@ -21,13 +21,14 @@ ERRORS = {-1: "invalid argument", -2: "heap layout already frozen", -3: "too man
           -9: "heap larger than the fixed no-allocation scratch allows"}
 
 DEV_OOM, DEV_SPIN, DEV_DOUBLE_FREE, DEV_BAD_HANDLE = 1, 2, 4, 8
-FLAG_NO_COALESCE, FLAG_NO_ROTATE = 1, 2
+FLAG_NO_COALESCE, FLAG_NO_ROTATE, FLAG_NO_HINT, FLAG_UNFUSED = 1, 2, 4, 8
 CHECK_NAMES = ["hier", "free_xor", "multi_type", "active_subset", "type", "free_word",
                "empty_alloc", "active_exact", "tail_bits"]
 
 # built-in ids (dsoa_apps.h)
 C_MICRO, M_MICRO_SCALE, M_MICRO_SCALE_SCALAR, M_MICRO_DELETE = 100, 101, 102, 103
 M_MICRO_GATHER, M_MICRO_STATS, M_MICRO_SCALE_TMA, M_MICRO_DELETE_ALL = 104, 105, 106, 107
+M_MICRO_HANDLES = 108
 C_GOL_CELL, M_GOL_SPREAD, M_GOL_REAP, M_GOL_DECIDE, M_GOL_READ, M_GOL_KILL = 200, 201, 202, 203, 204, 205
 K_GOL_ADVANCE = 250
 M_WATOR_FISH_CHOOSE, M_WATOR_FISH_MOVE, M_WATOR_SHARK_CHOOSE, M_WATOR_SHARK_MOVE = 301, 302, 303, 304
@@ -43,7 +44,8 @@ u8p = ctypes.c_void_p
 
 class MicroArgs(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("id_base", ctypes.c_uint32), ("round", ctypes.c_uint32),
-                ("x_out", P), ("live_out", P), ("n_ids", ctypes.c_uint64), ("stats", P)]
+                ("x_out", P), ("live_out", P), ("n_ids", ctypes.c_uint64), ("stats", P),
+                ("handles_out", P)]
 
 
 class MicroStats(ctypes.Structure):
@@ -78,7 +80,7 @@ class TrafficArgs(ctypes.Structure):
 ABI_FUNCTIONS = [
     "dsoa_heap_create", "dsoa_heap_create_from", "dsoa_register_type", "dsoa_heap_freeze",
     "dsoa_heap_info", "dsoa_field_offset", "dsoa_parallel_new", "dsoa_parallel_do",
-    "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_enumerate", "dsoa_count", "dsoa_count_async",
+    "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_delete_handles", "dsoa_enumerate", "dsoa_count", "dsoa_count_async",
     "dsoa_free_blocks_async", "dsoa_get_error", "dsoa_check", "dsoa_export_state",
     "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
     "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_launch_count",
@@ -109,6 +111,7 @@ def load(path: str | None = None):
         "dsoa_parallel_new": [vp, i32, u64, i32, vp, sz], "dsoa_parallel_do": [vp, i32, i32, vp, sz],
         "dsoa_parallel_do_enumerated": [vp, i32, i32, vp, sz],
         "dsoa_run_kernel": [vp, i32, u64, vp, sz], "dsoa_enumerate": [vp, i32, vp, vp, vp],
+        "dsoa_delete_handles": [vp, vp, u64],
         "dsoa_count": [vp, i32, vp], "dsoa_count_async": [vp, i32, vp],
         "dsoa_free_blocks_async": [vp, vp], "dsoa_get_error": [vp, vp], "dsoa_check": [vp, vp],
         "dsoa_export_state": [vp, vp, sz, vp, vp], "dsoa_get_ctx": [vp, vp, sz],
@@ -234,6 +237,9 @@ class Heap:
     def run_kernel(self, kernel: int, n: int, args):
         _ok(load().dsoa_run_kernel(self._h, kernel, n, ctypes.byref(args), ctypes.sizeof(args)),
             "dsoa_run_kernel")
+
+    def delete_handles(self, handles_dev, n: int):
+        _ok(load().dsoa_delete_handles(self._h, _addr(handles_dev), n), "dsoa_delete_handles")
 
     def enumerate(self, t: int):
         R, occ, r = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()

@@ -1,0 +1,105 @@
+"""Small, bounded workloads for kernel profiling (ncu) and quick timing.
+
+  python -m paper_1810_11765_gb300.profile_cases doall --log2n 24 [--holes] [--iters 3]
+  python -m paper_1810_11765_gb300.profile_cases wator --side 1024 --steps 3
+  python -m paper_1810_11765_gb300.profile_cases alloc --log2n 22
+
+Each case prints CUDA-event timings of its kernels (without a profiler attached
+these are the numbers to trust) and keeps its device footprint to a few hundred MB
+so that a multi-pass ncu capture stays small.
+"""
+from __future__ import annotations
+
+import argparse
+import statistics
+
+import torch
+
+from . import build, dsoa as D
+from .apps import Micro, WatorWorld
+
+
+def _ev():
+    return torch.cuda.Event(enable_timing=True)
+
+
+METHODS = {"vec": D.M_MICRO_SCALE, "bulk": D.M_MICRO_SCALE_TMA, "scalar": D.M_MICRO_SCALE_SCALAR}
+
+
+def case_doall(log2n: int, holes: bool, iters: int, method: str = "vec"):
+    n = 1 << log2n
+    m = Micro(int(n * 16 * 1.3) + (64 << 20), 0x5EED0001, n)
+    m.new(0)
+    if holes:
+        m.delete(0)
+    live = m.heap.count(m.type)
+    m.heap.enumerate(m.type)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    times = []
+    for _ in range(iters):
+        flush.zero_()
+        a, b = _ev(), _ev()
+        a.record()
+        m.heap.parallel_do_enumerated(m.type, METHODS[method], m.args())
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = statistics.median(times)
+    print(f"doall[{method}] 2^{log2n}{' holes' if holes else ''}: {live} objects, {ms:.4f} ms, "
+          f"{live * 12 / ms / 1e6:.1f} GB/s algorithmic, err={m.heap.get_error()}")
+    m.heap.close()
+
+
+def case_wator(side: int, steps: int):
+    heap = D.Heap(512 << 20)
+    w = WatorWorld(heap)
+    heap.freeze()
+    w.add(side, side, 0x5EED0003)
+    for _ in range(steps):
+        a, b = _ev(), _ev()
+        a.record()
+        w.step()
+        b.record()
+        b.synchronize()
+        print(f"wator {side}^2 step: {a.elapsed_time(b):.4f} ms  populations {w.counts()}")
+    print("err", heap.get_error())
+    heap.close()
+
+
+def case_alloc(log2n: int):
+    n = 1 << log2n
+    m = Micro(int(n * 16 * 2.2) + (64 << 20), 0x5EED0001, n)
+    for it in range(3):
+        a, b, c = _ev(), _ev(), _ev()
+        a.record()
+        m.new(0)
+        b.record()
+        m.heap.parallel_do(m.type, D.M_MICRO_DELETE_ALL, m.args())
+        c.record()
+        c.synchronize()
+        print(f"alloc 2^{log2n}: new {a.elapsed_time(b):.3f} ms, delete-all {b.elapsed_time(c):.3f} ms")
+    print("err", m.heap.get_error(), "left", m.heap.count(m.type))
+    m.heap.close()
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("case", choices=["doall", "wator", "alloc"])
+    p.add_argument("--log2n", type=int, default=24)
+    p.add_argument("--holes", action="store_true")
+    p.add_argument("--iters", type=int, default=3)
+    p.add_argument("--method", default="vec", choices=sorted(METHODS))
+    p.add_argument("--side", type=int, default=1024)
+    p.add_argument("--steps", type=int, default=3)
+    a = p.parse_args()
+    build.build()
+    if a.case == "doall":
+        case_doall(a.log2n, a.holes, a.iters, a.method)
+    elif a.case == "wator":
+        case_wator(a.side, a.steps)
+    else:
+        case_alloc(a.log2n)
+
+
+if __name__ == "__main__":
+    main()

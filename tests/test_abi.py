@@ -69,6 +69,7 @@ PROBE = r"""
 #define O(T, f) printf(#T " " #f " %zu\n", offsetof(T, f));
 int main(void) {
   S(dsoa_micro_args) O(dsoa_micro_args, round) O(dsoa_micro_args, x_out) O(dsoa_micro_args, stats)
+  O(dsoa_micro_args, handles_out)
   S(dsoa_micro_stats) O(dsoa_micro_stats, sum_x)
   S(dsoa_inst) O(dsoa_inst, seed) O(dsoa_inst, t) O(dsoa_inst, state)
   S(dsoa_gol_args) O(dsoa_gol_args, n_inst) O(dsoa_gol_args, alive_type)

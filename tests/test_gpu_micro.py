@@ -84,14 +84,15 @@ def test_ragged_sizes(n):
     assert np.array_equal(x[live_ref.astype(bool)], x_ref[live_ref.astype(bool)])
 
 
-@pytest.mark.parametrize("method", ["scalar", "spt1", "spt2", "spt4"])
+@pytest.mark.parametrize("method", ["scalar", "scalar_g2", "spt1", "spt2", "spt4", "bulk"])
 def test_scale_variants_agree(method):
     from paper_1810_11765_gb300 import dsoa as D
     n, rounds = 50000, 4
     ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
-    spt = {"scalar": 4, "spt1": 1, "spt2": 2, "spt4": 4}[method]
+    spt = {"scalar": 1, "scalar_g2": 2, "spt1": 1, "spt2": 2, "spt4": 4, "bulk": 4}[method]
     m = make(heap_bytes=16 << 20, n=n, slots_per_thread=spt)
-    meth = D.M_MICRO_SCALE_SCALAR if method == "scalar" else D.M_MICRO_SCALE
+    meth = {"scalar": D.M_MICRO_SCALE_SCALAR, "scalar_g2": D.M_MICRO_SCALE_SCALAR,
+            "bulk": D.M_MICRO_SCALE_TMA}.get(method, D.M_MICRO_SCALE)
     for r in range(rounds):
         m.round(r, method=meth)
     x, live = m.gather(n * rounds)
@@ -100,7 +101,7 @@ def test_scale_variants_agree(method):
     assert_clean(m)
 
 
-@pytest.mark.parametrize("flags", [1, 2, 3])
+@pytest.mark.parametrize("flags", [1, 2, 3, 4, 7])
 def test_ablations_keep_semantics(flags):
     """NoCoal / NoShift / both (Sec. 6.4) change placement, not results.  Without
     coalescing every thread of a burst on an empty heap may take a block of its own
@@ -200,3 +201,41 @@ def test_graph_capture_replays_rounds():
         x, live = m.gather(n * rounds)
     assert np.array_equal(live, live_ref)
     assert np.array_equal(x[live_ref.astype(bool)], x_ref[live_ref.astype(bool)])
+
+
+def test_delete_handles_matches_parity_delete():
+    """Freeing a host-chosen list of handles (the odd-parity ids of round 0) in one
+    kernel gives the same objects as the parity delete do-all."""
+    import torch
+    n = 30000
+    ref, x_ref, live_ref = oracle.micro_run(SEED, n, 1, per_object=True)
+    m = make(heap_bytes=16 << 20, n=n)
+    m.new(0)
+    m.scale()
+    hs = m.handles(n)
+    kill = torch.from_numpy((live_ref == 0).astype(np.bool_)).cuda()
+    m.heap.delete_handles(hs[kill].contiguous(), int(kill.sum()))
+    compare_round(m.stats(), ref[0])
+    x, live = m.gather(n)
+    assert np.array_equal(live, live_ref)
+    assert_clean(m)
+
+
+def test_double_free_and_bad_handles_are_reported_not_fatal():
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    n = 5000
+    m = make(heap_bytes=8 << 20, n=n)
+    m.new(0)
+    hs = m.handles(n)
+    first = hs[1:2000:2].contiguous()                   # odd ids: no block becomes empty
+    m.heap.delete_handles(first, 1000)
+    assert m.heap.get_error() == 0
+    m.heap.delete_handles(first, 1000)                  # second free of the same slots
+    assert m.heap.get_error() & D.DEV_DOUBLE_FREE
+    M = m.heap.info()["num_blocks"]
+    bad = torch.tensor([(200 << 56) | 5, (1 << 56) | ((M + 7) << 6), 0], dtype=torch.int64, device="cuda")
+    m.heap.delete_handles(bad, 3)                       # unknown type, block past M, null
+    assert m.heap.get_error() == D.DEV_BAD_HANDLE
+    assert m.heap.count(m.type) == n - 1000
+    assert_clean(m)
