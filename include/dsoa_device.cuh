@@ -248,7 +248,7 @@ __device__ inline int64_t dsoa_bm_find(const dsoa_ctx& c, uint32_t b, uint32_t h
 /* clear() = find-and-clear an arbitrary set bit (Sec. 4.1.2).  -1 when the
  * bitmap is empty at the top (OOM for the free-block bitmap), -2 when
  * DSOA_TAKE_ATTEMPTS attempts lost every race (the caller retries). */
-__device__ __noinline__ int64_t dsoa_bm_take(const dsoa_ctx& c, uint32_t b, uint32_t h) {
+static __device__ __noinline__ int64_t dsoa_bm_take(const dsoa_ctx& c, uint32_t b, uint32_t h) {
     for (uint32_t a = 0; a < DSOA_TAKE_ATTEMPTS; ++a) {
         const int64_t pos = dsoa_bm_find(c, b, dsoa_hash(h + a * 0x9E3779B9u));
         if (pos >= 0) {
@@ -279,7 +279,7 @@ __device__ inline void dsoa_block_init(const dsoa_ctx& c, uint64_t bid, uint32_t
  * thread freed a slot meanwhile it saw a "first free" and will set the active
  * bit, so the deferred deactivation is done here; retry if the block is empty
  * again. */
-__device__ __noinline__ void dsoa_block_invalidate(const dsoa_ctx& c, uint64_t bid) {
+static __device__ __noinline__ void dsoa_block_invalidate(const dsoa_ctx& c, uint64_t bid) {
     for (uint32_t it = 0; it < DSOA_SPIN_LIMIT; ++it) {
         const unsigned long long before = atomicAnd(&c.slot[bid], 0ull);
         if (before == DSOA_ALL) {
@@ -302,10 +302,10 @@ __device__ __noinline__ void dsoa_block_invalidate(const dsoa_ctx& c, uint64_t b
 
 /* Rare transitions of a block, kept out of line so that the hot paths of
  * allocation and deallocation stay small in registers. */
-__device__ __noinline__ void dsoa_block_first_free(const dsoa_ctx& c, uint32_t t, uint64_t bid) {
+static __device__ __noinline__ void dsoa_block_first_free(const dsoa_ctx& c, uint32_t t, uint64_t bid) {
     dsoa_bm_set(c, dsoa_bm_active(t), bid);                 /* was full: active again */
 }
-__device__ __noinline__ void dsoa_block_deactivate(const dsoa_ctx& c, uint32_t t, uint64_t bid) {
+static __device__ __noinline__ void dsoa_block_deactivate(const dsoa_ctx& c, uint32_t t, uint64_t bid) {
     dsoa_bm_clear(c, dsoa_bm_active(t), bid, true);         /* now full: inactive */
 }
 
@@ -326,7 +326,7 @@ __device__ __forceinline__ void dsoa_block_release(const dsoa_ctx& c, uint32_t t
 /* Slow path of Alg. 1 (lines 3-6): take a free block, initialise it for type
  * t, enter it into allocated[t] and active[t].  -1 = no free block, -2 = every
  * attempt lost its race. */
-__device__ __noinline__ int64_t dsoa_block_new(const dsoa_ctx& c, uint32_t t, uint32_t h) {
+static __device__ __noinline__ int64_t dsoa_block_new(const dsoa_ctx& c, uint32_t t, uint32_t h) {
     const int64_t bid = dsoa_bm_take(c, dsoa_bm_free(), h);
     if (bid < 0) return bid;
     dsoa_block_init(c, (uint64_t)bid, t);
@@ -336,7 +336,7 @@ __device__ __noinline__ int64_t dsoa_block_new(const dsoa_ctx& c, uint32_t t, ui
 }
 
 /* Roll back slots reserved in a block whose type changed (Alg. 1, line 14). */
-__device__ __noinline__ void dsoa_rollback(const dsoa_ctx& c, uint32_t bt, uint64_t bid, unsigned long long got) {
+static __device__ __noinline__ void dsoa_rollback(const dsoa_ctx& c, uint32_t bt, uint64_t bid, unsigned long long got) {
     dsoa_block_release(c, bt, bid, got);
 }
 
