@@ -101,7 +101,7 @@ def test_scale_variants_agree(method):
     assert_clean(m)
 
 
-@pytest.mark.parametrize("flags", [1, 2, 3, 4, 7])
+@pytest.mark.parametrize("flags", [1, 2, 3, 4, 7, 8, 15])
 def test_ablations_keep_semantics(flags):
     """NoCoal / NoShift / both (Sec. 6.4) change placement, not results.  Without
     coalescing every thread of a burst on an empty heap may take a block of its own

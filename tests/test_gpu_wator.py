@@ -80,8 +80,9 @@ def test_batched_instances_match_alone():
     assert heap.get_error() == 0
 
 
-@pytest.mark.parametrize("launch", [dict(), dict(tpb=128, ctas_per_sm=4, slots_per_thread=2, scan_tiles=2)])
-def test_graph_captured_steps_match_oracle(launch):
+@pytest.mark.parametrize("launch,flags", [(dict(), 0), (dict(tpb=128, ctas_per_sm=4, slots_per_thread=2, scan_tiles=2), 0),
+                                          (dict(), 8), (dict(tpb=512, ctas_per_sm=1), 4)])
+def test_graph_captured_steps_match_oracle(launch, flags):
     """One step captured as a CUDA graph and replayed: the step index lives in
     device memory, so replays advance the simulation exactly like plain steps."""
     import torch
@@ -91,6 +92,7 @@ def test_graph_captured_steps_match_oracle(launch):
         heap, w = world(32 << 20)
         if launch:
             heap.set_launch(**launch)
+        heap.set_flags(flags)
         slot = w.add(W, H, seed)
         heap.graph_begin()
         w.step()
