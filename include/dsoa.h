@@ -191,6 +191,16 @@ int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
  * not in the paper).  Takes effect for launches issued after the call. */
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags);
 
+/* r of Sec. 4.2 / Fig. 11: attempts to find an active block (try_find_set on
+ * the active bitmap) before an allocation initialises a new block; 1..64,
+ * default 5.  Takes effect for launches issued after the call. */
+int dsoa_set_lookups(dsoa_heap* h, int r);
+
+/* Blocks of `type` (popcount of its allocated-block bitmap) and its live
+ * objects, to out_host[0] and out_host[1]; fragmentation of Sec. 6.4 is
+ * F = 1 - out[1] / (64 * out[0]).  Synchronous. */
+int dsoa_type_stats(dsoa_heap* h, int type, uint64_t* out_host);
+
 /* Number of kernels this heap has launched so far (host-side counter). */
 int dsoa_launch_count(dsoa_heap* h, uint64_t* out_host);
 

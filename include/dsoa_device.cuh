@@ -76,6 +76,8 @@ struct dsoa_ctx {
     uint32_t ntypes;
     uint32_t seed;                       /* rotation seed of this launch           */
     uint32_t flags;                      /* DSOA_FLAG_*                            */
+    uint32_t lookups;                    /* active-block lookups before the slow path
+                                            (r of Sec. 4.2 / Fig. 11), >= 1           */
     uint16_t col_off[DSOA_MAX_TYPES][DSOA_MAX_FIELDS];
 };
 
@@ -126,6 +128,14 @@ __device__ __forceinline__ void dsoa_st32(uint32_t* p, uint32_t v) {
 __device__ __forceinline__ unsigned long long dsoa_and_acquire(unsigned long long* p, unsigned long long m) {
     unsigned long long old;
     asm volatile("atom.acquire.gpu.global.and.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(m) : "memory");
+    return old;
+}
+/* atomicOr with release semantics at device scope: stores before it (the
+ * freed object's last field writes) are visible before the freed slot can be
+ * observed -- and reserved -- by another thread. */
+__device__ __forceinline__ unsigned long long dsoa_or_release(unsigned long long* p, unsigned long long m) {
+    unsigned long long old;
+    asm volatile("atom.release.gpu.global.or.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(m) : "memory");
     return old;
 }
 __device__ __forceinline__ uint32_t dsoa_lane() {
@@ -313,7 +323,7 @@ static __device__ __noinline__ void dsoa_block_deactivate(const dsoa_ctx& c, uin
  * request coalescing and by rollback).  `t` is the block's type. */
 __device__ __forceinline__ void dsoa_block_release(const dsoa_ctx& c, uint32_t t, uint64_t bid,
                                                    unsigned long long bits) {
-    const unsigned long long before = atomicOr(&c.slot[bid], bits);
+    const unsigned long long before = dsoa_or_release(&c.slot[bid], bits);
     if (before & bits) {
         dsoa_raise(c, DSOA_DEV_DOUBLE_FREE);
         bits &= ~before;
@@ -367,7 +377,7 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
             const uint32_t hb = *hp;
             if (hb < c.M) bid = hb;
         }
-        for (uint32_t a = 0; a < DSOA_LOOKUP_ATTEMPTS && bid < 0; ++a)
+        for (uint32_t a = 0; a < c.lookups && bid < 0; ++a)
             bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
         if (bid < 0) {
             bid = dsoa_block_new(c, t, h ^ round);
@@ -438,6 +448,11 @@ __device__ inline dsoa_obj dsoa_new(const dsoa_ctx& c, uint32_t t) {
             out = dsoa_make_handle(t, bid, dsoa_nth_set(got, rank - served));
         served += k;
     }
+    /* Memory ordering across the group: the leader's acquire reservation
+     * happens-before every lane's constructor stores into its new slot, so a
+     * slot freed by another thread (release) cannot receive its old owner's
+     * late stores after the new owner's. */
+    __syncwarp(peers);
     return out;
 }
 
@@ -453,6 +468,9 @@ __device__ inline void dsoa_delete(const dsoa_ctx& c, dsoa_obj h) {
     const unsigned long long bit = ok ? (1ull << dsoa_h_slot(h)) : 0ull;
     const uint32_t lo = __reduce_or_sync(peers, (uint32_t)bit);
     const uint32_t hi = __reduce_or_sync(peers, (uint32_t)(bit >> 32));
+    /* every lane's last stores to its object happen-before the leader's
+     * release of the slots (dsoa_block_release) */
+    __syncwarp(peers);
     if (ok && lane == (uint32_t)__ffs((int)peers) - 1u)
         dsoa_block_release(c, dsoa_h_type(h), dsoa_h_block(h), ((unsigned long long)hi << 32) | lo);
 }

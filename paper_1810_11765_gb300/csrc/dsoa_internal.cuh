@@ -55,6 +55,7 @@ struct dsoa_heap {
     int scan_tiles_per_cta = 1;
 
     uint32_t flags = 0;              // DSOA_FLAG_* applied to every launch
+    uint32_t lookups = DSOA_LOOKUP_ATTEMPTS;  // r: active-block lookups before the slow path
     uint32_t launch_seq = 0;
     uint64_t launches = 0;
     bool enumerated[DSOA_MAX_TYPES] = {false};  // R[t] holds an enumeration of type t

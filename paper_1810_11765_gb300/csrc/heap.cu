@@ -305,6 +305,7 @@ dsoa_ctx dsoa_launch_ctx(dsoa_heap* h) {
     dsoa_ctx c = h->ctx;
     c.seed = 0x9E3779B9u * (++h->launch_seq);
     c.flags = h->flags;
+    c.lookups = h->lookups;
     return c;
 }
 
@@ -706,6 +707,31 @@ int dsoa_set_flags(dsoa_heap* h, uint32_t flags) {
     if (!h || (flags & ~(DSOA_FLAG_NO_COALESCE | DSOA_FLAG_NO_ROTATE | DSOA_FLAG_NO_HINT | DSOA_FLAG_UNFUSED)))
         return DSOA_ERR_INVALID_ARG;
     h->flags = flags;
+    return DSOA_OK;
+}
+
+int dsoa_set_lookups(dsoa_heap* h, int r) {
+    if (!h || r < 1 || r > 64) return DSOA_ERR_INVALID_ARG;
+    h->lookups = (uint32_t)r;
+    return DSOA_OK;
+}
+
+int dsoa_type_stats(dsoa_heap* h, int type, uint64_t* out_host) {
+    if (!h || !out_host) return DSOA_ERR_INVALID_ARG;
+    if (capturing(h->stream)) return DSOA_ERR_CAPTURE;
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+    unsigned long long* sc = h->scratch64;
+    DSOA_CUDA_TRY(cudaMemsetAsync(sc + 8, 0, 8, h->stream));
+    const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((h->ctx.lvl_words[0] + 255) / 256, (uint64_t)h->num_sms * 8));
+    k_popc_level0<<<g, 256, 0, h->stream>>>(h->ctx, dsoa_bm_alloc((uint32_t)type), sc + 8);
+    rc = dsoa_check_launch(h);
+    if (rc) return rc;
+    rc = dsoa_count_async(h, type, (uint64_t*)(sc + 9));
+    if (rc) return rc;
+    DSOA_CUDA_TRY(cudaMemcpyAsync(out_host, sc + 8, 16, cudaMemcpyDeviceToHost, h->stream));
+    DSOA_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return DSOA_OK;
 }
 

@@ -83,7 +83,8 @@ ABI_FUNCTIONS = [
     "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_delete_handles", "dsoa_enumerate", "dsoa_count", "dsoa_count_async",
     "dsoa_free_blocks_async", "dsoa_get_error", "dsoa_check", "dsoa_export_state",
     "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
-    "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_launch_count",
+    "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_set_lookups",
+    "dsoa_type_stats", "dsoa_launch_count",
     "dsoa_heap_destroy", "dsoa_error_string", "dsoa_enumerate_noalloc",
 ]
 
@@ -118,6 +119,7 @@ def load(path: str | None = None):
         "dsoa_graph_begin": [vp], "dsoa_graph_end": [vp, vp], "dsoa_graph_launch": [vp, vp],
         "dsoa_graph_destroy": [vp], "dsoa_set_launch": [vp, i32, i32, i32, i32],
         "dsoa_set_flags": [vp, u32], "dsoa_launch_count": [vp, vp], "dsoa_heap_destroy": [vp],
+        "dsoa_set_lookups": [vp, i32], "dsoa_type_stats": [vp, i32, vp],
         "dsoa_error_string": [i32],
         "dsoa_enumerate_noalloc": [vp, i32, vp, vp, vp, u64],
     }
@@ -286,6 +288,16 @@ class Heap:
 
     def set_flags(self, flags: int):
         _ok(load().dsoa_set_flags(self._h, flags), "dsoa_set_flags")
+
+    def set_lookups(self, r: int):
+        _ok(load().dsoa_set_lookups(self._h, r), "dsoa_set_lookups")
+
+    def type_stats(self, t: int) -> dict:
+        out = (ctypes.c_uint64 * 2)()
+        _ok(load().dsoa_type_stats(self._h, t, out), "dsoa_type_stats")
+        blocks, objs = int(out[0]), int(out[1])
+        frag = 1.0 - objs / (64.0 * blocks) if blocks else 0.0
+        return {"blocks": blocks, "objects": objs, "fragmentation": frag}
 
     @property
     def launches(self) -> int:

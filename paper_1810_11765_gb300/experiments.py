@@ -1,0 +1,120 @@
+"""The paper's detailed Wa-Tor analyses (Sec. 6.4-6.6), re-run on this runtime.
+
+  python -m paper_1810_11765_gb300.experiments frag      # F over time      (Fig. 10d)
+  python -m paper_1810_11765_gb300.experiments lookups   # F vs r            (Fig. 11)
+  python -m paper_1810_11765_gb300.experiments ablation  # NoCoal / NoShift  (Fig. 10c)
+  python -m paper_1810_11765_gb300.experiments heapsize  # time vs heap size (Fig. 12b)
+
+Each prints one JSON line.  Workload: Wa-Tor 1024 x 1024, 30 % fish / 5 % sharks,
+seed 0x5EED0003.  Fragmentation F = unused slots / slots of allocated blocks
+(Sec. 6.4), from the allocated-block bitmaps and live counts on the device.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+
+import torch
+
+from . import build, dsoa as D, inputs
+from .apps import WatorWorld
+
+
+def _world(heap_bytes=512 << 20, flags=0, lookups=None):
+    heap = D.Heap(heap_bytes)
+    w = WatorWorld(heap)
+    heap.freeze()
+    heap.set_flags(flags)
+    if lookups is not None:
+        heap.set_lookups(lookups)
+    w.add(1024, 1024, inputs.WatorConfig().seed)
+    return heap, w
+
+
+def _frag(heap, w):
+    f, s = heap.type_stats(w.fish_type), heap.type_stats(w.shark_type)
+    blocks = f["blocks"] + s["blocks"]
+    objs = f["objects"] + s["objects"]
+    return {"fish": f["objects"], "sharks": s["objects"], "blocks": blocks,
+            "F": 1.0 - objs / (64.0 * blocks) if blocks else 0.0}
+
+
+def frag_over_time(steps=500, every=25):
+    heap, w = _world()
+    rows = [dict(step=0, **_frag(heap, w))]
+    for k in range(1, steps + 1):
+        w.step()
+        if k % every == 0:
+            rows.append(dict(step=k, **_frag(heap, w)))
+    err = heap.get_error()
+    heap.close()
+    return {"experiment": "fragmentation over time (Fig. 10d)", "rows": rows, "device_errors": err}
+
+
+def frag_vs_lookups(rs=(1, 2, 3, 5, 8), steps=300):
+    rows = []
+    for r in rs:
+        heap, w = _world(lookups=r)
+        for _ in range(steps):
+            w.step()
+        rows.append(dict(r=r, **_frag(heap, w), device_errors=heap.get_error()))
+        heap.close()
+    return {"experiment": f"fragmentation after {steps} steps vs active-block lookups r (Fig. 11)", "rows": rows}
+
+
+def _timed_steps(heap, w, steps, flush):
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        w.step()
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def ablation(steps=200):
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    variants = {"dsoa": 0, "no_coalesce": D.FLAG_NO_COALESCE, "no_rotate": D.FLAG_NO_ROTATE,
+                "no_coalesce_no_rotate": D.FLAG_NO_COALESCE | D.FLAG_NO_ROTATE,
+                "no_hint": D.FLAG_NO_HINT, "unfused": D.FLAG_UNFUSED}
+    rows = []
+    for name, fl in variants.items():
+        heap, w = _world(heap_bytes=2 << 30, flags=fl)
+        t = _timed_steps(heap, w, steps, flush)
+        rows.append(dict(variant=name, steps_per_s=steps / (sum(t) / 1e3), median_ms=statistics.median(t),
+                         **_frag(heap, w), device_errors=heap.get_error()))
+        heap.close()
+    return {"experiment": f"ablations, {steps} plain steps (Fig. 10c)", "rows": rows}
+
+
+def heap_size(sizes_gib=(0.5, 1, 2, 4, 8, 16), steps=100):
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rows = []
+    for g in sizes_gib:
+        heap, w = _world(heap_bytes=int(g * (1 << 30)))
+        t = _timed_steps(heap, w, steps, flush)
+        rows.append(dict(heap_gib=g, blocks=heap.info()["num_blocks"], levels=heap.info()["num_levels"],
+                         steps_per_s=steps / (sum(t) / 1e3), device_errors=heap.get_error()))
+        heap.close()
+        torch.cuda.empty_cache()
+    return {"experiment": f"heap size vs step time, {steps} plain steps (Fig. 12b)", "rows": rows}
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("which", choices=["frag", "lookups", "ablation", "heapsize"])
+    a = p.parse_args()
+    build.build()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        res = {"frag": frag_over_time, "lookups": frag_vs_lookups, "ablation": ablation,
+               "heapsize": heap_size}[a.which]()
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -234,8 +234,28 @@ def test_double_free_and_bad_handles_are_reported_not_fatal():
     m.heap.delete_handles(first, 1000)                  # second free of the same slots
     assert m.heap.get_error() & D.DEV_DOUBLE_FREE
     M = m.heap.info()["num_blocks"]
-    bad = torch.tensor([(200 << 56) | 5, (1 << 56) | ((M + 7) << 6), 0], dtype=torch.int64, device="cuda")
+    bad_u64 = np.array([(200 << 56) | 5, (1 << 56) | ((M + 7) << 6), 0], dtype=np.uint64)
+    bad = torch.from_numpy(bad_u64.view(np.int64)).cuda()
     m.heap.delete_handles(bad, 3)                       # unknown type, block past M, null
     assert m.heap.get_error() == D.DEV_BAD_HANDLE
     assert m.heap.count(m.type) == n - 1000
     assert_clean(m)
+
+
+@pytest.mark.parametrize("r", [1, 2, 5, 16])
+def test_lookup_count_r_keeps_semantics_and_stats(r):
+    """r (Sec. 4.2, Fig. 11) changes how often new blocks are initialised, never the
+    results; type_stats reports blocks and objects consistent with the checkers."""
+    n, rounds = 40000, 3
+    ref, _, _ = oracle.micro_run(SEED, n, rounds)
+    m = make(heap_bytes=16 << 20, n=n)
+    m.heap.set_lookups(r)
+    for k in range(rounds):
+        m.round(k)
+        compare_round(m.stats(), ref[k])
+    st = m.heap.type_stats(m.type)
+    host = assert_clean(m)
+    assert st["objects"] == ref[-1]["live"] == host["live"][0]
+    assert st["blocks"] == host["blocks_in_use"]
+    assert abs(st["fragmentation"] - host["fragmentation"]) < 1e-12
+    assert 0.0 <= st["fragmentation"] < 1.0
