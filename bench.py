@@ -44,6 +44,22 @@ def parse():
     return p.parse_args()
 
 
+def ncu_traffic(kernel: str, units: float):
+    """DRAM bytes (read + write) per launch of `kernel` from an ncu capture recorded
+    in profiles/ncu_traffic.json, scaled to `units` (objects) per launch; None when
+    there is no capture or the kernels changed since (build fingerprint differs)."""
+    try:
+        from paper_1810_11765_gb300 import build
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)
+        if rec.get("fingerprint") != build.fingerprint():
+            return None
+        k = rec["kernels"][kernel]
+        return k["dram_bytes_per_unit"] * units
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -231,9 +247,10 @@ def wator_kernel_profile(seed, warmup, steps, flush):
             alg = n_agents * bpa + blocks * 12            # fields + R / snapshot read
             if not reuse:                                 # enumeration inside the kernel
                 alg += M / 8.0 + blocks * (12 + 8)        # level-0 bitmap, R/snapshot write, slot words
-            r = acc.setdefault(meth, {"ms": [], "bytes": []})
+            r = acc.setdefault(meth, {"ms": [], "bytes": [], "units": []})
             r["ms"].append(e0.elapsed_time(e1))
             r["bytes"].append(alg)
+            r["units"].append(n_agents)
         heap.run_kernel(D.K_WATOR_ADVANCE, 1, a)
     torch.cuda.synchronize()
     heap.close()
@@ -523,9 +540,11 @@ def dsoa_arm(args):
         avg_ms = statistics.mean(d["ms"])
         alg = statistics.mean(d["bytes"])
         ach = alg / (avg_ms / 1e3) / 1e9
+        units = statistics.mean(d["units"])
         out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                           "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
-                           "peak_kind": peak_kind, "avg_launch_ms": avg_ms, "alg_bytes_per_launch": alg}
+                           "unit": "GB/s", "frac": ach / hbm_peak, "traffic": ncu_traffic(dom, units),
+                           "peak_kind": peak_kind, "avg_launch_ms": avg_ms, "alg_bytes_per_launch": alg,
+                           "units_per_launch": units}
         out["step_kernels_ms"] = {k: statistics.mean(v["ms"]) for k, v in prof.items()}
         # --- do-all HBM sweep (spec kernel), > L2 working sets
         sweep = {}
@@ -538,7 +557,8 @@ def dsoa_arm(args):
         out["doall_hbm_gbs"] = best["gbs"]
         out["doall_roofline"] = {"kernel": DOALL_KERNELS[kbest][1], "bound": "hbm", "achieved": best["gbs"],
                                  "peak": hbm_peak, "unit": "GB/s", "frac": best["gbs"] / hbm_peak,
-                                 "traffic": None, "peak_kind": peak_kind,
+                                 "traffic": ncu_traffic(DOALL_KERNELS[kbest][1], best["objects"]),
+                                 "peak_kind": peak_kind,
                                  "alg_bytes_per_launch": best["alg_bytes"], "avg_launch_ms": best["ms"]}
         out["doall_sweep"] = sweep
         # --- alloc + free

@@ -64,7 +64,7 @@ struct dsoa_ctx {
     unsigned long long* bm;              /* all hierarchical bitmaps               */
     int* err;                            /* sticky DSOA_DEV_* bits                 */
     uint32_t* hint;                      /* [DSOA_HINT_SLOTS][ntypes] last block with
-                                            free slots per SM sub-slot (advisory)     */
+                                            free slots per warp slot (advisory)       */
     uint32_t* grid_scratch;              /* [DSOA_GRID_SCRATCH] per-CTA aggregates and
                                             grid-barrier words of the fused do-all    */
     uint64_t M;                          /* number of blocks                       */
@@ -84,7 +84,7 @@ struct dsoa_ctx {
 #define DSOA_FLAG_NO_COALESCE 1u          /* ablation: one request per leader       */
 #define DSOA_FLAG_NO_ROTATE 2u            /* ablation: plain find-first-set         */
 #define DSOA_FLAG_NO_HINT 4u              /* ablation: no per-SM block hint         */
-#define DSOA_HINT_SLOTS 1024u             /* 256 SMs x 4 warp groups                */
+#define DSOA_HINT_SLOTS 8192u             /* hint table entries per type (warps)    */
 #define DSOA_FLAG_UNFUSED 8u              /* enumerate with separate kernels        */
 #define DSOA_FUSED_MAX_CTAS 2048u         /* grid limit of the fused do-all         */
 #define DSOA_GRID_SCRATCH (DSOA_FUSED_MAX_CTAS + 64u)
@@ -361,14 +361,15 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
                                                          uint32_t h, uint64_t* bid_out) {
     const uint32_t act = dsoa_bm_active(t);
     const bool rot = !(c.flags & DSOA_FLAG_NO_ROTATE);
-    /* Per-SM hint: the block this SM (warp group) last reserved in while it
-     * still had free slots.  Trying it first skips the top-down bitmap search;
+    /* Per-warp hint: the block this warp (slot of the hint table) last reserved
+     * in while it still had free slots.  Trying it first skips the top-down
+     * bitmap search;
      * a stale hint is just another "Block Full / Deallocated / Replaced" case
      * of App. A.3 and is caught by the same checks as a stale try_find_set. */
     uint32_t* hp = nullptr;
     if (c.hint && !(c.flags & DSOA_FLAG_NO_HINT)) {
-        const uint32_t slot = (dsoa_smid() * 4u + ((threadIdx.x >> 5) & 3u)) % DSOA_HINT_SLOTS;
-        hp = c.hint + slot * c.ntypes + t;
+        const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        hp = c.hint + (gwarp % DSOA_HINT_SLOTS) * c.ntypes + t;
     }
     uint32_t empty_free = 0;   /* rounds that found the free-block bitmap empty */
     for (uint32_t round = 0; round < DSOA_ALLOC_ROUNDS; ++round) {

@@ -41,9 +41,14 @@ def _fingerprint(extra) -> str:
     for p in sorted(_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) +
                     glob.glob(os.path.join(INCLUDE, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.cuh"))):
         with open(p, "rb") as f:
-            h.update(p.encode() + b"\0" + f.read())
-    h.update(" ".join(ARCH + FLAGS + list(extra)).encode())
+            h.update(os.path.relpath(p, ROOT).encode() + b"\0" + f.read())
+    h.update(" ".join(ARCH + FLAGS + list(extra)).replace(ROOT, "").encode())
     return h.hexdigest()
+
+
+def fingerprint(extra_flags=()) -> str:
+    """Hash of every CUDA source, header and compile flag of the library."""
+    return _fingerprint(extra_flags)
 
 
 def build(force: bool = False, extra_flags=(), out_lib: str = LIB, verbose: bool = False) -> str:
