@@ -125,37 +125,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------- dist
-class Dist:
-    def __init__(self, n):
-        self.world = int(os.environ.get("WORLD_SIZE", "1"))
-        self.rank = int(os.environ.get("RANK", "0"))
-        self.local = int(os.environ.get("LOCAL_RANK", "0"))
-        self.pg = None
-        if self.world > 1:
-            import torch.distributed as dist
-            import torch
-            torch.cuda.set_device(self.local)
-            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
-            self.pg = dist
-
-    def barrier(self):
-        if self.pg:
-            self.pg.barrier()
-
-    def max(self, x: float) -> float:
-        if not self.pg:
-            return x
-        import torch
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
-        return float(t.item())
-
-    def close(self):
-        if self.pg:
-            self.pg.destroy_process_group()
-
-
 # ----------------------------------------------------------------------------- legs
 def ev():
     import torch
@@ -485,7 +454,8 @@ def dsoa_arm(args):
     import numpy as np
     import torch
     from paper_1810_11765_gb300 import build, inputs
-    dist = Dist(args.gpus)
+    from paper_1810_11765_gb300.replicas import Replicas, rank_seed
+    dist = Replicas()
     dev = dist.local if dist.world > 1 else 0
     torch.cuda.set_device(dev)
     build.build()
@@ -494,7 +464,7 @@ def dsoa_arm(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     cfg = inputs.WatorConfig()
-    seed = cfg.seed + 7919 * dist.rank          # one independent replica per rank
+    seed = rank_seed(cfg.seed, dist.rank)      # one independent replica per rank
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     hbm_peak, peak_kind = peaks()
 
@@ -509,7 +479,7 @@ def dsoa_arm(args):
     t_graph, grid_g, _, pop_g, err_g = run_wator(seed, args.warmup, args.steps, "graph", flush, launch)
     clk = clocks.stop()
     dist.barrier()
-    ms_graph = dist.max(sum(t_graph))
+    ms_graph = dist.max(sum(t_graph))         # slowest rank decides
     t_plain, grid_p, launches_per_step, pop_p, err_p = run_wator(seed, args.warmup, args.steps, "plain",
                                                                  flush, launch)
     ms_plain = dist.max(sum(t_plain))
