@@ -29,6 +29,8 @@ extern "C" {
 #define DSOA_M_MICRO_SCALE_TMA 106    /* same as SCALE, columns staged by bulk async copies */
 #define DSOA_M_MICRO_DELETE_ALL 107   /* delete this (every object of the snapshot)         */
 #define DSOA_M_MICRO_HANDLES 108      /* handles_out[id] = handle of the object with that id */
+#define DSOA_K_MICRO_DEVICE_DO 150    /* n threads; thread i visits every object with device_do
+                                         and writes (count, sum of id) to stats[i] as two u64 */
 typedef struct {
     uint64_t seed;       /* SplitMix64 key                                   */
     uint32_t id_base;    /* constructor: first id                            */

@@ -520,6 +520,32 @@ __global__ void __launch_bounds__(512) dsoa_doall_kernel(dsoa_ctx c, uint32_t t,
     }
 }
 
+/* device_do<T, f> (Sec. 2.1): run f(handle) on every object of type t, one
+ * after another, in the calling thread -- the sequential for-each that n-body
+ * style methods use to visit all pairs.  Walks the allocated-block bitmap of t
+ * top-down (level-1 containers select level-0 containers, Sec. 4.1) and the
+ * occupied slots of each block, one bit per object.  Objects created or
+ * deleted concurrently may or may not be visited. */
+template <typename F>
+__device__ inline void dsoa_device_do(const dsoa_ctx& c, uint32_t t, F&& f) {
+    const uint32_t b = dsoa_bm_alloc(t);
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, b, 1) : nullptr;
+    const uint64_t w1n = L1 ? c.lvl_words[1] : 1u;
+    for (uint64_t j = 0; j < w1n; ++j) {
+        unsigned long long sel = L1 ? dsoa_ld(&L1[j]) : 1ull;
+        for (; sel; sel &= sel - 1ull) {
+            const uint64_t i = j * 64 + (uint64_t)(__ffsll((long long)sel) - 1);
+            if (i >= c.lvl_words[0]) break;
+            for (unsigned long long w = dsoa_ld(&L0[i]); w; w &= w - 1ull) {
+                const uint64_t bid = i * 64 + (uint64_t)(__ffsll((long long)w) - 1);
+                for (unsigned long long o = ~dsoa_ld(&c.slot[bid]); o; o &= o - 1ull)
+                    f(dsoa_make_handle(t, bid, (uint32_t)(__ffsll((long long)o) - 1)));
+            }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------
  * Fused persistent do-all: enumeration and method in ONE cooperative launch.
  *   phase 1  CTA b counts the allocated blocks of its contiguous range of

@@ -80,6 +80,7 @@ unsigned dsoa_new_grid(dsoa_heap* h, uint64_t n, int tpb);
 // ---- per-application dispatchers (return DSOA_ERR_UNKNOWN_METHOD if not theirs) ----
 int dsoa_micro_new(dsoa_heap* h, int type, uint64_t n, int ctor, const void* a, size_t nb);
 int dsoa_micro_do(dsoa_heap* h, int type, int method, const void* a, size_t nb);
+int dsoa_micro_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_t nb);
 int dsoa_gol_new(dsoa_heap* h, int type, uint64_t n, int ctor, const void* a, size_t nb);
 int dsoa_gol_do(dsoa_heap* h, int type, int method, const void* a, size_t nb);
 int dsoa_gol_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_t nb);

@@ -535,6 +535,7 @@ int dsoa_parallel_do_enumerated(dsoa_heap* h, int type, int method_id, const voi
 int dsoa_run_kernel(dsoa_heap* h, int kernel_id, uint64_t n, const void* args, size_t nb) {
     int rc = dsoa_ensure_frozen(h);
     if (rc) return rc;
+    if (kernel_id >= 100 && kernel_id < 200) return dsoa_micro_kernel(h, kernel_id, n, args, nb);
     if (kernel_id >= 200 && kernel_id < 300) return dsoa_gol_kernel(h, kernel_id, n, args, nb);
     if (kernel_id >= 300 && kernel_id < 400) return dsoa_wator_kernel(h, kernel_id, n, args, nb);
     if (kernel_id >= 400 && kernel_id < 500) return dsoa_traffic_kernel(h, kernel_id, n, args, nb);

@@ -299,7 +299,32 @@ __global__ void __launch_bounds__(512) k_micro_stats(dsoa_ctx c, uint32_t t, con
     }
 }
 
+__global__ void k_micro_device_do(dsoa_ctx c, uint32_t t, uint64_t n, unsigned long long* out) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long cnt = 0, sid = 0;
+    dsoa_device_do(c, t, [&](dsoa_obj o) {
+        cnt += 1;
+        sid += (unsigned long long)(long long)dsoa_field<int32_t>(c, o, 0);
+    });
+    out[2 * i] = cnt;
+    out[2 * i + 1] = sid;
+}
+
 }  // namespace
+
+int dsoa_micro_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_t nb) {
+    dsoa_micro_args args;
+    int rc = dsoa_copy_args(&args, a, nb);
+    if (rc) return rc;
+    if (kernel != DSOA_K_MICRO_DEVICE_DO) return DSOA_ERR_UNKNOWN_METHOD;
+    if (!args.stats || n == 0 || h->ntypes < 1) return DSOA_ERR_INVALID_ARG;
+    const int type = (int)args.round;    /* the type to visit */
+    if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+    k_micro_device_do<<<(unsigned)((n + 127) / 128), 128, 0, h->stream>>>(dsoa_launch_ctx(h), (uint32_t)type, n,
+                                                                       (unsigned long long*)args.stats);
+    return dsoa_check_launch(h);
+}
 
 int dsoa_micro_new(dsoa_heap* h, int type, uint64_t n, int ctor, const void* a, size_t nb) {
     dsoa_micro_args args;

@@ -259,3 +259,21 @@ def test_lookup_count_r_keeps_semantics_and_stats(r):
     assert st["blocks"] == host["blocks_in_use"]
     assert abs(st["fragmentation"] - host["fragmentation"]) < 1e-12
     assert 0.0 <= st["fragmentation"] < 1.0
+
+
+def test_device_do_visits_every_object_once():
+    """device_do (Sec. 2.1): every thread's sequential for-each sees each live object
+    exactly once (count and sum of ids equal the oracle's)."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    n, rounds = 20000, 3
+    ref, _, _ = oracle.micro_run(SEED, n, rounds)
+    m = make(heap_bytes=16 << 20, n=n)
+    for k in range(rounds):
+        m.round(k)
+    threads = 3
+    out = torch.zeros(2 * threads, dtype=torch.int64, device="cuda")
+    m.heap.run_kernel(D.K_MICRO_DEVICE_DO, threads, m.args(stats=out.data_ptr(), round=m.type))
+    o = out.cpu().numpy().reshape(threads, 2)
+    assert np.all(o[:, 0] == ref[-1]["live"])
+    assert np.all(o[:, 1] == ref[-1]["sum_id"])
