@@ -138,7 +138,8 @@ def wator_world(seed, heap_bytes=512 << 20, launch=None):
     w = WatorWorld(heap)
     heap.freeze()
     if launch:
-        heap.set_launch(**launch)
+        from paper_1810_11765_gb300 import autotune
+        autotune.apply(heap, launch)
     return heap, w
 
 

@@ -185,10 +185,11 @@ int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
 
 /* Ablation switches of Sec. 6.4 (Fig. 10c): DSOA_FLAG_NO_COALESCE (1) turns
  * off allocation request coalescing, DSOA_FLAG_NO_ROTATE (2) turns off bitmap
- * rotation, DSOA_FLAG_NO_HINT (4) turns off the per-SM last-block hint and
- * DSOA_FLAG_UNFUSED (8) runs the enumeration of dsoa_parallel_do as separate
- * kernels instead of inside one cooperative do-all launch (the last two are
- * not in the paper).  Takes effect for launches issued after the call. */
+ * rotation, DSOA_FLAG_NO_HINT (4) turns off the per-warp last-block hint and
+ * DSOA_FLAG_FUSED (8) runs dsoa_parallel_do as ONE cooperative launch
+ * (enumeration and method separated by grid barriers) instead of the
+ * tile-count, compaction and do-all kernels (the last two are not in the
+ * paper).  Takes effect for launches issued after the call. */
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags);
 
 /* r of Sec. 4.2 / Fig. 11: attempts to find an active block (try_find_set on

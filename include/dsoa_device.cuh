@@ -85,7 +85,7 @@ struct dsoa_ctx {
 #define DSOA_FLAG_NO_ROTATE 2u            /* ablation: plain find-first-set         */
 #define DSOA_FLAG_NO_HINT 4u              /* ablation: no per-SM block hint         */
 #define DSOA_HINT_SLOTS 8192u             /* hint table entries per type (warps)    */
-#define DSOA_FLAG_UNFUSED 8u              /* enumerate with separate kernels        */
+#define DSOA_FLAG_FUSED 8u                /* one cooperative enumerate+do-all launch */
 #define DSOA_FUSED_MAX_CTAS 2048u         /* grid limit of the fused do-all         */
 #define DSOA_GRID_SCRATCH (DSOA_FUSED_MAX_CTAS + 64u)
 #define DSOA_NO_BLOCK 0xFFFFFFFFu

@@ -21,9 +21,16 @@ from .apps import WatorWorld
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_DIR = os.path.join(HERE, "_tune")
 
-CANDIDATES = [dict(tpb=tpb, ctas_per_sm=ctas, slots_per_thread=spt, scan_tiles=scan)
-              for tpb, ctas, spt, scan in itertools.product((128, 256, 512), (2, 4, 8), (1, 2), (1, 2))
+CANDIDATES = [dict(tpb=tpb, ctas_per_sm=ctas, slots_per_thread=spt, scan_tiles=scan, fused=fused)
+              for tpb, ctas, spt, scan, fused in itertools.product((128, 256, 512), (2, 4, 8), (1, 2), (1, 2), (0, 1))
               if tpb * ctas <= 4096]
+
+
+def apply(heap: D.Heap, launch: dict):
+    """Set a tuned launch shape on a heap (fused = cooperative enumeration + do-all)."""
+    shape = {k: v for k, v in launch.items() if k != "fused"}
+    heap.set_launch(**shape)
+    heap.set_flags(D.FLAG_FUSED if launch.get("fused") else 0)
 
 
 def _cache_path(key: str) -> str:
@@ -37,7 +44,7 @@ def time_wator_step(seed: int, launch: dict, side: int = 1024, warmup: int = 5, 
     heap = D.Heap(512 << 20)
     w = WatorWorld(heap)
     heap.freeze()
-    heap.set_launch(**launch)
+    apply(heap, launch)
     w.add(side, side, seed)
     heap.graph_begin()
     w.step()
@@ -60,7 +67,7 @@ def time_wator_step(seed: int, launch: dict, side: int = 1024, warmup: int = 5, 
 
 
 def best_wator_launch(seed: int, use_cache: bool = True, verbose: bool = False) -> dict:
-    path = _cache_path("wator1024")
+    path = _cache_path("wator1024-v2")
     if use_cache and os.path.exists(path):
         with open(path) as f:
             return json.load(f)["best"]

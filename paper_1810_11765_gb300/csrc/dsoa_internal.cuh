@@ -139,7 +139,7 @@ int dsoa_run_doall_fused(dsoa_heap* h, int type, const typename M::Args& args) {
 // Launch a do-all of method M over `type` (enumeration + persistent kernel).
 template <class M>
 int dsoa_run_doall(dsoa_heap* h, int type, const typename M::Args& args) {
-    if (!h->skip_enumeration && !(h->flags & DSOA_FLAG_UNFUSED)) {
+    if (!h->skip_enumeration && (h->flags & DSOA_FLAG_FUSED)) {
         if (!h->frozen) return DSOA_ERR_NOT_FROZEN;
         if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
         return h->slots_per_thread >= 2 ? dsoa_run_doall_fused<M, 2>(h, type, args)

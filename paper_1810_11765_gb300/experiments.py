@@ -80,7 +80,7 @@ def ablation(steps=200):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     variants = {"dsoa": 0, "no_coalesce": D.FLAG_NO_COALESCE, "no_rotate": D.FLAG_NO_ROTATE,
                 "no_coalesce_no_rotate": D.FLAG_NO_COALESCE | D.FLAG_NO_ROTATE,
-                "no_hint": D.FLAG_NO_HINT, "unfused": D.FLAG_UNFUSED}
+                "no_hint": D.FLAG_NO_HINT, "fused": D.FLAG_FUSED}
     rows = []
     for name, fl in variants.items():
         heap, w = _world(heap_bytes=2 << 30, flags=fl)
