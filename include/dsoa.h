@@ -179,7 +179,8 @@ int dsoa_graph_destroy(dsoa_graph* g);
 /* Launch shape of do-all and scan kernels (0 keeps the current value):
  * threads per CTA of the do-all (multiple of 64, at most 512), CTAs per SM of the persistent
  * do-all grid, slots handled per thread by vectorised methods (1, 2 or 4), and
- * allocated-bitmap level-1 words per CTA of the compaction kernel. */
+ * the enumeration: 1 or 2 = tile-count kernel + compaction kernel with that many
+ * level-1 tiles per CTA, 3 = single-pass decoupled look-back kernel (default). */
 int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
                     int slots_per_thread, int scan_tiles_per_cta);
 

@@ -22,7 +22,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_DIR = os.path.join(HERE, "_tune")
 
 CANDIDATES = [dict(tpb=tpb, ctas_per_sm=ctas, slots_per_thread=spt, scan_tiles=scan, fused=fused)
-              for tpb, ctas, spt, scan, fused in itertools.product((128, 256, 512), (2, 4, 8), (1, 2), (1, 2), (0, 1))
+              for tpb, ctas, spt, scan, fused in itertools.product((128, 256, 512), (2, 4, 8), (1, 2), (1, 3), (0, 1))
               if tpb * ctas <= 4096]
 
 
@@ -67,7 +67,7 @@ def time_wator_step(seed: int, launch: dict, side: int = 1024, warmup: int = 5, 
 
 
 def best_wator_launch(seed: int, use_cache: bool = True, verbose: bool = False) -> dict:
-    path = _cache_path("wator1024-v2")
+    path = _cache_path("wator1024-v3")
     if use_cache and os.path.exists(path):
         with open(path) as f:
             return json.load(f)["best"]

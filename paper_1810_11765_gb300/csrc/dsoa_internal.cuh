@@ -52,7 +52,9 @@ struct dsoa_heap {
     int slots_per_thread = 1;        // generic do-all: 1 (64 threads/block) or 2 (a warp/block);
                                      // vectorised microbench kernel: 1, 2 or 4
     int vec_slots_per_thread = 4;    // vectorised kernels: slots per thread (1, 2 or 4)
-    int scan_tiles_per_cta = 1;
+    int scan_tiles_per_cta = 0;      // 0 = single-pass look-back; 1, 2 = tile-count + compaction kernels
+    unsigned long long* lb_state = nullptr;  // [tiles] look-back state words (epoch, status, value)
+    uint32_t* lb_ctl = nullptr;              // ticket, done counter, epoch of the look-back kernel
 
     uint32_t flags = 0;              // DSOA_FLAG_* applied to every launch
     uint32_t lookups = DSOA_LOOKUP_ATTEMPTS;  // r: active-block lookups before the slow path

@@ -25,7 +25,7 @@ struct Layout {
     uint32_t nlevels = 0;
     uint64_t lvl_off[DSOA_MAX_LEVELS] = {0}, lvl_words[DSOA_MAX_LEVELS] = {0};
     uint64_t off_data = 0, off_slot = 0, off_btype = 0, off_bm = 0, off_R = 0, off_Rocc = 0,
-             off_tcnt = 0, off_toff = 0, off_hint = 0, off_grid = 0, off_small = 0, total = 0;
+             off_tcnt = 0, off_toff = 0, off_lb = 0, off_hint = 0, off_grid = 0, off_small = 0, total = 0;
 };
 
 bool make_layout(uint64_t M, uint32_t block_bytes, int ntypes, Layout* L) {
@@ -56,6 +56,7 @@ bool make_layout(uint64_t M, uint32_t block_bytes, int ntypes, Layout* L) {
     L->off_Rocc = p;  p = align_up(p + M * 8 * (uint64_t)ntypes, kAlign);
     L->off_tcnt = p;  p = align_up(p + L->tiles * 4, kAlign);
     L->off_toff = p;  p = align_up(p + L->tiles * 4, kAlign);
+    L->off_lb = p;    p = align_up(p + L->tiles * 8, kAlign);
     L->off_hint = p;  p = align_up(p + (uint64_t)DSOA_HINT_SLOTS * (uint64_t)ntypes * 4, kAlign);
     L->off_grid = p;  p = align_up(p + (uint64_t)DSOA_GRID_SCRATCH * 4, kAlign);
     L->off_small = p; p = align_up(p + kSmallWords * 8, kAlign);
@@ -175,6 +176,122 @@ __global__ void __launch_bounds__(64 * TPC) k_compact(dsoa_ctx c, uint32_t b, ui
         const uint32_t bid = list[tl][i];
         R[base + i] = bid;
         Rocc[base + i] = ~c.slot[bid];
+    }
+}
+
+// Single-pass enumeration (decoupled look-back, Merrill & Garland 2016): one
+// 64-thread CTA per level-1 tile.  A CTA takes its tile from a ticket counter
+// (so it only waits on tiles taken by CTAs that already run), publishes the
+// tile's aggregate, lets warp 0 walk back over its predecessors' published
+// aggregates / inclusive prefixes 32 at a time, publishes its own inclusive
+// prefix, and writes R and the occupancy snapshot of the tile.  State words
+// carry the enumeration's epoch, so nothing is reset between launches (safe
+// in graph replays); the last CTA to finish advances the epoch and resets the
+// ticket.  Every wait is bounded (DSOA_DEV_SPIN).
+constexpr unsigned long long kLbA = 1ull, kLbP = 2ull;
+__device__ __forceinline__ unsigned long long lb_word(uint32_t ep, unsigned long long st, unsigned long long v) {
+    return ((unsigned long long)(ep & 0xFFFFFFu) << 40) | (st << 38) | (v & ((1ull << 38) - 1ull));
+}
+
+__global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint32_t b, uint64_t tiles,
+                                                      unsigned long long* __restrict__ state,
+                                                      uint32_t* __restrict__ ctl, uint32_t* __restrict__ R,
+                                                      unsigned long long* __restrict__ Rocc,
+                                                      uint32_t* __restrict__ r_dev) {
+    __shared__ uint32_t list[4096];
+    __shared__ uint32_t wsum[2];
+    __shared__ uint32_t s_tile, s_ep;
+    __shared__ unsigned long long s_prefix;
+    uint32_t* ticket = ctl;
+    uint32_t* done = ctl + 1;
+    uint32_t* epoch = ctl + 2;
+    const uint32_t j = threadIdx.x, lane = j & 31u;
+    if (j == 0) {
+        s_tile = atomicAdd(ticket, 1u);
+        s_ep = dsoa_ld32(epoch) + 1u;
+    }
+    __syncthreads();
+    const uint64_t t = s_tile;
+    const uint32_t ep = s_ep;
+    unsigned long long w = 0ull;
+    const unsigned long long sel = c.nlevels >= 2 ? dsoa_level(c, b, 1)[t] : 1ull;
+    const uint64_t wi = t * 64 + j;
+    if (((sel >> j) & 1ull) && wi < c.lvl_words[0]) w = dsoa_level(c, b, 0)[wi];
+    const uint32_t cnt = __popcll(w);
+    uint32_t incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+    }
+    if (lane == 31) wsum[j >> 5] = incl;
+    __syncthreads();
+    const uint32_t total = wsum[0] + wsum[1];
+    /* publish this tile's aggregate (or its prefix, for tile 0) as early as possible */
+    if (j == 0) {
+        __threadfence();
+        dsoa_st(&state[t], lb_word(ep, t == 0 ? kLbP : kLbA, total));
+    }
+    /* stage this tile's block ids */
+    {
+        uint32_t k = incl - cnt + ((j >= 32) ? wsum[0] : 0u);
+        const uint64_t bid0 = wi * 64;
+        for (unsigned long long x = w; x; x &= x - 1ull)
+            list[k++] = (uint32_t)(bid0 + (uint32_t)(__ffsll((long long)x) - 1));
+    }
+    /* warp 0: look back over the predecessors */
+    if (j < 32) {
+        unsigned long long prefix = 0ull;
+        bool ok = true;
+        if (t > 0) {
+            int64_t base = (int64_t)t - 1;
+            for (;;) {
+                const int64_t q = base - (int64_t)lane;
+                unsigned long long sw = 0ull;
+                uint32_t spins = 0;
+                if (q >= 0) {
+                    for (;;) {
+                        sw = dsoa_ld(&state[q]);
+                        if ((uint32_t)(sw >> 40) == (ep & 0xFFFFFFu) && ((sw >> 38) & 3ull)) break;
+                        if (++spins >= DSOA_SPIN_LIMIT) { ok = false; break; }
+                        if (spins > 8) __nanosleep(32u);
+                    }
+                }
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                const bool isP = q >= 0 && ((sw >> 38) & 3ull) == kLbP;
+                const uint32_t pmask = __ballot_sync(0xffffffffu, isP);
+                const uint32_t stop = pmask ? (uint32_t)(__ffs((int)pmask) - 1) : 32u;   /* nearest P */
+                unsigned long long v = (q >= 0 && lane <= stop) ? (sw & ((1ull << 38) - 1ull)) : 0ull;
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                prefix += v;
+                if (pmask || base - 32 < 0) break;
+                base -= 32;
+            }
+        }
+        if (j == 0) {
+            if (!ok) dsoa_raise(c, DSOA_DEV_SPIN);
+            s_prefix = prefix;
+            __threadfence();
+            if (t > 0) dsoa_st(&state[t], lb_word(ep, kLbP, prefix + total));
+            if (t == tiles - 1) *r_dev = (uint32_t)(prefix + total);
+        }
+    }
+    __syncthreads();
+    const unsigned long long base = s_prefix;
+    for (uint32_t i = j; i < total; i += 64) {
+        const uint32_t bid = list[i];
+        R[base + i] = bid;
+        Rocc[base + i] = ~c.slot[bid];
+    }
+    /* the last CTA to finish closes the epoch */
+    __syncthreads();
+    if (j == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == (uint32_t)tiles - 1u) {
+            dsoa_st32(ticket, 0u);
+            dsoa_st32(done, 0u);
+            __threadfence();
+            dsoa_st32(epoch, ep);
+        }
     }
 }
 
@@ -348,6 +465,13 @@ int dsoa_enumerate_internal(dsoa_heap* h, int type) {
     if (rc) return rc;
     if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
     const uint32_t b = dsoa_bm_alloc((uint32_t)type);
+    if (h->scan_tiles_per_cta == 0) {      // single-pass look-back enumeration (default)
+        k_enum_lookback<<<(unsigned)h->tiles, 64, 0, h->stream>>>(h->ctx, b, h->tiles, h->lb_state, h->lb_ctl,
+                                                                 h->R[type], h->Rocc[type], h->r_dev[type]);
+        rc = dsoa_check_launch(h);
+        if (rc == DSOA_OK) h->enumerated[type] = true;
+        return rc;
+    }
     const int tpb = 256;
     const uint64_t warps = h->tiles;
     const unsigned g1 = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 7) / 8, (uint64_t)h->num_sms * 8));
@@ -449,6 +573,8 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     uint64_t* small = (uint64_t*)(base + L.off_small);
     c.err = (int*)(small + 0);
     c.hint = (uint32_t*)(base + L.off_hint);
+    h->lb_state = (unsigned long long*)(base + L.off_lb);
+    h->lb_ctl = (uint32_t*)(small + 4);      // ticket, done, epoch
     c.grid_scratch = (uint32_t*)(base + L.off_grid);
     h->done = (uint32_t*)(small + 1);
     h->scratch64 = (unsigned long long*)(small + 32);
@@ -476,6 +602,7 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     DSOA_CUDA_TRY(cudaMemsetAsync(small, 0, kSmallWords * 8, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(c.hint, 0xFF, (uint64_t)DSOA_HINT_SLOTS * (uint64_t)h->ntypes * 4, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(c.grid_scratch, 0, (uint64_t)DSOA_GRID_SCRATCH * 4, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(h->lb_state, 0, L.tiles * 8, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(h->R[0], 0, L.M * 4 * (uint64_t)h->ntypes, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(h->Rocc[0], 0, L.M * 8 * (uint64_t)h->ntypes, h->stream));
     k_init_free<<<std::max(1, h->num_sms * 4), 256, 0, h->stream>>>(c);
@@ -698,8 +825,8 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
         h->vec_slots_per_thread = slots_per_thread;
     }
     if (scan_tiles) {
-        if (scan_tiles != 1 && scan_tiles != 2) return DSOA_ERR_INVALID_ARG;
-        h->scan_tiles_per_cta = scan_tiles;
+        if (scan_tiles < 1 || scan_tiles > 3) return DSOA_ERR_INVALID_ARG;
+        h->scan_tiles_per_cta = scan_tiles == 3 ? 0 : scan_tiles;   // 3 = single-pass look-back
     }
     return DSOA_OK;
 }

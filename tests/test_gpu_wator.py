@@ -107,3 +107,17 @@ def test_graph_captured_steps_match_oracle(launch, flags):
     assert counts == (st[-1]["fish"], st[-1]["sharks"])
     assert heap.get_error() == 0
     g.close()
+
+
+@pytest.mark.parametrize("scan", [1, 2, 3])
+def test_enumeration_modes_agree(scan):
+    """Tile-count + compaction kernels (1 or 2 tiles per CTA) and the single-pass
+    look-back kernel give the same block list, hence the same simulation."""
+    heap, w = world(32 << 20)
+    heap.set_launch(scan_tiles=scan)
+    s = w.add(160, 120, 55)
+    for _ in range(40):
+        w.step()
+    ref, _ = oracle.wator_run(160, 120, 40, seed=55)
+    assert np.array_equal(w.read(s), ref)
+    assert heap.get_error() == 0
