@@ -44,10 +44,11 @@ def parse():
     return p.parse_args()
 
 
-def ncu_traffic(kernel: str, units: float):
-    """DRAM bytes (read + write) per launch of `kernel` from an ncu capture recorded
-    in profiles/ncu_traffic.json, scaled to `units` (objects) per launch; None when
-    there is no capture or the kernels changed since (build fingerprint differs)."""
+def ncu_traffic(kernel: str, units: float, key: str = "dram_bytes_per_unit"):
+    """DRAM bytes (read + write) per launch of `kernel` (or, with `key`, another
+    per-unit counter) from an ncu capture recorded in profiles/ncu_traffic.json,
+    scaled to `units` (objects) per launch; None when there is no capture or the
+    kernels changed since (build fingerprint differs)."""
     try:
         from paper_1810_11765_gb300 import build
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
@@ -55,7 +56,7 @@ def ncu_traffic(kernel: str, units: float):
         if rec.get("fingerprint") != build.fingerprint():
             return None
         k = rec["kernels"][kernel]
-        return k["dram_bytes_per_unit"] * units
+        return k[key] * units
     except Exception:
         return None
 
@@ -244,21 +245,32 @@ def doall_sweep(log2n, holes, flush, iters=10, kernel="vec128"):
     live = m.heap.count(m.type)
     m.heap.enumerate(m.type)
     args = m.args()
-    times = []
-    for _ in range(iters):
+    meth = getattr(D, DOALL_KERNELS[kernel][0])
+    single = []
+    for _ in range(3):                      # one launch, L2 flushed before it
         flush.zero_()
         a, b = ev(), ev()
         a.record()
-        m.heap.parallel_do_enumerated(m.type, getattr(D, DOALL_KERNELS[kernel][0]), args)
+        m.heap.parallel_do_enumerated(m.type, meth, args)
         b.record()
         b.synchronize()
-        times.append(a.elapsed_time(b))
+        single.append(a.elapsed_time(b))
+    # average launch duration over back-to-back launches (every launch streams the
+    # whole >L2 object set, so no flush is needed between them)
+    m.heap.parallel_do_enumerated(m.type, meth, args)
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(iters):
+        m.heap.parallel_do_enumerated(m.type, meth, args)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / iters
     err = m.heap.get_error()
     m.heap.close()
     del m
     torch.cuda.empty_cache()
-    ms = statistics.median(times)
-    return {"objects": live, "ms": ms, "alg_bytes": live * 12, "gbs": live * 12 / ms / 1e6, "err": err}
+    return {"objects": live, "ms": ms, "alg_bytes": live * 12, "gbs": live * 12 / ms / 1e6,
+            "single_launch_ms": statistics.median(single), "err": err}
 
 
 def alloc_free_storm(log2n, flush, iters=3):
@@ -287,6 +299,66 @@ def alloc_free_storm(log2n, flush, iters=3):
     del_ms = statistics.median(r[1] for r in res)
     return {"objects": n, "new_ms": new_ms, "delete_ms": del_ms,
             "ops_per_s": 2 * n / ((new_ms + del_ms) / 1e3), "left": left, "err": err}
+
+
+# Minimum bitmap atomics of the method for the storm's pattern (full warps of one
+# type into an empty heap, then delete-all), per 64-object block:
+#   new:    free-bitmap take, allocated set, active set, 2 warp reservations,
+#           active clear when full                                       = 6
+#   delete: 2 warp-combined releases, active set at the first free,
+#           invalidate, active clear, allocated clear, free set           = 7
+# (upper-level propagation, once per 64 blocks per bitmap, not counted).
+ALG_ATOMICS_PER_OBJECT = {"new": 6 / 64, "delete": 7 / 64}
+
+
+def l2_atomic_peak(iters=64, reps=5):
+    """Ceiling of single-lane 64-bit bitmap atomics with return: every lane's op
+    is its own L2 request, on a 32 MiB (L2-resident) word array, one resident
+    grid of threads (the K_MICRO_ATOMIC_PEAK probe of the library)."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import Micro
+    m = Micro(4 << 20, 0x5EED0001, 64)
+    nw = 1 << 22
+    words = torch.zeros(nw, dtype=torch.int64, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    n = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 2048
+    a = m.args(handles_out=words.data_ptr(), n_ids=nw, round=iters, stats=sink.data_ptr(), seed=1)
+    for _ in range(3):
+        m.heap.run_kernel(D.K_MICRO_ATOMIC_PEAK, n, a)
+    ts = []
+    for _ in range(reps):
+        e0, e1 = ev(), ev()
+        e0.record()
+        m.heap.run_kernel(D.K_MICRO_ATOMIC_PEAK, n, a)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    m.heap.close()
+    ms = statistics.median(ts)
+    return {"atomics_per_s": n * iters / (ms / 1e3), "ms": ms, "threads": n, "ops_per_thread": iters,
+            "words": nw}
+
+
+def alloc_roofline(storm, peak):
+    n = storm["objects"]
+    alg = {k: v * n for k, v in ALG_ATOMICS_PER_OBJECT.items()}
+    rate = (alg["new"] + alg["delete"]) / ((storm["new_ms"] + storm["delete_ms"]) / 1e3)
+    p = peak["atomics_per_s"]
+    key = "atomic_instructions_per_unit"
+    t_new = ncu_traffic("dsoa_new_kernel<MicroCtor>", n, key)
+    t_del = ncu_traffic("dsoa_doall_kernel<MicroDeleteAll>", n, key)
+    return {"kernel": "dsoa_new_kernel<MicroCtor> + do-all MicroDeleteAll", "bound": "l2_atomic",
+            "achieved": rate / 1e9, "peak": p / 1e9, "unit": "Gatomic/s", "frac": rate / p,
+            "traffic": None if t_new is None or t_del is None else t_new + t_del,
+            "traffic_unit": "atomic operations issued per storm (ncu smsp__sass_inst_executed_op_global_atom; "
+                            "every allocator atomic is single-lane)",
+            "alg_atomics_per_storm": alg["new"] + alg["delete"],
+            "new": {"achieved": alg["new"] / (storm["new_ms"] / 1e3) / 1e9,
+                    "frac": alg["new"] / (storm["new_ms"] / 1e3) / p},
+            "delete": {"achieved": alg["delete"] / (storm["delete_ms"] / 1e3) / 1e9,
+                       "frac": alg["delete"] / (storm["delete_ms"] / 1e3) / p},
+            "peak_kind": "measured live: K_MICRO_ATOMIC_PEAK probe"}
 
 
 def heap_utilisation(heap_bytes=1 << 30):
@@ -536,6 +608,8 @@ def dsoa_arm(args):
         storm = alloc_free_storm(24, flush)
         out["alloc_free_ops_per_s"] = storm["ops_per_s"]
         out["alloc_free"] = storm
+        out["l2_atomic_peak"] = l2_atomic_peak()
+        out["alloc_roofline"] = alloc_roofline(storm, out["l2_atomic_peak"])
         out["heap_utilisation"] = heap_utilisation()
         # --- other apps (plain vs graph) and serving
         out["gol_512"] = app_steps("gol", 100, flush)

@@ -31,6 +31,15 @@ extern "C" {
 #define DSOA_M_MICRO_HANDLES 108      /* handles_out[id] = handle of the object with that id */
 #define DSOA_K_MICRO_DEVICE_DO 150    /* n threads; thread i visits every object with device_do
                                          and writes (count, sum of id) to stats[i] as two u64 */
+#define DSOA_K_MICRO_ATOMIC_PEAK 151  /* n threads; thread i issues `round` 64-bit atomics with
+                                         return (atomicAnd / atomicOr alternating) on the words
+                                         handles_out[0 .. n_ids), word (i + k n) * 17 mod n_ids
+                                         at its k-th op, so that every lane's op is its own L2
+                                         request (n_ids a power of two >= 32, caller-owned
+                                         device buffer).  The XOR of the returned words is
+                                         stored to *(u64*)stats only when it equals seed.  It
+                                         measures the L2 ceiling of single-lane bitmap atomics,
+                                         the operation the allocator is built from (Sec. 4). */
 typedef struct {
     uint64_t seed;       /* SplitMix64 key                                   */
     uint32_t id_base;    /* constructor: first id                            */

@@ -81,6 +81,8 @@ struct dsoa_ctx {
     uint16_t col_off[DSOA_MAX_TYPES][DSOA_MAX_FIELDS];
 };
 
+#define DSOA_FRESH_GROUP 16u              /* group size that takes a fresh block
+                                             after a lost race (leader_reserve)    */
 #define DSOA_FLAG_NO_COALESCE 1u          /* ablation: one request per leader       */
 #define DSOA_FLAG_NO_ROTATE 2u            /* ablation: plain find-first-set         */
 #define DSOA_FLAG_NO_HINT 4u              /* ablation: no per-SM block hint         */
@@ -378,7 +380,14 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
             const uint32_t hb = *hp;
             if (hb < c.M) bid = hb;
         }
-        for (uint32_t a = 0; a < c.lookups && bid < 0; ++a)
+        /* After a lost race (round >= 1) a group of DSOA_FRESH_GROUP or more
+         * requests takes a fresh block instead of searching active[t] again: when
+         * far more warps allocate at once than there are active blocks with room
+         * (an allocation burst), they would otherwise keep converging on the same
+         * few blocks.  Small groups keep searching, so steady-state
+         * fragmentation is unchanged.  An empty free bitmap always searches. */
+        const bool search = round == 0 || empty_free || want < DSOA_FRESH_GROUP;
+        for (uint32_t a = 0; search && a < c.lookups && bid < 0; ++a)
             bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
         if (bid < 0) {
             bid = dsoa_block_new(c, t, h ^ round);

@@ -311,12 +311,37 @@ __global__ void k_micro_device_do(dsoa_ctx c, uint32_t t, uint64_t n, unsigned l
     out[2 * i + 1] = sid;
 }
 
+/* L2 ceiling of single-lane 64-bit bitmap atomics (the allocator's building
+ * block, Sec. 4): consecutive lanes hit words 17 apart (136 bytes), so each
+ * lane's op is a separate L2 request, as a warp leader's reservation is. */
+__global__ void k_micro_atomic_peak(unsigned long long* __restrict__ w, uint64_t mask, uint64_t n, uint32_t iters,
+                                    unsigned long long key, unsigned long long* __restrict__ sink) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long acc = 0ull;
+    for (uint32_t k = 0; k < iters; ++k) {
+        const uint64_t idx = ((i + (uint64_t)k * n) * 17u) & mask;
+        const unsigned long long bit = 1ull << (k & 63u);
+        acc ^= (k & 1u) ? atomicOr(w + idx, bit) : atomicAnd(w + idx, ~bit);
+    }
+    if (acc == key) *sink = acc;
+}
+
 }  // namespace
 
 int dsoa_micro_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_t nb) {
     dsoa_micro_args args;
     int rc = dsoa_copy_args(&args, a, nb);
     if (rc) return rc;
+    if (kernel == DSOA_K_MICRO_ATOMIC_PEAK) {
+        const uint64_t nw = args.n_ids;
+        if (!args.handles_out || !args.stats || n == 0 || args.round == 0 || nw < 32 || (nw & (nw - 1)))
+            return DSOA_ERR_INVALID_ARG;
+        k_micro_atomic_peak<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+            (unsigned long long*)args.handles_out, nw - 1, n, args.round, (unsigned long long)args.seed,
+            (unsigned long long*)args.stats);
+        return dsoa_check_launch(h);
+    }
     if (kernel != DSOA_K_MICRO_DEVICE_DO) return DSOA_ERR_UNKNOWN_METHOD;
     if (!args.stats || n == 0 || h->ntypes < 1) return DSOA_ERR_INVALID_ARG;
     const int type = (int)args.round;    /* the type to visit */

@@ -30,6 +30,7 @@ C_MICRO, M_MICRO_SCALE, M_MICRO_SCALE_SCALAR, M_MICRO_DELETE = 100, 101, 102, 10
 M_MICRO_GATHER, M_MICRO_STATS, M_MICRO_SCALE_TMA, M_MICRO_DELETE_ALL = 104, 105, 106, 107
 M_MICRO_HANDLES = 108
 K_MICRO_DEVICE_DO = 150
+K_MICRO_ATOMIC_PEAK = 151
 C_GOL_CELL, M_GOL_SPREAD, M_GOL_REAP, M_GOL_DECIDE, M_GOL_READ, M_GOL_KILL = 200, 201, 202, 203, 204, 205
 K_GOL_ADVANCE = 250
 M_WATOR_FISH_CHOOSE, M_WATOR_FISH_MOVE, M_WATOR_SHARK_CHOOSE, M_WATOR_SHARK_MOVE = 301, 302, 303, 304

@@ -3,6 +3,7 @@
   python -m paper_1810_11765_gb300.profile_cases doall --log2n 24 [--holes] [--iters 3]
   python -m paper_1810_11765_gb300.profile_cases wator --side 1024 --steps 3
   python -m paper_1810_11765_gb300.profile_cases alloc --log2n 22
+  python -m paper_1810_11765_gb300.profile_cases atomic --iters 64
 
 Each case prints CUDA-event timings of its kernels (without a profiler attached
 these are the numbers to trust) and keeps its device footprint to a few hundred MB
@@ -82,9 +83,29 @@ def case_alloc(log2n: int):
     m.heap.close()
 
 
+def case_atomic(iters: int):
+    """The L2 atomic-throughput probe (K_MICRO_ATOMIC_PEAK) on a 32 MiB word array."""
+    m = Micro(4 << 20, 0x5EED0001, 64)
+    nw = 1 << 22
+    words = torch.zeros(nw, dtype=torch.int64, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    n = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 2048
+    args = m.args(handles_out=words.data_ptr(), n_ids=nw, round=iters, stats=sink.data_ptr(), seed=1)
+    for _ in range(3):
+        a, b = _ev(), _ev()
+        a.record()
+        m.heap.run_kernel(D.K_MICRO_ATOMIC_PEAK, n, args)
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        print(f"atomic probe: {n} threads x {iters} ops, {ms:.4f} ms, {n * iters / ms / 1e6:.1f} G atomics/s")
+    print("err", m.heap.get_error())
+    m.heap.close()
+
+
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("case", choices=["doall", "wator", "alloc"])
+    p.add_argument("case", choices=["doall", "wator", "alloc", "atomic"])
     p.add_argument("--log2n", type=int, default=24)
     p.add_argument("--holes", action="store_true")
     p.add_argument("--iters", type=int, default=3)
@@ -97,6 +118,8 @@ def main():
         case_doall(a.log2n, a.holes, a.iters, a.method)
     elif a.case == "wator":
         case_wator(a.side, a.steps)
+    elif a.case == "atomic":
+        case_atomic(a.iters)
     else:
         case_alloc(a.log2n)
 

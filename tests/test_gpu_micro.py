@@ -286,3 +286,34 @@ def test_device_do_visits_every_object_once():
     o = out.cpu().numpy().reshape(threads, 2)
     assert np.all(o[:, 0] == ref[-1]["live"])
     assert np.all(o[:, 1] == ref[-1]["sum_id"])
+
+
+def test_atomic_peak_probe_final_words():
+    """The L2 atomic-throughput probe: every op's bit k & 63 is cleared by even k and
+    set by odd k, so ops on one word commute and the final words are fixed; they are
+    recomputed here with numpy from the stated index rule."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    m = make(heap_bytes=4 << 20, n=64)
+    nw, n, iters = 1 << 12, 3000, 9
+    rng = np.random.default_rng(7)
+    init = rng.integers(0, 2**63, size=nw, dtype=np.int64)
+    words = torch.from_numpy(init.copy()).cuda()
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    m.heap.run_kernel(D.K_MICRO_ATOMIC_PEAK, n, m.args(handles_out=words.data_ptr(), n_ids=nw, round=iters,
+                                                       stats=sink.data_ptr(), seed=1))
+    torch.cuda.synchronize()
+    w = init.view(np.uint64).copy()
+    i = np.arange(n, dtype=np.uint64)
+    for k in range(iters):
+        idx = ((i + np.uint64(k * n)) * np.uint64(17)) & np.uint64(nw - 1)
+        bit = np.uint64(1) << np.uint64(k & 63)
+        if k & 1:
+            np.bitwise_or.at(w, idx, bit)
+        else:
+            np.bitwise_and.at(w, idx, ~bit)
+    assert np.array_equal(words.cpu().numpy().view(np.uint64), w)
+    with pytest.raises(RuntimeError):
+        m.heap.run_kernel(D.K_MICRO_ATOMIC_PEAK, n, m.args(handles_out=words.data_ptr(), n_ids=nw - 1, round=1,
+                                                           stats=sink.data_ptr()))
+    assert m.heap.get_error() == 0
