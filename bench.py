@@ -173,10 +173,13 @@ def run_wator(seed, warmup, steps, mode, flush, launch=None):
     grid = w.read(slot)
     fish, sharks = w.counts()
     err = heap.get_error()
+    fs, ss = heap.type_stats(w.fish_type), heap.type_stats(w.shark_type)
+    blocks = fs["blocks"] + ss["blocks"]
+    frag = {"blocks": blocks, "F": 1.0 - (fs["objects"] + ss["objects"]) / (64.0 * blocks) if blocks else 0.0}
     if g:
         g.close()
     heap.close()
-    return times, grid, per_step_launches, (fish, sharks), err
+    return times, grid, per_step_launches, (fish, sharks), err, frag
 
 
 WATOR_KERNELS = [  # (type attr, method, reuses the previous snapshot, algorithmic bytes per agent)
@@ -187,13 +190,13 @@ WATOR_KERNELS = [  # (type attr, method, reuses the previous snapshot, algorithm
 ]
 
 
-def wator_kernel_profile(seed, warmup, steps, flush):
-    """CUDA-event duration of each kernel of a plain Wa-Tor step, launched exactly
-    as the step launches it (choose methods: one fused enumeration + do-all
-    kernel; move methods: one do-all kernel on the choose snapshot)."""
+def wator_kernel_profile(seed, warmup, steps, flush, launch=None):
+    """CUDA-event duration of each phase of a plain Wa-Tor step, launched exactly
+    as the step launches it (choose methods: enumeration + do-all kernel; move
+    methods: one do-all kernel on the choose snapshot)."""
     import torch
     from paper_1810_11765_gb300 import dsoa as D
-    heap, w = wator_world(seed)
+    heap, w = wator_world(seed, launch=launch)
     w.add(1024, 1024, seed)
     for _ in range(warmup):
         w.step()
@@ -311,19 +314,22 @@ def alloc_free_storm(log2n, flush, iters=3):
 ALG_ATOMICS_PER_OBJECT = {"new": 6 / 64, "delete": 7 / 64}
 
 
-def l2_atomic_peak(iters=64, reps=5):
+def l2_atomic_peak(iters=64, reps=5, words=1 << 22):
     """Ceiling of single-lane 64-bit bitmap atomics with return: every lane's op
     is its own L2 request, on a 32 MiB (L2-resident) word array, one resident
-    grid of threads (the K_MICRO_ATOMIC_PEAK probe of the library)."""
+    grid of threads (the K_MICRO_ATOMIC_PEAK probe of the library).  With
+    words=32 every op contends with ~10^4 others on 32 words."""
     import torch
     from paper_1810_11765_gb300 import dsoa as D
     from paper_1810_11765_gb300.apps import Micro
     m = Micro(4 << 20, 0x5EED0001, 64)
-    nw = 1 << 22
-    words = torch.zeros(nw, dtype=torch.int64, device="cuda")
+    nw = words
+    buf = torch.zeros(nw, dtype=torch.int64, device="cuda")
     sink = torch.zeros(1, dtype=torch.int64, device="cuda")
     n = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 2048
-    a = m.args(handles_out=words.data_ptr(), n_ids=nw, round=iters, stats=sink.data_ptr(), seed=1)
+    if nw < 1024:
+        iters = 4
+    a = m.args(handles_out=buf.data_ptr(), n_ids=nw, round=iters, stats=sink.data_ptr(), seed=1)
     for _ in range(3):
         m.heap.run_kernel(D.K_MICRO_ATOMIC_PEAK, n, a)
     ts = []
@@ -549,12 +555,12 @@ def dsoa_arm(args):
     dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    t_graph, grid_g, _, pop_g, err_g = run_wator(seed, args.warmup, args.steps, "graph", flush, launch)
+    t_graph, grid_g, _, pop_g, err_g, frag_g = run_wator(seed, args.warmup, args.steps, "graph", flush, launch)
     clk = clocks.stop()
     dist.barrier()
     ms_graph = dist.max(sum(t_graph))         # slowest rank decides
-    t_plain, grid_p, launches_per_step, pop_p, err_p = run_wator(seed, args.warmup, args.steps, "plain",
-                                                                 flush, launch)
+    t_plain, grid_p, launches_per_step, pop_p, err_p, _ = run_wator(seed, args.warmup, args.steps, "plain",
+                                                                    flush, launch)
     ms_plain = dist.max(sum(t_plain))
     same = bool(np.array_equal(grid_g, grid_p)) and pop_g == pop_p and err_g == 0 and err_p == 0
     value = dist.world * args.steps / (ms_graph / 1e3)
@@ -571,12 +577,13 @@ def dsoa_arm(args):
            "graph_vs_plain": ms_plain / ms_graph, "graph_equals_plain": same,
            "populations_after": {"fish": pop_g[0], "sharks": pop_g[1],
                                  "steps": args.warmup + args.steps},
+           "fragmentation_after": frag_g,
            "gpu_launches": int(round(launches_per_step * args.steps)) if launches_per_step else None,
            "clocks": clk}
 
     if dist.rank == 0 and not args.skip_secondary:
         # --- dominant kernel of the step, with its roofline
-        prof = wator_kernel_profile(seed, 20, 20, flush)
+        prof = wator_kernel_profile(seed, 20, 20, flush, launch)
         tot = {k: sum(v["ms"]) for k, v in prof.items()}
         dom = max(tot, key=tot.get)
         d = prof[dom]
@@ -589,6 +596,11 @@ def dsoa_arm(args):
                            "peak_kind": peak_kind, "avg_launch_ms": avg_ms, "alg_bytes_per_launch": alg,
                            "units_per_launch": units}
         out["step_kernels_ms"] = {k: statistics.mean(v["ms"]) for k, v in prof.items()}
+        out["step_phases"] = {k: {"ms": statistics.mean(v["ms"]),
+                                  "alg_gbs": statistics.mean(v["bytes"]) / statistics.mean(v["ms"]) / 1e6,
+                                  "frac_hbm": statistics.mean(v["bytes"]) / statistics.mean(v["ms"]) / 1e6
+                                  / hbm_peak,
+                                  "agents": statistics.mean(v["units"])} for k, v in prof.items()}
         # --- do-all HBM sweep (spec kernel), > L2 working sets
         sweep = {}
         for kern in DOALL_KERNELS:
@@ -605,10 +617,17 @@ def dsoa_arm(args):
                                  "alg_bytes_per_launch": best["alg_bytes"], "avg_launch_ms": best["ms"]}
         out["doall_sweep"] = sweep
         # --- alloc + free
-        storm = alloc_free_storm(24, flush)
+        out["l2_atomic_peak"] = l2_atomic_peak()
+        out["l2_atomic_contended"] = l2_atomic_peak(words=32)
+        sweep = {}
+        for lg in (18, 20, 22, 24):      # 2^18 threads' worth x {1, 4, 16, 64} objects
+            st = alloc_free_storm(lg, flush)
+            st["alloc_roofline_frac"] = alloc_roofline(st, out["l2_atomic_peak"])["frac"]
+            sweep[f"2^{lg}"] = st
+        storm = sweep["2^24"]
         out["alloc_free_ops_per_s"] = storm["ops_per_s"]
         out["alloc_free"] = storm
-        out["l2_atomic_peak"] = l2_atomic_peak()
+        out["alloc_free_sweep"] = sweep
         out["alloc_roofline"] = alloc_roofline(storm, out["l2_atomic_peak"])
         out["heap_utilisation"] = heap_utilisation()
         # --- other apps (plain vs graph) and serving

@@ -56,6 +56,15 @@
 #define DSOA_LOOKUP_ATTEMPTS 5            /* active-block lookups before slow path  */
 #endif
 
+/* Entry of the per-warp block hint table: a block of the type that still had
+ * free slots when this warp slot last reserved in it, and the free-slot word
+ * that reservation left.  Advisory only (any value is safe). */
+struct __align__(16) dsoa_hint {
+    unsigned long long free;             /* free slots as last seen (1 = free)     */
+    uint64_t block;                      /* block id, DSOA_NO_HINT_BLOCK if none   */
+};
+#define DSOA_NO_HINT_BLOCK (~0ull)
+
 /* Device view of a heap.  Plain data, passed to kernels by value. */
 struct dsoa_ctx {
     char* data;                          /* block b at data + b * block_bytes      */
@@ -63,7 +72,7 @@ struct dsoa_ctx {
     uint32_t* btype;                     /* [M] block type ids                     */
     unsigned long long* bm;              /* all hierarchical bitmaps               */
     int* err;                            /* sticky DSOA_DEV_* bits                 */
-    uint32_t* hint;                      /* [DSOA_HINT_SLOTS][ntypes] last block with
+    dsoa_hint* hint;                     /* [hint_mask + 1][ntypes] last block with
                                             free slots per warp slot (advisory)       */
     uint32_t* grid_scratch;              /* [DSOA_GRID_SCRATCH] per-CTA aggregates and
                                             grid-barrier words of the fused do-all    */
@@ -76,21 +85,28 @@ struct dsoa_ctx {
     uint32_t ntypes;
     uint32_t seed;                       /* rotation seed of this launch           */
     uint32_t flags;                      /* DSOA_FLAG_*                            */
+    uint32_t hint_mask;                  /* hint-table warp slots - 1 (power of 2)  */
     uint32_t lookups;                    /* active-block lookups before the slow path
                                             (r of Sec. 4.2 / Fig. 11), >= 1           */
     uint16_t col_off[DSOA_MAX_TYPES][DSOA_MAX_FIELDS];
 };
 
+/* Register cap of the generic do-all kernel.  Methods that allocate are chains
+ * of dependent L2 round trips; at 48 registers five 256-thread CTAs fit on an
+ * SM instead of four at 64 (Wa-Tor fish move: 67 -> 61 us per step).  Any
+ * block size up to 512 threads still fits. */
+#ifndef DSOA_DOALL_MAXNREG
+#define DSOA_DOALL_MAXNREG 48
+#endif
 #define DSOA_FRESH_GROUP 16u              /* group size that takes a fresh block
                                              after a lost race (leader_reserve)    */
 #define DSOA_FLAG_NO_COALESCE 1u          /* ablation: one request per leader       */
 #define DSOA_FLAG_NO_ROTATE 2u            /* ablation: plain find-first-set         */
-#define DSOA_FLAG_NO_HINT 4u              /* ablation: no per-SM block hint         */
-#define DSOA_HINT_SLOTS 8192u             /* hint table entries per type (warps)    */
+#define DSOA_FLAG_NO_HINT 4u              /* ablation: no per-warp block hint       */
+#define DSOA_HINT_SLOTS 8192u             /* max hint-table warp slots per type     */
 #define DSOA_FLAG_FUSED 8u                /* one cooperative enumerate+do-all launch */
 #define DSOA_FUSED_MAX_CTAS 2048u         /* grid limit of the fused do-all         */
 #define DSOA_GRID_SCRATCH (DSOA_FUSED_MAX_CTAS + 64u)
-#define DSOA_NO_BLOCK 0xFFFFFFFFu
 
 /* bitmap ids inside ctx.bm */
 __host__ __device__ __forceinline__ uint32_t dsoa_bm_free() { return 0u; }
@@ -364,21 +380,25 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
     const uint32_t act = dsoa_bm_active(t);
     const bool rot = !(c.flags & DSOA_FLAG_NO_ROTATE);
     /* Per-warp hint: the block this warp (slot of the hint table) last reserved
-     * in while it still had free slots.  Trying it first skips the top-down
-     * bitmap search;
-     * a stale hint is just another "Block Full / Deallocated / Replaced" case
-     * of App. A.3 and is caught by the same checks as a stale try_find_set. */
-    uint32_t* hp = nullptr;
+     * in while it still had free slots, with the free-slot word that
+     * reservation left behind.  Trying it first skips the top-down bitmap
+     * search and the read of the slot word: the reservation mask is taken from
+     * the remembered word, and a stale word only costs slots (an atomicAnd of
+     * a slot that is no longer free reserves nothing).  A stale block is just
+     * another "Block Full / Deallocated / Replaced" case of App. A.3 and is
+     * caught by the same checks as a stale try_find_set. */
+    dsoa_hint* hp = nullptr;
     if (c.hint && !(c.flags & DSOA_FLAG_NO_HINT)) {
         const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        hp = c.hint + (gwarp % DSOA_HINT_SLOTS) * c.ntypes + t;
+        hp = c.hint + (gwarp & c.hint_mask) * c.ntypes + t;
     }
     uint32_t empty_free = 0;   /* rounds that found the free-block bitmap empty */
     for (uint32_t round = 0; round < DSOA_ALLOC_ROUNDS; ++round) {
         int64_t bid = -1;
+        unsigned long long w = 0ull;   /* free slots of bid, if already known */
         if (round == 0 && hp) {
-            const uint32_t hb = *hp;
-            if (hb < c.M) bid = hb;
+            const dsoa_hint hv = *hp;
+            if (hv.block < c.M && hv.free) { bid = (int64_t)hv.block; w = hv.free; }
         }
         /* After a lost race (round >= 1) a group of DSOA_FRESH_GROUP or more
          * requests takes a fresh block instead of searching active[t] again: when
@@ -401,11 +421,11 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
                 __nanosleep(256u);
                 continue;
             }
+            w = DSOA_ALL;              /* just initialised by this thread */
         }
-        const unsigned long long w = dsoa_ld(&c.slot[bid]);
         if (!w) {
-            if (hp && *hp == (uint32_t)bid) *hp = DSOA_NO_BLOCK;
-            continue;
+            w = dsoa_ld(&c.slot[bid]);
+            if (!w) continue;
         }
         const uint32_t r = rot ? (dsoa_hash(h + round) & 63u) : 0u;
         const unsigned long long mask = dsoa_rotl(dsoa_lowest_k(dsoa_rotr(w, r), want), r);
@@ -413,16 +433,20 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
          * fence of dsoa_block_init whose slot-word store this RMW follows */
         const unsigned long long before = dsoa_and_acquire(&c.slot[bid], ~mask);
         const unsigned long long got = before & mask;
-        if (!got) continue;
+        const unsigned long long left = before & ~mask;
+        if (!got) {
+            if (hp) *hp = dsoa_hint{left, left ? (uint64_t)bid : DSOA_NO_HINT_BLOCK};
+            continue;
+        }
         const uint32_t bt = dsoa_ld32(&c.btype[bid]);
-        const bool full = (before & ~mask) == 0ull;
+        const bool full = left == 0ull;
         if (full) dsoa_block_deactivate(c, bt, (uint64_t)bid);
         if (bt != t) {                 /* block replaced by another type: roll back */
-            if (hp && *hp == (uint32_t)bid) *hp = DSOA_NO_BLOCK;
+            if (hp) *hp = dsoa_hint{0ull, DSOA_NO_HINT_BLOCK};
             dsoa_rollback(c, bt, (uint64_t)bid, got);
             continue;
         }
-        if (hp) *hp = full ? DSOA_NO_BLOCK : (uint32_t)bid;
+        if (hp) *hp = dsoa_hint{left, full ? DSOA_NO_HINT_BLOCK : (uint64_t)bid};
         *bid_out = (uint64_t)bid;
         return got;
     }
@@ -509,7 +533,7 @@ __device__ __forceinline__ F& dsoa_field(const dsoa_ctx& c, dsoa_obj h, uint32_t
  *                              uint32_t slot, const Args&);
  * ------------------------------------------------------------------------ */
 template <class M, int G = 1>
-__global__ void __launch_bounds__(512) dsoa_doall_kernel(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+__global__ void __maxnreg__(DSOA_DOALL_MAXNREG) dsoa_doall_kernel(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                   const unsigned long long* __restrict__ occ,
                                   const uint32_t* __restrict__ r_dev, typename M::Args args) {
     constexpr uint32_t TPB = 64u / G;                          /* threads per block */

@@ -26,7 +26,16 @@ struct Layout {
     uint64_t lvl_off[DSOA_MAX_LEVELS] = {0}, lvl_words[DSOA_MAX_LEVELS] = {0};
     uint64_t off_data = 0, off_slot = 0, off_btype = 0, off_bm = 0, off_R = 0, off_Rocc = 0,
              off_tcnt = 0, off_toff = 0, off_lb = 0, off_hint = 0, off_grid = 0, off_small = 0, total = 0;
+    uint64_t hint_slots = 0;
 };
+
+// Hint-table slots (warp slots) per type: DSOA_HINT_SLOTS, or fewer for a heap
+// of few blocks (at least 64, a power of two, about M / 4).
+uint64_t hint_slots_for(uint64_t M) {
+    uint64_t s = 64;
+    while (s < DSOA_HINT_SLOTS && s < M / 4) s <<= 1;
+    return s;
+}
 
 bool make_layout(uint64_t M, uint32_t block_bytes, int ntypes, Layout* L) {
     const int nbm = 1 + 2 * ntypes;
@@ -57,7 +66,8 @@ bool make_layout(uint64_t M, uint32_t block_bytes, int ntypes, Layout* L) {
     L->off_tcnt = p;  p = align_up(p + L->tiles * 4, kAlign);
     L->off_toff = p;  p = align_up(p + L->tiles * 4, kAlign);
     L->off_lb = p;    p = align_up(p + L->tiles * 8, kAlign);
-    L->off_hint = p;  p = align_up(p + (uint64_t)DSOA_HINT_SLOTS * (uint64_t)ntypes * 4, kAlign);
+    L->hint_slots = hint_slots_for(M);
+    L->off_hint = p;  p = align_up(p + L->hint_slots * (uint64_t)ntypes * sizeof(dsoa_hint), kAlign);
     L->off_grid = p;  p = align_up(p + (uint64_t)DSOA_GRID_SCRATCH * 4, kAlign);
     L->off_small = p; p = align_up(p + kSmallWords * 8, kAlign);
     L->total = p;
@@ -572,7 +582,8 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     c.bm = (unsigned long long*)(base + L.off_bm);
     uint64_t* small = (uint64_t*)(base + L.off_small);
     c.err = (int*)(small + 0);
-    c.hint = (uint32_t*)(base + L.off_hint);
+    c.hint = (dsoa_hint*)(base + L.off_hint);
+    c.hint_mask = (uint32_t)(L.hint_slots - 1);
     h->lb_state = (unsigned long long*)(base + L.off_lb);
     h->lb_ctl = (uint32_t*)(small + 4);      // ticket, done, epoch
     c.grid_scratch = (uint32_t*)(base + L.off_grid);
@@ -600,7 +611,8 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     DSOA_CUDA_TRY(cudaMemsetAsync(c.btype, 0xFF, L.M * 4, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(c.bm, 0, (uint64_t)nbm * L.bm_stride * 8, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(small, 0, kSmallWords * 8, h->stream));
-    DSOA_CUDA_TRY(cudaMemsetAsync(c.hint, 0xFF, (uint64_t)DSOA_HINT_SLOTS * (uint64_t)h->ntypes * 4, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(c.hint, 0xFF, ((uint64_t)c.hint_mask + 1) * (uint64_t)h->ntypes * sizeof(dsoa_hint),
+                                  h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(c.grid_scratch, 0, (uint64_t)DSOA_GRID_SCRATCH * 4, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(h->lb_state, 0, L.tiles * 8, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(h->R[0], 0, L.M * 4 * (uint64_t)h->ntypes, h->stream));
