@@ -426,20 +426,20 @@ def e2e_wator(seed, warmup, steps, flush):
             "ms": ms, "final_fish": int(counts_host[-2]), "final_sharks": int(counts_host[-1])}
 
 
-def app_steps(kind, steps, flush, warmup=3):
+def app_steps(kind, steps, flush, warmup=3, side=None, heap_bytes=1 << 30):
     """Steps/s of the other apps, graph-captured step vs plain launches (L2
-    flushed between timed steps)."""
+    flushed between timed steps).  `side` overrides the game-of-life torus side."""
     import torch
     from paper_1810_11765_gb300 import dsoa as D, inputs
     from paper_1810_11765_gb300.apps import GolWorld, TrafficWorld
     res = {}
     for mode in ("plain", "graph"):
-        heap = D.Heap(1 << 30)
+        heap = D.Heap(heap_bytes)
         if kind == "gol":
             cfg = inputs.GolConfig()
             w = GolWorld(heap)
             heap.freeze()
-            w.add(cfg.width, cfg.height, cfg.seed)
+            w.add(side or cfg.width, side or cfg.height, cfg.seed)
         else:
             L, thr = inputs.traffic_instances()
             w = TrafficWorld(heap, L, thr, inputs.SEED_TRAFFIC)
@@ -468,7 +468,8 @@ def app_steps(kind, steps, flush, warmup=3):
             g.close()
         heap.close()
     res["graph_vs_plain"] = res["graph_steps_per_s"] / res["plain_steps_per_s"]
-    res["workload"] = ("game of life 512x512 torus, density 1/4" if kind == "gol"
+    gs = side or 512
+    res["workload"] = (f"game of life {gs}x{gs} torus, density 1/4" if kind == "gol"
                        else "traffic: 64 Nagel-Schreckenberg rings, 2^12..2^20 cells")
     return res
 
@@ -632,6 +633,7 @@ def dsoa_arm(args):
         out["heap_utilisation"] = heap_utilisation()
         # --- other apps (plain vs graph) and serving
         out["gol_512"] = app_steps("gol", 100, flush)
+        out["gol_4096"] = app_steps("gol", 20, flush, side=4096)
         out["traffic_64_rings"] = app_steps("traffic", 50, flush)
         out["serving"] = serving_leg()
         # --- end to end through host buffers

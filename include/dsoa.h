@@ -177,12 +177,19 @@ int dsoa_graph_launch(dsoa_graph* g, void* stream);
 int dsoa_graph_destroy(dsoa_graph* g);
 
 /* Launch shape of do-all and scan kernels (0 keeps the current value):
- * threads per CTA of the do-all (multiple of 64, at most 512), CTAs per SM of the persistent
- * do-all grid, slots handled per thread by vectorised methods (1, 2 or 4), and
- * the enumeration: 1 or 2 = tile-count kernel + compaction kernel with that many
- * level-1 tiles per CTA, 3 = single-pass decoupled look-back kernel (default). */
+ * threads per CTA of the do-all (multiple of 64, at most 512; default 256), CTAs
+ * per SM of the resident do-all grid (1..32, capped by what fits; default 8),
+ * slots handled per thread (1 or 2 for method do-alls, 1, 2 or 4 for vectorised
+ * ones), the enumeration (1 or 2 = tile-count kernel + compaction kernel with
+ * that many level-1 tiles per CTA, 3 = single-pass decoupled look-back kernel,
+ * the default), and the waves of the method do-all grid (1..DSOA_MAX_WAVES, default
+ * 4): its grid is `waves` times the resident grid, so that SMs that finish their
+ * share early take over the rest (streaming do-alls keep one resident wave).
+ * Returns DSOA_ERR_INVALID_ARG at the first value out of range (the values before
+ * it in the argument list are applied). */
+#define DSOA_MAX_WAVES 16
 int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
-                    int slots_per_thread, int scan_tiles_per_cta);
+                    int slots_per_thread, int scan_tiles_per_cta, int doall_waves);
 
 /* Ablation switches of Sec. 6.4 (Fig. 10c): DSOA_FLAG_NO_COALESCE (1) turns
  * off allocation request coalescing, DSOA_FLAG_NO_ROTATE (2) turns off bitmap

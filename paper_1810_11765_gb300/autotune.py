@@ -1,7 +1,8 @@
 """Launch-shape autotuner for graph-captured step loops.
 
-Searches do-all threads per CTA, persistent CTAs per SM, slots per thread (one block
-per 64 threads, or one block per warp) and the compaction kernel's tiles per CTA.
+Searches do-all threads per CTA, slots per thread (one block per 64 threads, or one
+block per warp), the enumeration (two kernels, or the single-pass look-back kernel)
+and the waves of the method do-all grid; the fused cooperative do-all is tried once.
 Each candidate runs a fresh world from the same seed, captures one step as a CUDA
 graph and times replays with CUDA events (L2 flushed between replays, as in the
 benchmark).  Results are cached per GPU name and workload in ``_tune/``.
@@ -21,9 +22,9 @@ from .apps import WatorWorld
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_DIR = os.path.join(HERE, "_tune")
 
-CANDIDATES = [dict(tpb=tpb, ctas_per_sm=ctas, slots_per_thread=spt, scan_tiles=scan, fused=fused)
-              for tpb, ctas, spt, scan, fused in itertools.product((128, 256, 512), (2, 4, 8), (1, 2), (1, 3), (0, 1))
-              if tpb * ctas <= 4096]
+CANDIDATES = [dict(tpb=tpb, ctas_per_sm=8, slots_per_thread=spt, scan_tiles=scan, waves=waves, fused=0)
+              for tpb, spt, scan, waves in itertools.product((128, 256, 512), (1, 2), (1, 3), (1, 2, 4, 8))]
+CANDIDATES.append(dict(tpb=256, ctas_per_sm=8, slots_per_thread=1, scan_tiles=3, waves=1, fused=1))
 
 
 def apply(heap: D.Heap, launch: dict):
@@ -67,7 +68,7 @@ def time_wator_step(seed: int, launch: dict, side: int = 1024, warmup: int = 5, 
 
 
 def best_wator_launch(seed: int, use_cache: bool = True, verbose: bool = False) -> dict:
-    path = _cache_path("wator1024-v3")
+    path = _cache_path("wator1024-v4")
     if use_cache and os.path.exists(path):
         with open(path) as f:
             return json.load(f)["best"]

@@ -49,6 +49,7 @@ struct dsoa_heap {
     // launch shapes
     int doall_tpb = 256;
     int doall_ctas_per_sm = 8;
+    int doall_waves = 4;             // generic do-all grid = resident CTAs x waves
     int slots_per_thread = 1;        // generic do-all: 1 (64 threads/block) or 2 (a warp/block);
                                      // vectorised microbench kernel: 1, 2 or 4
     int vec_slots_per_thread = 4;    // vectorised kernels: slots per thread (1, 2 or 4)
@@ -107,6 +108,15 @@ unsigned dsoa_persistent_grid(dsoa_heap* h, K* kernel, int tpb) {
     return (unsigned)(per_sm * h->num_sms);
 }
 
+// Grid of the generic (method) do-all: `doall_waves` times the resident grid.
+// Methods differ in work per object (allocation, conflicts), so with one
+// resident wave the slowest warps set the kernel's duration; several waves let
+// the CTA scheduler hand the remaining work to SMs that finished early.
+template <typename K>
+unsigned dsoa_doall_grid(dsoa_heap* h, K* kernel, int tpb) {
+    return dsoa_persistent_grid(h, kernel, tpb) * (unsigned)h->doall_waves;
+}
+
 // Cooperative launch (every CTA co-resident) of a kernel that uses grid barriers.
 template <typename... KArgs, typename... Args>
 cudaError_t dsoa_launch_cooperative(void (*kernel)(KArgs...), unsigned grid, unsigned tpb, cudaStream_t s,
@@ -152,11 +162,11 @@ int dsoa_run_doall(dsoa_heap* h, int type, const typename M::Args& args) {
     const int tpb = h->doall_tpb;
     if (h->slots_per_thread >= 2) {
         auto* k = &dsoa_doall_kernel<M, 2>;
-        k<<<dsoa_persistent_grid(h, k, tpb), tpb, 0, h->stream>>>(
+        k<<<dsoa_doall_grid(h, k, tpb), tpb, 0, h->stream>>>(
             dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], args);
     } else {
         auto* k = &dsoa_doall_kernel<M, 1>;
-        k<<<dsoa_persistent_grid(h, k, tpb), tpb, 0, h->stream>>>(
+        k<<<dsoa_doall_grid(h, k, tpb), tpb, 0, h->stream>>>(
             dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], args);
     }
     return dsoa_check_launch(h);

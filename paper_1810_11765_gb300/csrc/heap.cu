@@ -821,7 +821,7 @@ int dsoa_graph_destroy(dsoa_graph* g) {
     return DSOA_OK;
 }
 
-int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread, int scan_tiles) {
+int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread, int scan_tiles, int waves) {
     if (!h) return DSOA_ERR_INVALID_ARG;
     if (tpb) {
         if (tpb < 64 || tpb > 512 || tpb % 64) return DSOA_ERR_INVALID_ARG;
@@ -839,6 +839,10 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
     if (scan_tiles) {
         if (scan_tiles < 1 || scan_tiles > 3) return DSOA_ERR_INVALID_ARG;
         h->scan_tiles_per_cta = scan_tiles == 3 ? 0 : scan_tiles;   // 3 = single-pass look-back
+    }
+    if (waves) {
+        if (waves < 1 || waves > DSOA_MAX_WAVES) return DSOA_ERR_INVALID_ARG;
+        h->doall_waves = waves;
     }
     return DSOA_OK;
 }

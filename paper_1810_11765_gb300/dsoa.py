@@ -119,7 +119,7 @@ def load(path: str | None = None):
         "dsoa_free_blocks_async": [vp, vp], "dsoa_get_error": [vp, vp], "dsoa_check": [vp, vp],
         "dsoa_export_state": [vp, vp, sz, vp, vp], "dsoa_get_ctx": [vp, vp, sz],
         "dsoa_graph_begin": [vp], "dsoa_graph_end": [vp, vp], "dsoa_graph_launch": [vp, vp],
-        "dsoa_graph_destroy": [vp], "dsoa_set_launch": [vp, i32, i32, i32, i32],
+        "dsoa_graph_destroy": [vp], "dsoa_set_launch": [vp, i32, i32, i32, i32, i32],
         "dsoa_set_flags": [vp, u32], "dsoa_launch_count": [vp, vp], "dsoa_heap_destroy": [vp],
         "dsoa_set_lookups": [vp, i32], "dsoa_type_stats": [vp, i32, vp],
         "dsoa_error_string": [i32],
@@ -285,8 +285,9 @@ class Heap:
         bm = buf[M * 12:].view(np.uint64).reshape(-1, words.value)
         return {"slot": slot, "btype": btype, "bitmaps": bm}
 
-    def set_launch(self, tpb=0, ctas_per_sm=0, slots_per_thread=0, scan_tiles=0):
-        _ok(load().dsoa_set_launch(self._h, tpb, ctas_per_sm, slots_per_thread, scan_tiles), "dsoa_set_launch")
+    def set_launch(self, tpb=0, ctas_per_sm=0, slots_per_thread=0, scan_tiles=0, waves=0):
+        _ok(load().dsoa_set_launch(self._h, tpb, ctas_per_sm, slots_per_thread, scan_tiles, waves),
+            "dsoa_set_launch")
 
     def set_flags(self, flags: int):
         _ok(load().dsoa_set_flags(self._h, flags), "dsoa_set_flags")

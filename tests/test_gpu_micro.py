@@ -124,12 +124,12 @@ def test_ablations_keep_semantics(flags):
         assert_clean(m)
 
 
-@pytest.mark.parametrize("tpb,ctas,scan", [(64, 1, 1), (128, 4, 2), (512, 2, 1), (512, 8, 2), (256, 8, 3),
-                                           (64, 2, 3)])
-def test_launch_shapes_keep_semantics(tpb, ctas, scan):
+@pytest.mark.parametrize("tpb,ctas,scan,waves", [(64, 1, 1, 1), (128, 4, 2, 2), (512, 2, 1, 4), (512, 8, 2, 16),
+                                                 (256, 8, 3, 4), (64, 2, 3, 8)])
+def test_launch_shapes_keep_semantics(tpb, ctas, scan, waves):
     n, rounds = 30000, 3
     ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
-    m = make(heap_bytes=16 << 20, n=n, tpb=tpb, ctas_per_sm=ctas, scan_tiles=scan)
+    m = make(heap_bytes=16 << 20, n=n, tpb=tpb, ctas_per_sm=ctas, scan_tiles=scan, waves=waves)
     for r in range(rounds):
         m.round(r)
         compare_round(m.stats(), ref[r])
@@ -169,7 +169,8 @@ def test_out_of_memory_is_reported_not_hung():
 def test_launch_shape_bounds():
     from paper_1810_11765_gb300 import dsoa as D
     m = make(heap_bytes=4 << 20, n=10)
-    for bad in (dict(tpb=1024), dict(tpb=96), dict(ctas_per_sm=64), dict(slots_per_thread=3)):
+    for bad in (dict(tpb=1024), dict(tpb=96), dict(ctas_per_sm=64), dict(slots_per_thread=3), dict(waves=17),
+                dict(waves=-1)):
         with pytest.raises(D.DsoaError):
             m.heap.set_launch(**bad)
 
