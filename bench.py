@@ -18,6 +18,7 @@ oracle timed on the host cores.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -429,10 +430,11 @@ def e2e_wator(seed, warmup, steps, flush):
 def app_steps(kind, steps, flush, warmup=3, side=None, heap_bytes=1 << 30):
     """Steps/s of the other apps, graph-captured step vs plain launches (L2
     flushed between timed steps).  `side` overrides the game-of-life torus side."""
+    import numpy as np
     import torch
     from paper_1810_11765_gb300 import dsoa as D, inputs
     from paper_1810_11765_gb300.apps import GolWorld, TrafficWorld
-    res = {}
+    res, finals = {}, {}
     for mode in ("plain", "graph"):
         heap = D.Heap(heap_bytes)
         if kind == "gol":
@@ -464,10 +466,13 @@ def app_steps(kind, steps, flush, warmup=3, side=None, heap_bytes=1 << 30):
             times.append(a.elapsed_time(b))
         res[f"{mode}_steps_per_s"] = steps / (sum(times) / 1e3)
         res["device_errors"] = heap.get_error()
+        state = w.read(0) if kind == "gol" else np.concatenate(w.read())
+        finals[mode] = hashlib.sha256(np.ascontiguousarray(state).tobytes()).hexdigest()
         if g:
             g.close()
         heap.close()
     res["graph_vs_plain"] = res["graph_steps_per_s"] / res["plain_steps_per_s"]
+    res["graph_equals_plain"] = finals["graph"] == finals["plain"]
     gs = side or 512
     res["workload"] = (f"game of life {gs}x{gs} torus, density 1/4" if kind == "gol"
                        else "traffic: 64 Nagel-Schreckenberg rings, 2^12..2^20 cells")

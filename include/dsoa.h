@@ -182,7 +182,9 @@ int dsoa_graph_destroy(dsoa_graph* g);
  * slots handled per thread (1 or 2 for method do-alls, 1, 2 or 4 for vectorised
  * ones), the enumeration (1 or 2 = tile-count kernel + compaction kernel with
  * that many level-1 tiles per CTA, 3 = single-pass decoupled look-back kernel,
- * the default), and the waves of the method do-all grid (1..DSOA_MAX_WAVES, default
+ * the default, 4 = as 3, but methods that create no objects of their own type
+ * enumerate inside their own kernel, tile by tile), and the waves of the
+ * method do-all grid (1..DSOA_MAX_WAVES, default
  * 4): its grid is `waves` times the resident grid, so that SMs that finish their
  * share early take over the rest (streaming do-alls keep one resident wave).
  * Returns DSOA_ERR_INVALID_ARG at the first value out of range (the values before

@@ -553,6 +553,107 @@ __global__ void __maxnreg__(DSOA_DOALL_MAXNREG) dsoa_doall_kernel(dsoa_ctx c, ui
     }
 }
 
+/* ------------------------------------------------------------------------
+ * Streamed do-all: the enumeration of Sec. 3.7 done inside the method kernel.
+ * The snapshot of a block only has to be taken before that block's objects
+ * run, so a method that never creates objects of its own type (it may delete
+ * `this`, and create or delete objects of other types) can enumerate and run
+ * tile by tile: each CTA takes tiles of DSOA_STREAM_TILE_WORDS level-0 words
+ * of allocated[t] by ticket, stages the tile's block ids and free-slot words
+ * (its part of the snapshot) in shared memory, appends them to R / the
+ * snapshot at a position reserved with one atomicAdd, and runs the method on
+ * them.  R is not sorted (nothing depends on its order, Sec. 4.1.5 only needs
+ * a list).  An object is visited only by the CTA holding its tile, so a
+ * deletion of `this` cannot race with the snapshot of another tile.
+ * ctl = {ticket, finished CTAs, length of R}: the last CTA to finish writes r
+ * and resets ctl, so a replayed graph starts from zero.  No waits.
+ * A method opts in with  static constexpr bool kNoNewOfOwnType = true;
+ * ------------------------------------------------------------------------ */
+#define DSOA_STREAM_TILE_WORDS 8u               /* 512 blocks per tile */
+
+template <class M, class = void>
+struct dsoa_streamable { static constexpr bool value = false; };
+template <class M>
+struct dsoa_streamable<M, decltype((void)M::kNoNewOfOwnType, void())> {
+    static constexpr bool value = M::kNoNewOfOwnType;
+};
+
+template <class M, int G = 1>
+__global__ void __maxnreg__(DSOA_DOALL_MAXNREG) dsoa_doall_stream_kernel(dsoa_ctx c, uint32_t t,
+                                  uint32_t* __restrict__ R, unsigned long long* __restrict__ occ,
+                                  uint32_t* __restrict__ r_dev, uint32_t* __restrict__ ctl,
+                                  typename M::Args args) {
+    constexpr uint32_t TW = DSOA_STREAM_TILE_WORDS, TB = 64u * TW;
+    constexpr uint32_t TPB = 64u / G;                          /* threads per block */
+    __shared__ uint32_t s_list[TB];
+    __shared__ unsigned long long s_occ[TB];
+    __shared__ unsigned long long s_word[TW];
+    __shared__ uint32_t s_off[TW + 1];
+    __shared__ uint32_t s_tile, s_base;
+    const uint32_t b = dsoa_bm_alloc(t);
+    const uint64_t w0 = c.lvl_words[0];
+    const uint64_t ntiles = (w0 + TW - 1) / TW;
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, b, 1) : nullptr;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t grp = tid / TPB, ngrp = blockDim.x / TPB, s0 = tid % TPB;
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(&ctl[0], 1u);
+        __syncthreads();
+        const uint64_t q = s_tile;
+        if (q >= ntiles) break;                                 /* uniform */
+        if (tid < TW) {
+            const uint64_t wi = q * TW + tid;
+            unsigned long long w = 0ull;
+            if (wi < w0 && (!L1 || ((dsoa_ld(&L1[wi >> 6]) >> (wi & 63u)) & 1ull))) w = dsoa_ld(&L0[wi]);
+            s_word[tid] = w;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t acc = 0;
+            for (uint32_t k = 0; k < TW; ++k) { s_off[k] = acc; acc += (uint32_t)__popcll(s_word[k]); }
+            s_off[TW] = acc;
+            if (acc) s_base = atomicAdd(&ctl[2], acc);
+        }
+        __syncthreads();
+        const uint32_t n = s_off[TW];
+        for (uint32_t k = tid; k < TB; k += blockDim.x) {     /* stage the tile's part of the snapshot */
+            const unsigned long long w = s_word[k >> 6];
+            const uint32_t bit = k & 63u;
+            if ((w >> bit) & 1ull) {
+                const uint32_t pos = s_off[k >> 6] + (uint32_t)__popcll(w & ((1ull << bit) - 1ull));
+                const uint32_t bid = (uint32_t)(q * TB + k);
+                const unsigned long long o = ~dsoa_ld(&c.slot[bid]);
+                s_list[pos] = bid;
+                s_occ[pos] = o;
+                R[s_base + pos] = bid;
+                occ[s_base + pos] = o;
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = grp; i < n; i += ngrp) {
+            const uint64_t bid = s_list[i];
+            const unsigned long long o = s_occ[i];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const uint32_t s = s0 + (uint32_t)k * TPB;
+                if ((o >> s) & 1ull) M::run(c, t, bid, s, args);
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&ctl[1], 1u) == gridDim.x - 1u) {      /* last CTA: publish r, reset */
+            __threadfence();
+            *r_dev = dsoa_ld32(&ctl[2]);
+            dsoa_st32(&ctl[0], 0u);
+            dsoa_st32(&ctl[2], 0u);
+            dsoa_st32(&ctl[1], 0u);
+        }
+    }
+}
+
 /* device_do<T, f> (Sec. 2.1): run f(handle) on every object of type t, one
  * after another, in the calling thread -- the sequential for-each that n-body
  * style methods use to visit all pairs.  Walks the allocated-block bitmap of t

@@ -54,6 +54,8 @@ struct dsoa_heap {
                                      // vectorised microbench kernel: 1, 2 or 4
     int vec_slots_per_thread = 4;    // vectorised kernels: slots per thread (1, 2 or 4)
     int scan_tiles_per_cta = 0;      // 0 = single-pass look-back; 1, 2 = tile-count + compaction kernels
+    bool stream_enum = false;        // enumerate inside methods that create no objects of their own type
+    uint32_t* stream_ctl = nullptr;  // ticket, finished CTAs, R length of the streamed do-all
     unsigned long long* lb_state = nullptr;  // [tiles] look-back state words (epoch, status, value)
     uint32_t* lb_ctl = nullptr;              // ticket, done counter, epoch of the look-back kernel
 
@@ -156,6 +158,27 @@ int dsoa_run_doall(dsoa_heap* h, int type, const typename M::Args& args) {
         if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
         return h->slots_per_thread >= 2 ? dsoa_run_doall_fused<M, 2>(h, type, args)
                                         : dsoa_run_doall_fused<M, 1>(h, type, args);
+    }
+    if constexpr (dsoa_streamable<M>::value) {
+        if (!h->skip_enumeration && h->stream_enum) {
+            if (!h->frozen) return DSOA_ERR_NOT_FROZEN;
+            if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+            const int tpb = h->doall_tpb;
+            if (h->slots_per_thread >= 2) {
+                auto* k = &dsoa_doall_stream_kernel<M, 2>;
+                k<<<dsoa_persistent_grid(h, k, tpb), tpb, 0, h->stream>>>(
+                    dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], h->stream_ctl,
+                    args);
+            } else {
+                auto* k = &dsoa_doall_stream_kernel<M, 1>;
+                k<<<dsoa_persistent_grid(h, k, tpb), tpb, 0, h->stream>>>(
+                    dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], h->stream_ctl,
+                    args);
+            }
+            const int rc = dsoa_check_launch(h);
+            if (rc == DSOA_OK) h->enumerated[type] = true;
+            return rc;
+        }
     }
     int rc = dsoa_prepare_doall(h, type);
     if (rc) return rc;

@@ -40,6 +40,7 @@ struct CellCtor {
 // Alive.spread: one atomic increment of each of the 8 neighbours' counts.
 struct Spread {
     using Args = dsoa_gol_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
         const dsoa_inst I = a.inst[k];
@@ -60,6 +61,7 @@ struct Spread {
 // cell dies and the agent deletes itself.
 struct Reap {
     using Args = dsoa_gol_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
         const dsoa_inst& I = a.inst[k];
@@ -78,6 +80,7 @@ struct Reap {
 // Cell.decide: a dead cell with exactly 3 live neighbours is born (new Alive).
 struct Decide {
     using Args = dsoa_gol_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
         if (a.inst[k].state != DSOA_INST_RUN) return;
@@ -97,6 +100,7 @@ struct Decide {
 
 struct Read {
     using Args = dsoa_gol_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
         uint8_t* occ = a.inst[k].occ;
@@ -106,6 +110,7 @@ struct Read {
 
 struct Kill {
     using Args = dsoa_gol_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
         if (a.inst[k].state == DSOA_INST_KILL) dsoa_delete(c, dsoa_make_handle(t, bid, s));

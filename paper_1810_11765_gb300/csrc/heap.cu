@@ -589,6 +589,7 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     c.grid_scratch = (uint32_t*)(base + L.off_grid);
     h->done = (uint32_t*)(small + 1);
     h->scratch64 = (unsigned long long*)(small + 32);
+    h->stream_ctl = (uint32_t*)(small + 44);  // [3] of the streamed do-all
     c.M = L.M;
     c.bm_stride = L.bm_stride;
     for (int l = 0; l < DSOA_MAX_LEVELS; ++l) { c.lvl_off[l] = L.lvl_off[l]; c.lvl_words[l] = L.lvl_words[l]; }
@@ -837,8 +838,9 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
         h->vec_slots_per_thread = slots_per_thread;
     }
     if (scan_tiles) {
-        if (scan_tiles < 1 || scan_tiles > 3) return DSOA_ERR_INVALID_ARG;
-        h->scan_tiles_per_cta = scan_tiles == 3 ? 0 : scan_tiles;   // 3 = single-pass look-back
+        if (scan_tiles < 1 || scan_tiles > 4) return DSOA_ERR_INVALID_ARG;
+        h->scan_tiles_per_cta = scan_tiles >= 3 ? 0 : scan_tiles;   // 3, 4 = single-pass look-back
+        h->stream_enum = scan_tiles == 4;                           // 4 = + streamed do-alls
     }
     if (waves) {
         if (waves < 1 || waves > DSOA_MAX_WAVES) return DSOA_ERR_INVALID_ARG;

@@ -25,6 +25,7 @@ __device__ __forceinline__ float micro_update(float x, int32_t id) {
 
 struct MicroScale {
     using Args = dsoa_micro_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args&) {
         const int32_t id = dsoa_column<int32_t>(c, t, bid, 0)[s];
         float* x = dsoa_column<float>(c, t, bid, 1) + s;
@@ -34,6 +35,7 @@ struct MicroScale {
 
 struct MicroDelete {
     using Args = dsoa_micro_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t id = (uint32_t)dsoa_column<int32_t>(c, t, bid, 0)[s];
         if (dsoa_sm3(a.seed, id, a.round) & 1ull) dsoa_delete(c, dsoa_make_handle(t, bid, s));
@@ -42,6 +44,7 @@ struct MicroDelete {
 
 struct MicroDeleteAll {
     using Args = dsoa_micro_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args&) {
         dsoa_delete(c, dsoa_make_handle(t, bid, s));
     }
@@ -49,6 +52,7 @@ struct MicroDeleteAll {
 
 struct MicroHandles {
     using Args = dsoa_micro_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t id = (uint32_t)dsoa_column<int32_t>(c, t, bid, 0)[s];
         if (id < a.n_ids) a.handles_out[id] = dsoa_make_handle(t, bid, s);
@@ -57,6 +61,7 @@ struct MicroHandles {
 
 struct MicroGather {
     using Args = dsoa_micro_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t id = (uint32_t)dsoa_column<int32_t>(c, t, bid, 0)[s];
         if (id < a.n_ids) {

@@ -21,6 +21,7 @@ __device__ __forceinline__ uint32_t ring_of(const uint64_t* base, uint32_t n, ui
 
 struct Move {
     using Args = dsoa_traffic_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t step = *a.t_dev;
         const uint8_t* cur = (step & 1u) ? a.occ1 : a.occ0;
@@ -50,6 +51,7 @@ struct Move {
 
 struct Read {
     using Args = dsoa_traffic_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t i = dsoa_column<uint32_t>(c, t, bid, 0)[s];
         a.vel_out[a.ring_base[i] + dsoa_column<uint32_t>(c, t, bid, 1)[s]] =

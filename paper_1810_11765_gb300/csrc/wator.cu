@@ -33,6 +33,7 @@ __device__ __forceinline__ void neighbours(uint32_t c, uint32_t w, uint32_t h, u
 
 struct FishChoose {
     using Args = dsoa_wator_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const dsoa_inst I = a.inst[dsoa_column<uint32_t>(c, t, bid, 0)[s]];
         if (I.state != DSOA_INST_RUN) return;
@@ -86,6 +87,7 @@ struct FishMove {
 
 struct SharkChoose {
     using Args = dsoa_wator_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const dsoa_inst I = a.inst[dsoa_column<uint32_t>(c, t, bid, 0)[s]];
         if (I.state != DSOA_INST_RUN) return;
@@ -171,6 +173,7 @@ struct SharkMove {
 
 struct Kill {
     using Args = dsoa_wator_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
         if (a.inst[k].state == DSOA_INST_KILL) dsoa_delete(c, dsoa_make_handle(t, bid, s));

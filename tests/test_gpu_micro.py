@@ -125,7 +125,7 @@ def test_ablations_keep_semantics(flags):
 
 
 @pytest.mark.parametrize("tpb,ctas,scan,waves", [(64, 1, 1, 1), (128, 4, 2, 2), (512, 2, 1, 4), (512, 8, 2, 16),
-                                                 (256, 8, 3, 4), (64, 2, 3, 8)])
+                                                 (256, 8, 3, 4), (64, 2, 3, 8), (128, 8, 4, 1), (512, 1, 4, 2)])
 def test_launch_shapes_keep_semantics(tpb, ctas, scan, waves):
     n, rounds = 30000, 3
     ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
@@ -170,7 +170,7 @@ def test_launch_shape_bounds():
     from paper_1810_11765_gb300 import dsoa as D
     m = make(heap_bytes=4 << 20, n=10)
     for bad in (dict(tpb=1024), dict(tpb=96), dict(ctas_per_sm=64), dict(slots_per_thread=3), dict(waves=17),
-                dict(waves=-1)):
+                dict(waves=-1), dict(scan_tiles=5)):
         with pytest.raises(D.DsoaError):
             m.heap.set_launch(**bad)
 

@@ -110,10 +110,11 @@ def test_graph_captured_steps_match_oracle(launch, flags):
     g.close()
 
 
-@pytest.mark.parametrize("scan", [1, 2, 3])
+@pytest.mark.parametrize("scan", [1, 2, 3, 4])
 def test_enumeration_modes_agree(scan):
-    """Tile-count + compaction kernels (1 or 2 tiles per CTA) and the single-pass
-    look-back kernel give the same block list, hence the same simulation."""
+    """Tile-count + compaction kernels (1 or 2 tiles per CTA), the single-pass
+    look-back kernel and the streamed enumeration inside the choose methods give
+    the same snapshots, hence the same simulation."""
     heap, w = world(32 << 20)
     heap.set_launch(scan_tiles=scan)
     s = w.add(160, 120, 55)
