@@ -58,6 +58,7 @@ struct dsoa_heap {
     uint32_t* stream_ctl = nullptr;  // ticket, finished CTAs, R length of the streamed do-all
     unsigned long long* lb_state = nullptr;  // [tiles] look-back state words (epoch, status, value)
     uint32_t* lb_ctl = nullptr;              // ticket, done counter, epoch of the look-back kernel
+    int lb_fits = -1;                        // 1: every look-back CTA resident at once (tile = blockIdx)
 
     uint32_t flags = 0;              // DSOA_FLAG_* applied to every launch
     uint32_t lookups = DSOA_LOOKUP_ATTEMPTS;  // r: active-block lookups before the slow path

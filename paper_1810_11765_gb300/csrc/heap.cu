@@ -190,14 +190,22 @@ __global__ void __launch_bounds__(64 * TPC) k_compact(dsoa_ctx c, uint32_t b, ui
 }
 
 // Single-pass enumeration (decoupled look-back, Merrill & Garland 2016): one
-// 64-thread CTA per level-1 tile.  A CTA takes its tile from a ticket counter
-// (so it only waits on tiles taken by CTAs that already run), publishes the
-// tile's aggregate, lets warp 0 walk back over its predecessors' published
-// aggregates / inclusive prefixes 32 at a time, publishes its own inclusive
-// prefix, and writes R and the occupancy snapshot of the tile.  State words
-// carry the enumeration's epoch, so nothing is reset between launches (safe
-// in graph replays); the last CTA to finish advances the epoch and resets the
-// ticket.  Every wait is bounded (DSOA_DEV_SPIN).
+// 64-thread CTA per level-1 tile (64 level-0 words).  The CTA reads its tile's
+// level-0 words (the enumeration runs between kernels, when a level-0 word is
+// non-zero iff its level-1 bit is set, so the level-1 word need not be read
+// first), publishes the tile's aggregate, and then warp 0 walks back over its
+// predecessors' published aggregates / inclusive prefixes 32 at a time while
+// warp 1 reads the tile's free-slot words (the snapshot, up to 2048 of them)
+// into shared memory.
+// The CTA publishes its inclusive prefix and writes R and the snapshot.
+// Tile order: when every tile's CTA fits on the GPU at once, the tile is
+// blockIdx.x (CTAs are dispatched in index order, so a CTA only waits on
+// tiles of CTAs that already run); otherwise a ticket counter hands tiles out
+// in the order the CTAs start.  State words carry the enumeration's epoch, so
+// nothing is reset between launches (safe in graph replays); the last CTA to
+// finish advances the epoch and resets the ticket.  A published value is only
+// ever read as itself, so no fence precedes it.  Every wait is bounded
+// (DSOA_DEV_SPIN).
 constexpr unsigned long long kLbA = 1ull, kLbP = 2ull;
 __device__ __forceinline__ unsigned long long lb_word(uint32_t ep, unsigned long long st, unsigned long long v) {
     return ((unsigned long long)(ep & 0xFFFFFFu) << 40) | (st << 38) | (v & ((1ull << 38) - 1ull));
@@ -207,8 +215,10 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint32_t b, ui
                                                       unsigned long long* __restrict__ state,
                                                       uint32_t* __restrict__ ctl, uint32_t* __restrict__ R,
                                                       unsigned long long* __restrict__ Rocc,
-                                                      uint32_t* __restrict__ r_dev) {
+                                                      uint32_t* __restrict__ r_dev, uint32_t use_ticket) {
     __shared__ uint32_t list[4096];
+    constexpr uint32_t kSnap = 2048;                 /* snapshot words staged by warp 1 */
+    __shared__ unsigned long long snap[kSnap];
     __shared__ uint32_t wsum[2];
     __shared__ uint32_t s_tile, s_ep;
     __shared__ unsigned long long s_prefix;
@@ -216,17 +226,26 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint32_t b, ui
     uint32_t* done = ctl + 1;
     uint32_t* epoch = ctl + 2;
     const uint32_t j = threadIdx.x, lane = j & 31u;
-    if (j == 0) {
-        s_tile = atomicAdd(ticket, 1u);
-        s_ep = dsoa_ld32(epoch) + 1u;
-    }
-    __syncthreads();
-    const uint64_t t = s_tile;
-    const uint32_t ep = s_ep;
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    const uint64_t w0 = c.lvl_words[0];
+    uint64_t t;
     unsigned long long w = 0ull;
-    const unsigned long long sel = c.nlevels >= 2 ? dsoa_level(c, b, 1)[t] : 1ull;
+    if (use_ticket) {
+        if (j == 0) {
+            s_tile = atomicAdd(ticket, 1u);
+            s_ep = dsoa_ld32(epoch) + 1u;
+        }
+        __syncthreads();
+        t = s_tile;
+        if (t * 64 + j < w0) w = L0[t * 64 + j];
+    } else {
+        t = blockIdx.x;
+        if (t * 64 + j < w0) w = L0[t * 64 + j];              /* in flight with the epoch read */
+        if (j == 0) s_ep = dsoa_ld32(epoch) + 1u;
+        __syncthreads();
+    }
+    const uint32_t ep = s_ep;
     const uint64_t wi = t * 64 + j;
-    if (((sel >> j) & 1ull) && wi < c.lvl_words[0]) w = dsoa_level(c, b, 0)[wi];
     const uint32_t cnt = __popcll(w);
     uint32_t incl = cnt;
     for (int o = 1; o < 32; o <<= 1) {
@@ -237,10 +256,7 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint32_t b, ui
     __syncthreads();
     const uint32_t total = wsum[0] + wsum[1];
     /* publish this tile's aggregate (or its prefix, for tile 0) as early as possible */
-    if (j == 0) {
-        __threadfence();
-        dsoa_st(&state[t], lb_word(ep, t == 0 ? kLbP : kLbA, total));
-    }
+    if (j == 0) dsoa_st(&state[t], lb_word(ep, t == 0 ? kLbP : kLbA, total));
     /* stage this tile's block ids */
     {
         uint32_t k = incl - cnt + ((j >= 32) ? wsum[0] : 0u);
@@ -248,8 +264,9 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint32_t b, ui
         for (unsigned long long x = w; x; x &= x - 1ull)
             list[k++] = (uint32_t)(bid0 + (uint32_t)(__ffsll((long long)x) - 1));
     }
-    /* warp 0: look back over the predecessors */
+    __syncthreads();
     if (j < 32) {
+        /* warp 0: look back over the predecessors */
         unsigned long long prefix = 0ull;
         bool ok = true;
         if (t > 0) {
@@ -280,17 +297,19 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint32_t b, ui
         if (j == 0) {
             if (!ok) dsoa_raise(c, DSOA_DEV_SPIN);
             s_prefix = prefix;
-            __threadfence();
             if (t > 0) dsoa_st(&state[t], lb_word(ep, kLbP, prefix + total));
             if (t == tiles - 1) *r_dev = (uint32_t)(prefix + total);
         }
+    } else {
+        /* warp 1, meanwhile: the tile's part of the snapshot */
+        for (uint32_t i = lane; i < total && i < kSnap; i += 32) snap[i] = ~c.slot[list[i]];
     }
     __syncthreads();
     const unsigned long long base = s_prefix;
     for (uint32_t i = j; i < total; i += 64) {
         const uint32_t bid = list[i];
         R[base + i] = bid;
-        Rocc[base + i] = ~c.slot[bid];
+        Rocc[base + i] = i < kSnap ? snap[i] : ~c.slot[bid];
     }
     /* the last CTA to finish closes the epoch */
     __syncthreads();
@@ -476,8 +495,14 @@ int dsoa_enumerate_internal(dsoa_heap* h, int type) {
     if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
     const uint32_t b = dsoa_bm_alloc((uint32_t)type);
     if (h->scan_tiles_per_cta == 0) {      // single-pass look-back enumeration (default)
+        if (h->lb_fits < 0) {          // can every tile's CTA be resident at once?
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enum_lookback, 64, 0);
+            h->lb_fits = (uint64_t)per_sm * (uint64_t)h->num_sms >= h->tiles ? 1 : 0;
+        }
         k_enum_lookback<<<(unsigned)h->tiles, 64, 0, h->stream>>>(h->ctx, b, h->tiles, h->lb_state, h->lb_ctl,
-                                                                 h->R[type], h->Rocc[type], h->r_dev[type]);
+                                                                 h->R[type], h->Rocc[type], h->r_dev[type],
+                                                                 h->lb_fits ? 0u : 1u);
         rc = dsoa_check_launch(h);
         if (rc == DSOA_OK) h->enumerated[type] = true;
         return rc;
