@@ -198,8 +198,11 @@ int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
  * rotation, DSOA_FLAG_NO_HINT (4) turns off the per-warp last-block hint and
  * DSOA_FLAG_FUSED (8) runs dsoa_parallel_do as ONE cooperative launch
  * (enumeration and method separated by grid barriers) instead of the
- * tile-count, compaction and do-all kernels (the last two are not in the
- * paper).  Takes effect for launches issued after the call. */
+ * enumeration and do-all kernels, and DSOA_FLAG_PDL (16) launches the
+ * enumeration, do-all and step-counter kernels with programmatic dependent
+ * launch, so that each may be scheduled while its predecessor finishes (the
+ * last three are not in the paper).  Returns DSOA_ERR_INVALID_ARG for an
+ * unknown bit.  Takes effect for launches issued after the call. */
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags);
 
 /* r of Sec. 4.2 / Fig. 11: attempts to find an active block (try_find_set on

@@ -106,7 +106,21 @@ struct dsoa_ctx {
 #define DSOA_HINT_SLOTS 8192u             /* max hint-table warp slots per type     */
 #define DSOA_FLAG_FUSED 8u                /* one cooperative enumerate+do-all launch */
 #define DSOA_FUSED_MAX_CTAS 2048u         /* grid limit of the fused do-all         */
+#define DSOA_FLAG_PDL 16u                 /* programmatic dependent launch of the
+                                             enumeration, do-all and step kernels  */
 #define DSOA_GRID_SCRATCH (DSOA_FUSED_MAX_CTAS + 64u)
+
+/* Programmatic dependent launch (sm_90 and later).  A kernel launched with the
+ * programmatic-serialization attribute may be scheduled while its predecessor
+ * in the stream still runs; dsoa_pdl_wait() (griddepcontrol.wait) blocks until
+ * that predecessor has completed and its memory operations are visible to this
+ * grid, and returns at once for a kernel launched without the attribute.  The
+ * kernels the library launches that way call it before their first global
+ * memory access, so each of them also completes after its predecessor and the
+ * chain stays ordered.  dsoa_pdl_release() (griddepcontrol.launch_dependents)
+ * lets the next kernel be scheduled once every CTA of this one has started. */
+__device__ __forceinline__ void dsoa_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dsoa_pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 /* bitmap ids inside ctx.bm */
 __host__ __device__ __forceinline__ uint32_t dsoa_bm_free() { return 0u; }
@@ -537,14 +551,20 @@ __global__ void __maxnreg__(DSOA_DOALL_MAXNREG) dsoa_doall_kernel(dsoa_ctx c, ui
                                   const unsigned long long* __restrict__ occ,
                                   const uint32_t* __restrict__ r_dev, typename M::Args args) {
     constexpr uint32_t TPB = 64u / G;                          /* threads per block */
+    dsoa_pdl_wait();
+    dsoa_pdl_release();
     const uint64_t n = (uint64_t)gridDim.x * blockDim.x;      /* multiple of 64 */
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t s0 = (uint32_t)(tid % TPB);
-    const uint64_t total = (uint64_t)(*r_dev) * TPB;
+    /* Under programmatic dependent launch R, the snapshot and r may have been
+     * written while this grid was already resident: read them coherently then;
+     * otherwise through the read-only path. */
+    const bool pdl = (c.flags & DSOA_FLAG_PDL) != 0u;
+    const uint64_t total = (uint64_t)(pdl ? dsoa_ld32(r_dev) : __ldg(r_dev)) * TPB;
     for (uint64_t g = tid; g < total; g += n) {
         const uint64_t i = g / TPB;
-        const unsigned long long o = __ldg(&occ[i]);
-        const uint64_t bid = (uint64_t)__ldg(&R[i]);
+        const unsigned long long o = pdl ? dsoa_ld(&occ[i]) : __ldg(&occ[i]);
+        const uint64_t bid = (uint64_t)(pdl ? dsoa_ld32(&R[i]) : __ldg(&R[i]));
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             const uint32_t s = s0 + (uint32_t)k * TPB;

@@ -120,6 +120,30 @@ unsigned dsoa_doall_grid(dsoa_heap* h, K* kernel, int tpb) {
     return dsoa_persistent_grid(h, kernel, tpb) * (unsigned)h->doall_waves;
 }
 
+// Launch of a step kernel on the heap's stream; with DSOA_FLAG_PDL it carries
+// the programmatic-serialization attribute (the kernel calls dsoa_pdl_wait()
+// before touching global memory).  Counts the launch; DSOA_ERR_CUDA on failure.
+template <typename... KArgs, typename... Args>
+int dsoa_launch_step(dsoa_heap* h, void (*kernel)(KArgs...), unsigned grid, unsigned tpb, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tpb);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = (h->flags & DSOA_FLAG_PDL) ? 1u : 0u;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+    h->launches++;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DSOA_ERR_CUDA;
+    }
+    return DSOA_OK;
+}
+
 // Cooperative launch (every CTA co-resident) of a kernel that uses grid barriers.
 template <typename... KArgs, typename... Args>
 cudaError_t dsoa_launch_cooperative(void (*kernel)(KArgs...), unsigned grid, unsigned tpb, cudaStream_t s,
@@ -184,16 +208,17 @@ int dsoa_run_doall(dsoa_heap* h, int type, const typename M::Args& args) {
     int rc = dsoa_prepare_doall(h, type);
     if (rc) return rc;
     const int tpb = h->doall_tpb;
+    const uint32_t* R = h->R[type];
+    const unsigned long long* occ = h->Rocc[type];
+    const uint32_t* r = h->r_dev[type];
     if (h->slots_per_thread >= 2) {
         auto* k = &dsoa_doall_kernel<M, 2>;
-        k<<<dsoa_doall_grid(h, k, tpb), tpb, 0, h->stream>>>(
-            dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], args);
-    } else {
-        auto* k = &dsoa_doall_kernel<M, 1>;
-        k<<<dsoa_doall_grid(h, k, tpb), tpb, 0, h->stream>>>(
-            dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], args);
+        return dsoa_launch_step(h, k, dsoa_doall_grid(h, k, tpb), (unsigned)tpb, dsoa_launch_ctx(h), (uint32_t)type,
+                                R, occ, r, args);
     }
-    return dsoa_check_launch(h);
+    auto* k = &dsoa_doall_kernel<M, 1>;
+    return dsoa_launch_step(h, k, dsoa_doall_grid(h, k, tpb), (unsigned)tpb, dsoa_launch_ctx(h), (uint32_t)type,
+                            R, occ, r, args);
 }
 
 // parallel_new kernel: logical thread i allocates one object and constructs it.

@@ -105,6 +105,8 @@ __global__ void k_init_free(dsoa_ctx c) {
 __global__ void k_tile_count(dsoa_ctx c, uint32_t b, uint64_t tiles, uint32_t* __restrict__ tcnt,
                              uint32_t* __restrict__ toff, uint32_t* __restrict__ r_dev,
                              uint32_t* __restrict__ done) {
+    dsoa_pdl_wait();
+    dsoa_pdl_release();
     const uint32_t lane = threadIdx.x & 31u, wpc = blockDim.x >> 5;
     const unsigned long long* L0 = dsoa_level(c, b, 0);
     const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, b, 1) : nullptr;
@@ -155,6 +157,8 @@ __global__ void __launch_bounds__(64 * TPC) k_compact(dsoa_ctx c, uint32_t b, ui
                                                       const uint32_t* __restrict__ toff,
                                                       uint32_t* __restrict__ R,
                                                       unsigned long long* __restrict__ Rocc) {
+    dsoa_pdl_wait();
+    dsoa_pdl_release();
     __shared__ uint32_t list[TPC][4096];
     __shared__ uint32_t wsum[TPC][2];
     const uint32_t tl = threadIdx.x >> 6, j = threadIdx.x & 63u, lane = threadIdx.x & 31u;
@@ -226,6 +230,8 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint32_t b, ui
     uint32_t* done = ctl + 1;
     uint32_t* epoch = ctl + 2;
     const uint32_t j = threadIdx.x, lane = j & 31u;
+    dsoa_pdl_wait();
+    dsoa_pdl_release();
     const unsigned long long* L0 = dsoa_level(c, b, 0);
     const uint64_t w0 = c.lvl_words[0];
     uint64_t t;
@@ -500,28 +506,24 @@ int dsoa_enumerate_internal(dsoa_heap* h, int type) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enum_lookback, 64, 0);
             h->lb_fits = (uint64_t)per_sm * (uint64_t)h->num_sms >= h->tiles ? 1 : 0;
         }
-        k_enum_lookback<<<(unsigned)h->tiles, 64, 0, h->stream>>>(h->ctx, b, h->tiles, h->lb_state, h->lb_ctl,
-                                                                 h->R[type], h->Rocc[type], h->r_dev[type],
-                                                                 h->lb_fits ? 0u : 1u);
-        rc = dsoa_check_launch(h);
+        rc = dsoa_launch_step(h, k_enum_lookback, (unsigned)h->tiles, 64u, h->ctx, b, h->tiles, h->lb_state,
+                              h->lb_ctl, h->R[type], h->Rocc[type], h->r_dev[type], h->lb_fits ? 0u : 1u);
         if (rc == DSOA_OK) h->enumerated[type] = true;
         return rc;
     }
     const int tpb = 256;
     const uint64_t warps = h->tiles;
     const unsigned g1 = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 7) / 8, (uint64_t)h->num_sms * 8));
-    k_tile_count<<<g1, tpb, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_cnt, h->tile_off, h->r_dev[type], h->done);
-    rc = dsoa_check_launch(h);
+    rc = dsoa_launch_step(h, k_tile_count, g1, (unsigned)tpb, h->ctx, b, h->tiles, h->tile_cnt, h->tile_off,
+                          h->r_dev[type], h->done);
     if (rc) return rc;
-    switch (h->scan_tiles_per_cta) {
-        case 2:
-            k_compact<2><<<(unsigned)((h->tiles + 1) / 2), 128, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_off, h->R[type], h->Rocc[type]);
-            break;
-        default:
-            k_compact<1><<<(unsigned)h->tiles, 64, 0, h->stream>>>(h->ctx, b, h->tiles, h->tile_off, h->R[type], h->Rocc[type]);
-            break;
-    }
-    rc = dsoa_check_launch(h);
+    const uint32_t* toff = h->tile_off;
+    if (h->scan_tiles_per_cta == 2)
+        rc = dsoa_launch_step(h, k_compact<2>, (unsigned)((h->tiles + 1) / 2), 128u, h->ctx, b, h->tiles, toff,
+                              h->R[type], h->Rocc[type]);
+    else
+        rc = dsoa_launch_step(h, k_compact<1>, (unsigned)h->tiles, 64u, h->ctx, b, h->tiles, toff, h->R[type],
+                              h->Rocc[type]);
     if (rc == DSOA_OK) h->enumerated[type] = true;
     return rc;
 }
@@ -875,7 +877,8 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
 }
 
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags) {
-    if (!h || (flags & ~(DSOA_FLAG_NO_COALESCE | DSOA_FLAG_NO_ROTATE | DSOA_FLAG_NO_HINT | DSOA_FLAG_FUSED)))
+    if (!h || (flags & ~(DSOA_FLAG_NO_COALESCE | DSOA_FLAG_NO_ROTATE | DSOA_FLAG_NO_HINT | DSOA_FLAG_FUSED |
+                         DSOA_FLAG_PDL)))
         return DSOA_ERR_INVALID_ARG;
     h->flags = flags;
     return DSOA_OK;

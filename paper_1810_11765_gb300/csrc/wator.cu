@@ -216,6 +216,7 @@ __global__ void k_init(dsoa_ctx c, dsoa_wator_args a, uint64_t n) {
 }
 
 __global__ void k_advance(dsoa_inst* inst, uint32_t n) {
+    dsoa_pdl_wait();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && inst[i].state == DSOA_INST_RUN) inst[i].t += 1u;
 }
@@ -255,8 +256,7 @@ int dsoa_wator_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_
         }
         case DSOA_K_WATOR_ADVANCE:
             if (n > args.n_inst) return DSOA_ERR_INVALID_ARG;
-            k_advance<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(args.inst, (uint32_t)n);
-            return dsoa_check_launch(h);
+            return dsoa_launch_step(h, k_advance, (unsigned)((n + 255) / 256), 256u, args.inst, (uint32_t)n);
         default: return DSOA_ERR_UNKNOWN_METHOD;
     }
 }

@@ -21,7 +21,7 @@ ERRORS = {-1: "invalid argument", -2: "heap layout already frozen", -3: "too man
           -9: "heap larger than the fixed no-allocation scratch allows"}
 
 DEV_OOM, DEV_SPIN, DEV_DOUBLE_FREE, DEV_BAD_HANDLE = 1, 2, 4, 8
-FLAG_NO_COALESCE, FLAG_NO_ROTATE, FLAG_NO_HINT, FLAG_FUSED = 1, 2, 4, 8
+FLAG_NO_COALESCE, FLAG_NO_ROTATE, FLAG_NO_HINT, FLAG_FUSED, FLAG_PDL = 1, 2, 4, 8, 16
 CHECK_NAMES = ["hier", "free_xor", "multi_type", "active_subset", "type", "free_word",
                "empty_alloc", "active_exact", "tail_bits"]
 

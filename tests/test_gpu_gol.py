@@ -92,3 +92,32 @@ def test_batched_instances_match_alone():
     assert heap.count(w.cell_type) == specs[0][0] * specs[0][1] + specs[2][0] * specs[2][1]
     assert heap.get_error() == 0
     assert all(v == 0 for v in heap.check().values())
+
+
+@pytest.mark.parametrize("launch,flags", [(dict(), 16), (dict(scan_tiles=1, waves=8), 16), (dict(scan_tiles=4), 16)])
+def test_launch_modes_graph_captured(launch, flags):
+    """Programmatic dependent launch, the two-kernel and the streamed enumeration:
+    a graph-captured generation replayed 30 times equals the oracle."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    W, H, gens, seed = 200, 150, 30, 21
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        heap, w = world(32 << 20)
+        if launch:
+            heap.set_launch(**launch)
+        heap.set_flags(flags)
+        slot = w.add(W, H, seed)
+        heap.graph_begin()
+        w.step()
+        g = heap.graph_end()
+        for _ in range(gens):
+            g.launch()
+        s.synchronize()
+        grid = w.read(slot)
+        alive = w.alive_objects()
+    ref, alive_ref, _ = oracle.gol_run(W, H, gens, seed=seed)
+    assert np.array_equal(grid, ref)
+    assert alive == alive_ref[-1]
+    assert heap.get_error() == 0
+    g.close()

@@ -101,7 +101,7 @@ def test_scale_variants_agree(method):
     assert_clean(m)
 
 
-@pytest.mark.parametrize("flags", [1, 2, 3, 4, 7, 8, 15])
+@pytest.mark.parametrize("flags", [1, 2, 3, 4, 7, 8, 15, 16, 24])
 def test_ablations_keep_semantics(flags):
     """NoCoal / NoShift / both (Sec. 6.4) change placement, not results.  Without
     coalescing every thread of a burst on an empty heap may take a block of its own
@@ -318,3 +318,21 @@ def test_atomic_peak_probe_final_words():
         m.heap.run_kernel(D.K_MICRO_ATOMIC_PEAK, n, m.args(handles_out=words.data_ptr(), n_ids=nw - 1, round=1,
                                                            stats=sink.data_ptr()))
     assert m.heap.get_error() == 0
+
+
+@pytest.mark.parametrize("scan", [3, 1])
+def test_heap_beyond_one_wave_of_enumeration_ctas(scan):
+    """A 5 GiB heap has more level-1 tiles (~1200) than look-back CTAs fit on the
+    GPU at once (~900), so tiles are handed out by the ticket counter instead of
+    blockIdx; the rounds still match the oracle.  The two-kernel enumeration runs
+    the same heap."""
+    n, rounds = 1 << 18, 3
+    ref, _, _ = oracle.micro_run(SEED, n, rounds)
+    m = make(heap_bytes=5 << 30, n=n, scan_tiles=scan)
+    assert m.heap.info()["num_blocks"] > 4096 * 1100
+    for r in range(rounds):
+        m.round(r)
+        compare_round(m.stats(), ref[r])
+    assert m.heap.get_error() == 0
+    assert all(v == 0 for v in m.heap.check().values())
+    m.heap.close()

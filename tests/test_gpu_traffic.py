@@ -78,3 +78,20 @@ def test_full_config_sampled_rings():
     assert heap.count(w.car_type) == int(go.sum())
     assert gv.max() <= 5 and np.all(gv[~go.astype(bool)] == 0)
     assert heap.get_error() == 0
+
+
+@pytest.mark.parametrize("flags", [16])
+def test_programmatic_dependent_launch(flags):
+    """The batch stepped with programmatic dependent launch equals the oracle."""
+    L = [16, 23, 300, 4096, 5000]
+    thr = [int(d * 2**32) for d in (0.3, 0.6, 0.2, 0.1, 0.3)]
+    seed = 78
+    heap, w = world(L, thr, seed, ramp_thr=int(0.3 * 2**32))
+    heap.set_flags(flags)
+    while w.steps_done < 25:
+        w.step()
+    o, v, cars = oracle.traffic_run(L, thr, 25, seed=seed, ramp_thr=int(0.3 * 2**32))
+    go, gv = w.read()
+    assert np.array_equal(go, o)
+    assert np.array_equal(gv, v)
+    assert heap.get_error() == 0

@@ -82,7 +82,9 @@ def test_batched_instances_match_alone():
 
 @pytest.mark.parametrize("launch,flags", [(dict(), 0), (dict(tpb=128, ctas_per_sm=4, slots_per_thread=2, scan_tiles=2), 0),
                                           (dict(), 8), (dict(tpb=512, ctas_per_sm=1), 12),
-                                          (dict(waves=1), 0), (dict(tpb=128, slots_per_thread=2, waves=16), 0)])
+                                          (dict(waves=1), 0), (dict(tpb=128, slots_per_thread=2, waves=16), 0),
+                                          (dict(), 16), (dict(tpb=128, scan_tiles=2, waves=8), 16),
+                                          (dict(tpb=512, ctas_per_sm=1, waves=1), 20)])
 def test_graph_captured_steps_match_oracle(launch, flags):
     """One step captured as a CUDA graph and replayed: the step index lives in
     device memory, so replays advance the simulation exactly like plain steps."""
