@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-Wall", "-Wextra", "-o", tmp, _SRC]
+           "-shared", "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -46,6 +46,12 @@ class MicroRound(ctypes.Structure):
                 ("sum_tag", ctypes.c_uint64), ("xor_tag", ctypes.c_uint64),
                 ("sum_x", ctypes.c_double), ("news", ctypes.c_uint64),
                 ("deletes", ctypes.c_uint64)]
+
+
+class NBodyParams(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_float), ("dt", ctypes.c_float), ("eps2", ctypes.c_float),
+                ("rc2", ctypes.c_float), ("fscale", ctypes.c_float), ("vscale", ctypes.c_float),
+                ("mass_max", ctypes.c_uint32), ("collide", ctypes.c_uint32)]
 
 
 class WatorStep(ctypes.Structure):
@@ -78,6 +84,8 @@ def _load():
             lib.orc_traffic_run.argtypes = [u32, u32, P, P, u64, u32, u32, u32, P, P, u64,
                                             P, P, P]
             lib.orc_traffic_run.restype = i32
+            lib.orc_nbody_run.argtypes = [u32, P, u64, P, u32, u64, P, P, P, P]
+            lib.orc_nbody_run.restype = i32
             _lib = lib
     return _lib
 
@@ -171,3 +179,21 @@ def traffic_run(L, thr, steps: int, seed: int = 0, slow_thr: int = SLOW_THR,
     if rc != 0:
         raise RuntimeError("oracle traffic failed")
     return occ, v, cars
+
+
+def nbody_run(n: int, steps: int, seed: int = 0, *, G: float, dt: float, eps2: float,
+              rc2: float = 0.0, fscale: float = 2.0 ** 40, vscale: float = 2.0 ** -8,
+              mass_max: int = 16, collide: bool = False, init=None, order_seed: int = 0):
+    """N-body (collide=False) or particle collisions.  Returns (state float32[n,5] by id:
+    px, py, vx, vy, m; alive uint8[n]; counts uint32[steps+1]; force sums int64[steps,2])."""
+    prm = NBodyParams(G, dt, eps2, rc2, fscale, vscale, mass_max, 1 if collide else 0)
+    ini = None if init is None else np.ascontiguousarray(np.asarray(init, dtype=np.float32).reshape(n, 5))
+    out = np.zeros((max(n, 1), 5), dtype=np.float32)
+    alive = np.zeros(max(n, 1), dtype=np.uint8)
+    counts = np.zeros(steps + 1, dtype=np.uint32)
+    fsum = np.zeros((max(steps, 1), 2), dtype=np.int64)
+    rc = _load().orc_nbody_run(n, _ptr(ini), seed, ctypes.byref(prm), steps, order_seed,
+                               _ptr(out), _ptr(alive), _ptr(counts), _ptr(fsum))
+    if rc != 0:
+        raise RuntimeError("oracle n-body failed")
+    return out[:n], alive[:n], counts, fsum[:steps]

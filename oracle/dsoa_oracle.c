@@ -16,6 +16,7 @@
  */
 #include "dsoa_oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -608,5 +609,216 @@ int orc_traffic_run(uint32_t n_inst, uint32_t first_ring, const uint32_t* L, con
     if (st.failed) rc = -1;
     store_free(&st);
     free(off); free(cur); free(nxt); free(cars);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* N-body and particle collisions (Table 1 "nbody", "collision"; Sec. 2's   */
+/* running example).  One type, Body {id, pos, vel, mass, force, target,    */
+/* incoming, merged}.  Every body of the current set acts on every other    */
+/* one through a device_do (Sec. 2.1, the sequential for-each over a type), */
+/* so a force do-all is O(n^2).                                             */
+/*                                                                          */
+/* Arithmetic (our reading, chosen so that the result does not depend on    */
+/* the order in which the for-each or the do-all visits bodies): every      */
+/* float operation is one IEEE binary32 operation rounded to nearest, never */
+/* contracted; the pairwise force is rounded to an integer of the fixed-    */
+/* point scale S and summed in 64-bit two's complement arithmetic, which is */
+/* associative, so the force on a body is exact whatever the visit order.   */
+/* Because x_j - x_i == -(x_i - x_j) exactly and G S is a power of two, the */
+/* pair (j, i) yields exactly the negated integers of (i, j): the forces of */
+/* one FORCE do-all sum to zero exactly (Newton's third law).               */
+/*                                                                          */
+/* n-body step (2 do-alls): FORCE, MOVE.                                    */
+/*   FORCE  F_i = sum over j != i of fix(((G S m_i) m_j) d^-3 (x_j - x_i)), */
+/*          d2 = |x_j - x_i|^2 + eps2, d = sqrt(d2), d^-3 = (1/d)(1/d)(1/d) */
+/*          (the paper's G m_i m_j / d^2 along the unit vector, softened,  */
+/*          with the scale S folded into G; G and S are powers of two, so  */
+/*          (G S m_i) is exact and m_i, m_j enter symmetrically)           */
+/*   MOVE   v += (F S^-1 / m) dt;  x += v dt   (velocity first)             */
+/* collision step (6 do-alls): FORCE, MOVE, then                            */
+/*   FIND   target = nearest body j with |x_j - x_i|^2 < rc2 that is bigger */
+/*          (heavier, or as heavy with a lower id); ties of distance go to  */
+/*          the lower id.  Resets incoming and merged.                      */
+/*   CLAIM  a body with a target proposes itself: incoming of the target    */
+/*          = min(incoming, own id)  (lowest id wins, as in Wa-Tor)         */
+/*   MERGE  a body with an incoming proposal that has no target itself      */
+/*          absorbs the winner: perfectly inelastic, mass and momentum      */
+/*          added, position at the centre of mass; the winner is marked     */
+/*   DELETE a marked body deletes itself                                    */
+/* A proposer whose target is itself merging waits for a later step, so     */
+/* chains resolve one link per step and no body is absorbed twice.          */
+/* ------------------------------------------------------------------------ */
+#define NB_NONE 0xFFFFFFFFu
+#define NB_FIX_MAX 0x1p62f
+
+typedef struct {
+    uint32_t id;
+    float px, py, vx, vy, m;
+    int64_t fx, fy;
+    uint32_t target, incoming, merged;
+} nb_body;
+
+/* u in [0, 1) from the top 24 bits of a Philox word, exact in binary32 */
+static float nb_unit(uint32_t w) { return (float)(w >> 8) * 0x1p-24f; }
+
+/* Initial state of body i: Philox(seed; 0xFFFFFFFF, i, k, 0) word 0 for
+ * k = 0..4 gives pos x, pos y in [-1, 1), vel x, vel y in
+ * [-vscale/2, vscale/2) and the integer mass 1 + w mod mass_max. */
+static void nb_draw(uint64_t seed, uint32_t i, const orc_nbody_params* p, float st[5]) {
+    st[0] = nb_unit(philox_w0(seed, 0xFFFFFFFFu, i, 0, 0)) * 2.0f - 1.0f;
+    st[1] = nb_unit(philox_w0(seed, 0xFFFFFFFFu, i, 1, 0)) * 2.0f - 1.0f;
+    st[2] = (nb_unit(philox_w0(seed, 0xFFFFFFFFu, i, 2, 0)) - 0.5f) * p->vscale;
+    st[3] = (nb_unit(philox_w0(seed, 0xFFFFFFFFu, i, 3, 0)) - 0.5f) * p->vscale;
+    st[4] = (float)(1u + philox_w0(seed, 0xFFFFFFFFu, i, 4, 0) % p->mass_max);
+}
+
+/* one pair term, already scaled by S, clamped to +-2^62 and rounded to the
+ * nearest integer (ties to even) */
+static int64_t nb_fix(float s) {
+    if (s > NB_FIX_MAX) s = NB_FIX_MAX;
+    if (s < -NB_FIX_MAX) s = -NB_FIX_MAX;
+    return (int64_t)llrintf(s);
+}
+
+int orc_nbody_run(uint32_t n, const float* init, uint64_t seed, const orc_nbody_params* p,
+                  uint32_t steps, uint64_t order_seed, float* out, uint8_t* out_alive,
+                  uint32_t* count_per_step, int64_t* force_sum) {
+    if (!p || !(p->eps2 > 0.0f) || !(p->fscale > 0.0f) || p->mass_max == 0) return -1;
+    store_t st;
+    store_init(&st, sizeof(nb_body));
+    uint32_t* of_id = (uint32_t*)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    if (!of_id) return -1;
+    int rc = 0;
+    /* parallel_new<Body>(n): constructor index i is the body id */
+    for (uint32_t i = 0; i < n; ++i) {
+        uint32_t k = store_new(&st);
+        if (k == UINT32_MAX) { rc = -1; break; }
+        nb_body* b = (nb_body*)store_get(&st, k);
+        float s[5];
+        if (init) memcpy(s, init + (size_t)5 * i, sizeof(s)); else nb_draw(seed, i, p, s);
+        b->id = i; b->px = s[0]; b->py = s[1]; b->vx = s[2]; b->vy = s[3]; b->m = s[4];
+        b->target = NB_NONE; b->incoming = NB_NONE; b->merged = 0;
+        of_id[i] = k;
+    }
+    if (count_per_step && rc == 0) count_per_step[0] = st.nlive;
+    const float GS = p->G * p->fscale, Sinv = 1.0f / p->fscale;
+    for (uint32_t step = 0; step < steps && rc == 0; ++step) {
+        uint64_t os = order_seed ? order_seed + 8ull * step : 0;
+        uint32_t n_snap, n_all;
+        /* do-all FORCE, each body running device_do over every body */
+        uint32_t* snap = store_snapshot(&st, os ? os + 1 : 0, &n_snap);
+        uint32_t* all = store_snapshot(&st, os ? os + 7 : 0, &n_all);
+        uint64_t sx = 0, sy = 0;
+        for (uint32_t a = 0; a < n_snap; ++a) {
+            nb_body* bi = (nb_body*)store_get(&st, snap[a]);
+            uint64_t fx = 0, fy = 0;
+            const float gsm = GS * bi->m;
+            for (uint32_t c = 0; c < n_all; ++c) {
+                if (all[c] == snap[a]) continue;
+                const nb_body* bj = (const nb_body*)store_get(&st, all[c]);
+                float dx = bj->px - bi->px;
+                float dy = bj->py - bi->py;
+                float dxx = dx * dx, dyy = dy * dy;
+                float d2 = (dxx + dyy) + p->eps2;
+                float d = sqrtf(d2);
+                float inv = 1.0f / d;
+                float inv2 = inv * inv;
+                float inv3 = inv2 * inv;
+                float k = (gsm * bj->m) * inv3;
+                fx += (uint64_t)nb_fix(k * dx);
+                fy += (uint64_t)nb_fix(k * dy);
+            }
+            bi->fx = (int64_t)fx;
+            bi->fy = (int64_t)fy;
+            sx += fx; sy += fy;
+        }
+        free(all);
+        if (force_sum) { force_sum[2 * step] = (int64_t)sx; force_sum[2 * step + 1] = (int64_t)sy; }
+        /* do-all MOVE */
+        for (uint32_t a = 0; a < n_snap; ++a) {
+            nb_body* b = (nb_body*)store_get(&st, snap[a]);
+            float ax = ((float)b->fx * Sinv) / b->m;
+            float ay = ((float)b->fy * Sinv) / b->m;
+            b->vx = b->vx + ax * p->dt;
+            b->vy = b->vy + ay * p->dt;
+            b->px = b->px + b->vx * p->dt;
+            b->py = b->py + b->vy * p->dt;
+        }
+        if (p->collide) {
+            /* do-all FIND (device_do over every body) */
+            for (uint32_t a = 0; a < n_snap; ++a) {
+                nb_body* bi = (nb_body*)store_get(&st, snap[a]);
+                uint32_t best = NB_NONE;
+                float bestd = 0.0f;
+                for (uint32_t c = 0; c < n_snap; ++c) {
+                    if (c == a) continue;
+                    const nb_body* bj = (const nb_body*)store_get(&st, snap[c]);
+                    float dx = bj->px - bi->px;
+                    float dy = bj->py - bi->py;
+                    float dxx = dx * dx, dyy = dy * dy;
+                    float d2 = dxx + dyy;
+                    int bigger = bj->m > bi->m || (bj->m == bi->m && bj->id < bi->id);
+                    if (d2 < p->rc2 && bigger &&
+                        (best == NB_NONE || d2 < bestd || (d2 == bestd && bj->id < best))) {
+                        best = bj->id;
+                        bestd = d2;
+                    }
+                }
+                bi->target = best;
+                bi->incoming = NB_NONE;
+                bi->merged = 0;
+            }
+            /* do-all CLAIM */
+            for (uint32_t a = 0; a < n_snap; ++a) {
+                nb_body* b = (nb_body*)store_get(&st, snap[a]);
+                if (b->target == NB_NONE) continue;
+                nb_body* tb = (nb_body*)store_get(&st, of_id[b->target]);
+                if (b->id < tb->incoming) tb->incoming = b->id;
+            }
+            /* do-all MERGE */
+            for (uint32_t a = 0; a < n_snap; ++a) {
+                nb_body* b = (nb_body*)store_get(&st, snap[a]);
+                if (b->incoming == NB_NONE || b->target != NB_NONE) continue;
+                nb_body* s = (nb_body*)store_get(&st, of_id[b->incoming]);
+                float M = b->m + s->m;
+                float mvx = b->m * b->vx, svx = s->m * s->vx;
+                float mvy = b->m * b->vy, svy = s->m * s->vy;
+                float mpx = b->m * b->px, spx = s->m * s->px;
+                float mpy = b->m * b->py, spy = s->m * s->py;
+                b->vx = (mvx + svx) / M;
+                b->vy = (mvy + svy) / M;
+                b->px = (mpx + spx) / M;
+                b->py = (mpy + spy) / M;
+                b->m = M;
+                s->merged = 1;
+            }
+            /* do-all DELETE */
+            for (uint32_t a = 0; a < n_snap; ++a) {
+                nb_body* b = (nb_body*)store_get(&st, snap[a]);
+                if (!b->merged) continue;
+                of_id[b->id] = NB_NONE;
+                store_delete(&st, snap[a]);
+            }
+        }
+        free(snap);
+        if (st.failed) rc = -1;
+        if (count_per_step && rc == 0) count_per_step[step + 1] = st.nlive;
+    }
+    if (rc == 0) {
+        if (out) memset(out, 0, (size_t)n * 5 * sizeof(float));
+        if (out_alive) memset(out_alive, 0, n);
+        for (uint32_t k = 0; k < st.hw; ++k) {
+            if (!st.live[k]) continue;
+            const nb_body* b = (const nb_body*)store_get(&st, k);
+            if (out) {
+                float* o = out + (size_t)5 * b->id;
+                o[0] = b->px; o[1] = b->py; o[2] = b->vx; o[3] = b->vy; o[4] = b->m;
+            }
+            if (out_alive) out_alive[b->id] = 1;
+        }
+    }
+    free(of_id);
+    store_free(&st);
     return rc;
 }

@@ -22,6 +22,10 @@
  *                       order independence
  *   orc_traffic_run     pinned: deterministic (p=0) closed forms of Nagel &
  *                       Schreckenberg 1992, conservation, brute force on L=16
+ *   orc_nbody_run       pinned: two-body closed forms (first step of a pair at
+ *                       rest, circular orbit), free motion, Newton's third law
+ *                       exactly, hand-derived merges and merge chains, mass
+ *                       conservation, order independence
  */
 #ifndef DSOA_ORACLE_H
 #define DSOA_ORACLE_H
@@ -96,6 +100,27 @@ int orc_traffic_run(uint32_t n_inst, uint32_t first_ring, const uint32_t* L, con
                     uint32_t ramp_thr, const uint8_t* init_occ,
                     const uint8_t* init_v, uint64_t order_seed,
                     uint8_t* out_occ, uint8_t* out_v, uint32_t* cars_per_step);
+
+/* ---- n-body and particle collisions (one type, Body) ---- */
+typedef struct {
+    float    G;         /* gravitational constant (a power of two)              */
+    float    dt;        /* time step                                            */
+    float    eps2;      /* softening added to the squared distance in FORCE (>0)*/
+    float    rc2;       /* collisions: merge below this squared distance        */
+    float    fscale;    /* fixed-point scale S of the force sums (a power of 2) */
+    float    vscale;    /* initial velocities in [-vscale/2, vscale/2)          */
+    uint32_t mass_max;  /* initial masses are the integers 1..mass_max          */
+    uint32_t collide;   /* 0: n-body (FORCE, MOVE); 1: + FIND, CLAIM, MERGE, DELETE */
+} orc_nbody_params;
+
+/* n bodies with ids 0..n-1, initial state from `init` (nullable, n x 5 floats
+ * px, py, vx, vy, m) or drawn from `seed`; `steps` steps.  out: n x 5 floats
+ * of the final state by id (zeros for merged bodies), out_alive: n bytes,
+ * count_per_step: steps+1 body counts, force_sum: 2*steps wrapped sums of the
+ * fixed-point forces of each FORCE do-all (all nullable).  Returns 0 or -1. */
+int orc_nbody_run(uint32_t n, const float* init, uint64_t seed, const orc_nbody_params* p,
+                  uint32_t steps, uint64_t order_seed, float* out, uint8_t* out_alive,
+                  uint32_t* count_per_step, int64_t* force_sum);
 
 #ifdef __cplusplus
 }
