@@ -10,6 +10,8 @@
  *   game of life  Cell per site + Alive agent per live cell, B3/S23 torus
  *   wa-tor      Fish / Shark agents on a torus with per-cell occupancy
  *   traffic     Nagel-Schreckenberg cars on batched rings
+ *   n-body / collisions  Body objects under pairwise gravity (device_do), merged
+ *               by perfectly inelastic collisions
  */
 #ifndef DSOA_APPS_H
 #define DSOA_APPS_H
@@ -133,6 +135,58 @@ typedef struct {
     uint32_t ramp_thr;           /* 214748364 = floor(0.05 * 2^32)                     */
     int32_t car_type;
 } dsoa_traffic_args;
+
+/* ---------------- n-body / particle collisions (Table 1 "nbody", "collision"):
+ *   Body {0 id u32, 1 px f32, 2 py f32, 3 vx f32, 4 vy f32, 5 m f32, 6 fx i64,
+ *         7 fy i64, 8 target u32, 9 incoming u32, 10 merged u32}
+ * Arithmetic: every float op is one binary32 op rounded to nearest (no FMA);
+ * a pair term k (x_j - x_i), k = ((G S m_i) m_j) (1/d)^3, d = sqrt(|x_j - x_i|^2
+ * + eps2), is clamped to +-2^62, rounded to an integer and summed in wrapping
+ * 64-bit arithmetic, so a force does not depend on the order bodies are visited
+ * in.  G and the fixed-point scale S are powers of two; masses are integers.
+ * The force fields are zero between steps (the constructor and MOVE clear them).
+ * n-body step: FORCE (or FORCE_TILED), MOVE.  Collision step: FORCE, MOVE,
+ * FIND, CLAIM, MERGE, DELETE (one enumeration; the others reuse its snapshot). */
+#define DSOA_C_NBODY 500              /* ctor i: body id i from `init` (nullable, 5 floats
+                                         px py vx vy m per id) or Philox(seed; 0xFFFFFFFF, i,
+                                         k, 0) word 0, k = 0..4; handle_of[i] = handle      */
+#define DSOA_M_NBODY_FORCE 501        /* F = sum of pair terms over every other body, by a
+                                         device_do in the calling thread (Sec. 2.1)        */
+#define DSOA_M_NBODY_MOVE 502         /* v += ((F / S) / m) dt; x += v dt; F = 0            */
+#define DSOA_M_COLL_FIND 503          /* target = id of the nearest body with squared
+                                         distance < rc2 that is heavier, or as heavy with a
+                                         lower id (ties of distance: lower id), by device_do;
+                                         incoming = none, merged = 0                         */
+#define DSOA_M_COLL_CLAIM 504         /* atomicMin(incoming of the target, own id)          */
+#define DSOA_M_COLL_MERGE 505         /* incoming and no target: absorb the winner (mass,
+                                         momentum, centre of mass); mark it merged           */
+#define DSOA_M_COLL_DELETE 506        /* merged: handle_of[id] = 0, delete this              */
+#define DSOA_M_NBODY_READ 507         /* out[5 id + 0..4] = px py vx vy m; alive_out[id] = 1;
+                                         force_out[2 id + 0..1] = fx fy when non-null         */
+#define DSOA_M_NBODY_FORCE_TILED 508  /* FORCE's result (bit for bit) from a pairwise kernel
+                                         over the enumerated snapshot: CTAs take (256 bodies)
+                                         x (a chunk of bodies) tiles staged in shared memory
+                                         and add their integer partial sums atomically      */
+#define DSOA_NBODY_NONE 0xFFFFFFFFu   /* no target / no incoming proposal                    */
+typedef struct {
+    uint64_t* handle_of;  /* [n_ids] id -> handle; needed by collisions (CLAIM, MERGE read
+                             it, the ctor writes it, DELETE clears it); nullable for n-body */
+    const float* init;    /* ctor: nullable [n_ids * 5] (device)                          */
+    float* out;           /* READ: [n_ids * 5] (device, pre-zeroed)                       */
+    uint8_t* alive_out;   /* READ: [n_ids] (device, pre-zeroed)                           */
+    int64_t* force_out;   /* READ: nullable [n_ids * 2] fixed-point forces (device)         */
+    uint64_t seed;        /* Philox key of the initial draw                               */
+    uint32_t n_ids;       /* bodies created by the ctor (ids 0 .. n_ids-1)                */
+    uint32_t mass_max;    /* initial masses 1 .. mass_max                                 */
+    float G;              /* gravitational constant (power of two)                        */
+    float dt;             /* time step                                                    */
+    float eps2;           /* softening added to the squared distance (> 0)                */
+    float rc2;            /* squared merge distance                                       */
+    float fscale;         /* fixed-point scale S (power of two)                           */
+    float vscale;         /* initial velocities in [-vscale/2, vscale/2)                  */
+    int32_t body_type;
+    uint32_t pad;
+} dsoa_nbody_args;
 
 #ifdef __cplusplus
 }

@@ -86,6 +86,8 @@ def _load():
             lib.orc_traffic_run.restype = i32
             lib.orc_nbody_run.argtypes = [u32, P, u64, P, u32, u64, P, P, P, P]
             lib.orc_nbody_run.restype = i32
+            lib.orc_nbody_force_on.argtypes = [u32, P, P, P, u32, P]
+            lib.orc_nbody_force_on.restype = i32
             _lib = lib
     return _lib
 
@@ -197,3 +199,19 @@ def nbody_run(n: int, steps: int, seed: int = 0, *, G: float, dt: float, eps2: f
     if rc != 0:
         raise RuntimeError("oracle n-body failed")
     return out[:n], alive[:n], counts, fsum[:steps]
+
+
+def nbody_force_on(state, ids, alive=None, *, G: float, eps2: float, fscale: float = 2.0 ** 40):
+    """Fixed-point forces int64[len(ids), 2] of one FORCE do-all on the bodies ``ids``
+    of ``state`` (float32[n, 5]), from every other (alive) body."""
+    st = np.ascontiguousarray(np.asarray(state, dtype=np.float32))
+    n = st.shape[0]
+    al = None if alive is None else np.ascontiguousarray(np.asarray(alive, dtype=np.uint8))
+    prm = NBodyParams(G, 1.0, eps2, 0.0, fscale, 0.0, 1, 0)
+    out = np.zeros((len(ids), 2), dtype=np.int64)
+    row = np.zeros(2, dtype=np.int64)
+    for k, i in enumerate(ids):
+        if _load().orc_nbody_force_on(n, _ptr(st), _ptr(al), ctypes.byref(prm), int(i), _ptr(row)) != 0:
+            raise RuntimeError("oracle n-body force failed")
+        out[k] = row
+    return out

@@ -681,6 +681,39 @@ static int64_t nb_fix(float s) {
     return (int64_t)llrintf(s);
 }
 
+/* The pair term of body j (qx, qy, qm) on body i (px, py; gsm = G S m_i),
+ * added to the two's complement force words. */
+static void nb_pair(float px, float py, float gsm, float qx, float qy, float qm, float eps2,
+                    uint64_t* fx, uint64_t* fy) {
+    float dx = qx - px;
+    float dy = qy - py;
+    float dxx = dx * dx, dyy = dy * dy;
+    float d2 = (dxx + dyy) + eps2;
+    float d = sqrtf(d2);
+    float inv = 1.0f / d;
+    float inv2 = inv * inv;
+    float inv3 = inv2 * inv;
+    float k = (gsm * qm) * inv3;
+    *fx += (uint64_t)nb_fix(k * dx);
+    *fy += (uint64_t)nb_fix(k * dy);
+}
+
+int orc_nbody_force_on(uint32_t n, const float* state, const uint8_t* alive,
+                       const orc_nbody_params* p, uint32_t i, int64_t out[2]) {
+    if (!p || !state || i >= n || !(p->eps2 > 0.0f)) return -1;
+    const float* si = state + (size_t)5 * i;
+    const float gsm = (p->G * p->fscale) * si[4];
+    uint64_t fx = 0, fy = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+        if (j == i || (alive && !alive[j])) continue;
+        const float* sj = state + (size_t)5 * j;
+        nb_pair(si[0], si[1], gsm, sj[0], sj[1], sj[4], p->eps2, &fx, &fy);
+    }
+    out[0] = (int64_t)fx;
+    out[1] = (int64_t)fy;
+    return 0;
+}
+
 int orc_nbody_run(uint32_t n, const float* init, uint64_t seed, const orc_nbody_params* p,
                   uint32_t steps, uint64_t order_seed, float* out, uint8_t* out_alive,
                   uint32_t* count_per_step, int64_t* force_sum) {
@@ -717,17 +750,7 @@ int orc_nbody_run(uint32_t n, const float* init, uint64_t seed, const orc_nbody_
             for (uint32_t c = 0; c < n_all; ++c) {
                 if (all[c] == snap[a]) continue;
                 const nb_body* bj = (const nb_body*)store_get(&st, all[c]);
-                float dx = bj->px - bi->px;
-                float dy = bj->py - bi->py;
-                float dxx = dx * dx, dyy = dy * dy;
-                float d2 = (dxx + dyy) + p->eps2;
-                float d = sqrtf(d2);
-                float inv = 1.0f / d;
-                float inv2 = inv * inv;
-                float inv3 = inv2 * inv;
-                float k = (gsm * bj->m) * inv3;
-                fx += (uint64_t)nb_fix(k * dx);
-                fy += (uint64_t)nb_fix(k * dy);
+                nb_pair(bi->px, bi->py, gsm, bj->px, bj->py, bj->m, p->eps2, &fx, &fy);
             }
             bi->fx = (int64_t)fx;
             bi->fy = (int64_t)fy;

@@ -122,6 +122,13 @@ int orc_nbody_run(uint32_t n, const float* init, uint64_t seed, const orc_nbody_
                   uint32_t steps, uint64_t order_seed, float* out, uint8_t* out_alive,
                   uint32_t* count_per_step, int64_t* force_sum);
 
+/* The fixed-point force of one FORCE do-all on body i of a state (n x 5 floats
+ * px, py, vx, vy, m by id), summed over every other body j with alive[j]
+ * (alive nullable: all).  Used to check single bodies of large runs.
+ * Returns 0 or -1. */
+int orc_nbody_force_on(uint32_t n, const float* state, const uint8_t* alive,
+                       const orc_nbody_params* p, uint32_t i, int64_t out[2]);
+
 #ifdef __cplusplus
 }
 #endif

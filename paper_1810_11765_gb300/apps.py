@@ -1,4 +1,5 @@
-"""Workload drivers over the C ABI: microbench, game of life, wa-tor, traffic.
+"""Workload drivers over the C ABI: microbench, game of life, wa-tor, traffic,
+n-body and particle collisions.
 
 Each driver only sequences library calls (``dsoa_parallel_new``, ``dsoa_parallel_do``,
 ``dsoa_run_kernel``) and owns the plain device arrays of its workload as torch
@@ -304,3 +305,72 @@ class TrafficWorld:
         t = int(self.t_dev.cpu().numpy()[0])
         occ = self.occ1 if (t & 1) else self.occ0
         return occ[:self.total].cpu().numpy(), self.vel[:self.total].cpu().numpy()
+
+
+# ----------------------------------------------------------------------------- n-body
+class NBodyWorld:
+    """n-body (``collide=False``: FORCE, MOVE) or particle collisions (FORCE, MOVE,
+    FIND, CLAIM, MERGE, DELETE) over one Body type.  ``tiled`` selects the pairwise
+    shared-memory FORCE kernel instead of the per-thread device_do walk (same
+    integers)."""
+
+    BODY_FIELDS = [4, 4, 4, 4, 4, 4, 8, 8, 4, 4, 4]   # id px py vx vy m fx fy target incoming merged
+
+    def __init__(self, heap: D.Heap, cfg, collide: bool = False, tiled: bool = True, body_type=None):
+        self.heap = heap
+        self.cfg = cfg
+        self.collide = collide
+        self.force_method = D.M_NBODY_FORCE_TILED if tiled else D.M_NBODY_FORCE
+        self.type = heap.register_type(self.BODY_FIELDS) if body_type is None else body_type
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.n = 0
+        self.handle_of = None
+        self._init = None
+
+    def args(self, **kw) -> D.NBodyArgs:
+        c = self.cfg
+        a = D.NBodyArgs(handle_of=D._addr(self.handle_of), seed=c.seed, n_ids=self.n,
+                        mass_max=c.mass_max, G=c.G, dt=c.dt, eps2=c.eps2, rc2=c.rc2,
+                        fscale=c.fscale, vscale=c.vscale, body_type=self.type)
+        for k, v in kw.items():
+            setattr(a, k, v)
+        return a
+
+    def create(self, n: int, init=None):
+        """parallel_new<Body>(n): ids 0..n-1, from ``init`` (n x 5 floats) or the seed."""
+        self.n = n
+        self.handle_of = torch.zeros(max(n, 1), dtype=torch.int64, device=self.device)
+        self._init = None
+        if init is not None:
+            self._init = torch.as_tensor(np.ascontiguousarray(init, dtype=np.float32).reshape(-1)).to(self.device)
+        self.heap.parallel_new(self.type, n, D.C_NBODY, self.args(init=D._addr(self._init)))
+
+    def step(self):
+        """One step: a single enumeration, every other do-all on its snapshot (no
+        Body is created during a step; DELETE only deletes itself)."""
+        a = self.args()
+        self.heap.parallel_do(self.type, self.force_method, a)
+        self.heap.parallel_do_enumerated(self.type, D.M_NBODY_MOVE, a)
+        if self.collide:
+            for m in (D.M_COLL_FIND, D.M_COLL_CLAIM, D.M_COLL_MERGE, D.M_COLL_DELETE):
+                self.heap.parallel_do_enumerated(self.type, m, a)
+
+    def force(self):
+        """FORCE alone (adds the pair sums to the force fields, which MOVE clears)."""
+        self.heap.parallel_do(self.type, self.force_method, self.args())
+
+    def read(self, forces: bool = False):
+        """(state float32[n, 5] by id: px py vx vy m, alive uint8[n]) and, with
+        ``forces``, the fixed-point forces int64[n, 2]."""
+        out = torch.zeros(max(self.n, 1) * 5, dtype=torch.float32, device=self.device)
+        alive = torch.zeros(max(self.n, 1), dtype=torch.uint8, device=self.device)
+        fo = torch.zeros(max(self.n, 1) * 2, dtype=torch.int64, device=self.device) if forces else None
+        self.heap.parallel_do(self.type, D.M_NBODY_READ,
+                              self.args(out=out.data_ptr(), alive_out=alive.data_ptr(), force_out=D._addr(fo)))
+        res = (out.view(-1, 5)[:self.n].cpu().numpy(), alive[:self.n].cpu().numpy())
+        if forces:
+            res += (fo.view(-1, 2)[:self.n].cpu().numpy(),)
+        return res
+
+    def count(self) -> int:
+        return self.heap.count(self.type)

@@ -94,6 +94,8 @@ int dsoa_wator_do(dsoa_heap* h, int type, int method, const void* a, size_t nb);
 int dsoa_wator_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_t nb);
 int dsoa_traffic_do(dsoa_heap* h, int type, int method, const void* a, size_t nb);
 int dsoa_traffic_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_t nb);
+int dsoa_nbody_new(dsoa_heap* h, int type, uint64_t n, int ctor, const void* a, size_t nb);
+int dsoa_nbody_do(dsoa_heap* h, int type, int method, const void* a, size_t nb);
 
 #define DSOA_CUDA_TRY(expr)                              \
     do {                                                 \

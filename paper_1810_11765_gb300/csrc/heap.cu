@@ -676,6 +676,7 @@ int dsoa_parallel_new(dsoa_heap* h, int type, uint64_t n, int ctor_id, const voi
     if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
     if (ctor_id >= 100 && ctor_id < 200) return dsoa_micro_new(h, type, n, ctor_id, args, nb);
     if (ctor_id >= 200 && ctor_id < 300) return dsoa_gol_new(h, type, n, ctor_id, args, nb);
+    if (ctor_id >= 500 && ctor_id < 600) return dsoa_nbody_new(h, type, n, ctor_id, args, nb);
     return DSOA_ERR_UNKNOWN_METHOD;
 }
 
@@ -687,6 +688,7 @@ int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args, si
     if (method_id >= 200 && method_id < 300) return dsoa_gol_do(h, type, method_id, args, nb);
     if (method_id >= 300 && method_id < 400) return dsoa_wator_do(h, type, method_id, args, nb);
     if (method_id >= 400 && method_id < 500) return dsoa_traffic_do(h, type, method_id, args, nb);
+    if (method_id >= 500 && method_id < 600) return dsoa_nbody_do(h, type, method_id, args, nb);
     return DSOA_ERR_UNKNOWN_METHOD;
 }
 

@@ -37,6 +37,9 @@ M_WATOR_FISH_CHOOSE, M_WATOR_FISH_MOVE, M_WATOR_SHARK_CHOOSE, M_WATOR_SHARK_MOVE
 M_WATOR_KILL, K_WATOR_INIT, K_WATOR_ADVANCE = 305, 350, 351
 M_TRAFFIC_MOVE, M_TRAFFIC_READ = 401, 402
 K_TRAFFIC_INIT, K_TRAFFIC_CLEAR, K_TRAFFIC_ONRAMP, K_TRAFFIC_ADVANCE = 450, 451, 452, 453
+C_NBODY, M_NBODY_FORCE, M_NBODY_MOVE = 500, 501, 502
+M_COLL_FIND, M_COLL_CLAIM, M_COLL_MERGE, M_COLL_DELETE = 503, 504, 505, 506
+M_NBODY_READ, M_NBODY_FORCE_TILED = 507, 508
 
 INST_IDLE, INST_RUN, INST_KILL = 0, 1, 2
 
@@ -76,6 +79,14 @@ class TrafficArgs(ctypes.Structure):
                 ("init_occ", P), ("init_v", P), ("t_dev", P), ("seed", ctypes.c_uint64),
                 ("n_rings", ctypes.c_uint32), ("slow_thr", ctypes.c_uint32),
                 ("ramp_thr", ctypes.c_uint32), ("car_type", ctypes.c_int32)]
+
+
+class NBodyArgs(ctypes.Structure):
+    _fields_ = [("handle_of", P), ("init", P), ("out", P), ("alive_out", P), ("force_out", P),
+                ("seed", ctypes.c_uint64), ("n_ids", ctypes.c_uint32), ("mass_max", ctypes.c_uint32),
+                ("G", ctypes.c_float), ("dt", ctypes.c_float), ("eps2", ctypes.c_float),
+                ("rc2", ctypes.c_float), ("fscale", ctypes.c_float), ("vscale", ctypes.c_float),
+                ("body_type", ctypes.c_int32), ("pad", ctypes.c_uint32)]
 
 
 # exported names of include/dsoa.h, in declaration order

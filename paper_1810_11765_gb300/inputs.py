@@ -11,6 +11,7 @@ Workload recipe (shapes follow the paper's applications, Table 1 and Sec. 6):
   * game of life: 512 x 512 torus, density 1/4, 200 generations
   * wa-tor: 1024 x 1024 torus, 30 % fish / 5 % sharks, 500 steps
   * traffic: 64 rings, length floor(2^(12 + 8u)), density U(0.1, 0.3), 1000 steps
+  * n-body / collisions: 65,536 bodies in [-1, 1)^2, integer masses 1..16
   * serving: Poisson arrivals of game-of-life / wa-tor instances, side
     2^U(8, 12), U(100, 1000) steps
 """
@@ -27,6 +28,8 @@ SEED_GOL = SEED_BASE + 1
 SEED_WATOR = SEED_BASE + 2
 SEED_TRAFFIC = SEED_BASE + 3
 SEED_SERVING = SEED_BASE + 4
+SEED_NBODY = SEED_BASE + 5
+SEED_COLLISION = SEED_BASE + 6
 
 
 @dataclass(frozen=True)
@@ -43,6 +46,22 @@ class GolConfig:
     height: int = 512
     gens: int = 200
     seed: int = SEED_GOL
+
+
+@dataclass(frozen=True)
+class NBodyConfig:
+    """n-body / collision parameters (the paper gives none; 65,536 bodies as in its
+    n-body listing).  G and fscale are powers of two."""
+    n: int = 1 << 16
+    steps: int = 10
+    G: float = 2.0 ** -30
+    dt: float = 0.25
+    eps2: float = 2.0 ** -18
+    rc2: float = 2.0 ** -18
+    fscale: float = 2.0 ** 40
+    vscale: float = 2.0 ** -8
+    mass_max: int = 16
+    seed: int = SEED_NBODY
 
 
 @dataclass(frozen=True)

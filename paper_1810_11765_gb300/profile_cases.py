@@ -4,6 +4,7 @@
   python -m paper_1810_11765_gb300.profile_cases wator --side 1024 --steps 3
   python -m paper_1810_11765_gb300.profile_cases alloc --log2n 22
   python -m paper_1810_11765_gb300.profile_cases atomic --iters 64
+  python -m paper_1810_11765_gb300.profile_cases nbody --n 16384 [--walk] [--iters 3]
 
 Each case prints CUDA-event timings of its kernels (without a profiler attached
 these are the numbers to trust) and keeps its device footprint to a few hundred MB
@@ -17,7 +18,7 @@ import statistics
 import torch
 
 from . import build, dsoa as D
-from .apps import Micro, WatorWorld
+from .apps import Micro, NBodyWorld, WatorWorld
 
 
 def _ev():
@@ -103,9 +104,33 @@ def case_atomic(iters: int):
     m.heap.close()
 
 
+def case_nbody(n: int, walk: bool, iters: int):
+    """FORCE over n bodies of the configured n-body workload: the pairwise tiled
+    kernel, or (walk) the per-thread device_do walk."""
+    from . import inputs
+    cfg = inputs.NBodyConfig()
+    heap = D.Heap(max(64 << 20, n * 256))
+    w = NBodyWorld(heap, cfg, tiled=not walk)
+    heap.freeze()
+    w.create(n)
+    for _ in range(iters):
+        a, b = _ev(), _ev()
+        a.record()
+        w.force()
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        print(f"nbody[{'walk' if walk else 'tiled'}] n={n}: FORCE {ms:.4f} ms, "
+              f"{n * (n - 1) / ms / 1e6:.2f} G pair terms/s")
+    print("err", heap.get_error())
+    heap.close()
+
+
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("case", choices=["doall", "wator", "alloc", "atomic"])
+    p.add_argument("case", choices=["doall", "wator", "alloc", "atomic", "nbody"])
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--walk", action="store_true")
     p.add_argument("--log2n", type=int, default=24)
     p.add_argument("--holes", action="store_true")
     p.add_argument("--iters", type=int, default=3)
@@ -120,6 +145,8 @@ def main():
         case_wator(a.side, a.steps)
     elif a.case == "atomic":
         case_atomic(a.iters)
+    elif a.case == "nbody":
+        case_nbody(a.n, a.walk, a.iters)
     else:
         case_alloc(a.log2n)
 

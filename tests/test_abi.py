@@ -75,6 +75,8 @@ int main(void) {
   S(dsoa_gol_args) O(dsoa_gol_args, n_inst) O(dsoa_gol_args, alive_type)
   S(dsoa_wator_args) O(dsoa_wator_args, shark_type)
   S(dsoa_traffic_args) O(dsoa_traffic_args, seed) O(dsoa_traffic_args, car_type)
+  S(dsoa_nbody_args) O(dsoa_nbody_args, seed) O(dsoa_nbody_args, n_ids) O(dsoa_nbody_args, G)
+  O(dsoa_nbody_args, vscale) O(dsoa_nbody_args, body_type)
   return 0;
 }
 """
@@ -89,7 +91,7 @@ def test_ctypes_layouts_match_c_headers(tmp_path):
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     py = {"dsoa_micro_args": D.MicroArgs, "dsoa_micro_stats": D.MicroStats, "dsoa_inst": D.Inst,
           "dsoa_gol_args": D.GolArgs, "dsoa_wator_args": D.WatorArgs,
-          "dsoa_traffic_args": D.TrafficArgs}
+          "dsoa_traffic_args": D.TrafficArgs, "dsoa_nbody_args": D.NBodyArgs}
     n = 0
     for ln in lines:
         if not ln:

@@ -183,3 +183,29 @@ def test_initial_draw():
     assert np.all(np.abs(hist - n / 16) < 5 * math.sqrt(n / 16))
     # distinct draws per body: no two bodies share a position
     assert len({(a, b) for a, b in s[:, :2].tolist()}) == n
+
+
+def test_force_on_single_bodies():
+    # closed form of the pair at rest, on the fixed-point grid
+    G, a, m, eps2 = 2.0 ** -10, 0.25, 2.0, 2.0 ** -6
+    st = np.array([[-a, 0, 0, 0, m], [a, 0, 0, 0, m]], np.float32)
+    f = oracle.nbody_force_on(st, [0, 1], G=G, eps2=eps2)
+    d2 = (2 * a) ** 2 + eps2
+    assert f[0, 0] == pytest.approx(G * m * m * 2 * a / d2 ** 1.5 * S, rel=1e-6)
+    assert f[1, 0] == -f[0, 0] and f[0, 1] == 0 and f[1, 1] == 0
+    # the forces of a random state sum to zero, and the first step of a run moves
+    # each body by exactly those forces
+    kw = dict(G=2.0 ** -20, eps2=2.0 ** -18)
+    s0, _, _, _ = oracle.nbody_run(300, 0, 21, dt=0.25, **kw)
+    F = oracle.nbody_force_on(s0, range(300), **kw)
+    assert np.all(F.sum(0) == 0) and np.abs(F).max() > 0
+    s1, _, _, _ = oracle.nbody_run(300, 1, 21, dt=0.25, **kw)
+    f32 = np.float32
+    ax = (F[:, 0].astype(f32) * f32(2.0 ** -40)) / s0[:, 4]
+    vx = s0[:, 2] + ax * f32(0.25)
+    assert np.array_equal(s1[:, 2], vx)
+    # dead bodies exert no force
+    alive = np.ones(300, np.uint8)
+    alive[::2] = 0
+    Fa = oracle.nbody_force_on(s0, [1], alive, **kw)
+    assert Fa[0, 0] == oracle.nbody_force_on(s0[1::2], [0], **kw)[0, 0]
