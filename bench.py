@@ -479,6 +479,89 @@ def app_steps(kind, steps, flush, warmup=3, side=None, heap_bytes=1 << 30):
     return res
 
 
+# Algorithmic operations of one pair term of the n-body force: dx, dy (2 sub),
+# d2 (2 mul, 2 add), sqrt, reciprocal, d^-3 (2 mul), G S m_i m_j (1 mul), k (1 mul),
+# k dx, k dy (2 mul), two conversions to the fixed-point grid, two 64-bit adds.
+NBODY_OPS_PER_PAIR = 19
+
+
+def fp32_lane_peak(clock_mhz):
+    """FP32 lane operations per second: SMs x 128 lanes x SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * 128 * clock_mhz * 1e6
+
+
+def nbody_leg(flush, steps=5, collide_steps=10):
+    """n-body (65,536 bodies, the listing's size): FORCE by the pairwise tiled
+    kernel and by the per-thread device_do walk, steps/s plain vs graph;
+    particle collisions on the same bodies (six do-alls per step)."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D, inputs
+    from paper_1810_11765_gb300.apps import NBodyWorld
+    cfg = inputs.NBodyConfig()
+    n = cfg.n
+    out = {"workload": f"n-body {n} bodies in [-1,1)^2, integer masses 1..{cfg.mass_max}, G=2^-30, dt=1/4",
+           "pairs_per_force": n * (n - 1)}
+    for tiled in (True, False):
+        heap = D.Heap(256 << 20)
+        w = NBodyWorld(heap, cfg, tiled=tiled)
+        heap.freeze()
+        w.create(n)
+        w.step()
+        torch.cuda.synchronize()
+        k = steps if tiled else 1
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(k):
+            w.force()
+        b.record()
+        b.synchronize()
+        force_ms = a.elapsed_time(b) / k
+        w.step()          # apply (and clear) the forces accumulated above
+        key = "tiled" if tiled else "device_do"
+        out[f"force_ms_{key}"] = force_ms
+        out[f"pair_terms_per_s_{key}"] = n * (n - 1) / (force_ms / 1e3)
+        if tiled:
+            for mode in ("plain", "graph"):
+                g = None
+                if mode == "graph":
+                    heap.graph_begin()
+                    w.step()
+                    g = heap.graph_end()
+                step = (lambda: g.launch()) if g else w.step
+                step()
+                torch.cuda.synchronize()
+                a, b = ev(), ev()
+                a.record()
+                for _ in range(steps):
+                    step()
+                b.record()
+                b.synchronize()
+                out[f"{mode}_steps_per_s"] = steps / (a.elapsed_time(b) / 1e3)
+                if g:
+                    g.close()
+        out[f"device_errors_{key}"] = heap.get_error()
+        heap.close()
+    # collisions: 10 steps from the initial draw, plain launches
+    heap = D.Heap(256 << 20)
+    w = NBodyWorld(heap, cfg, collide=True, tiled=True)
+    heap.freeze()
+    w.create(n)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(collide_steps):
+        w.step()
+    b.record()
+    b.synchronize()
+    out["collision"] = {"steps": collide_steps, "steps_per_s": collide_steps / (a.elapsed_time(b) / 1e3),
+                        "bodies_after": w.count(), "device_errors": heap.get_error()}
+    heap.close()
+    return out
+
+
 def serving_leg(n_req=24, rates=(50.0, 200.0)):
     """Continuous batching of game-of-life / wa-tor instances (sides 2^8..2^10 and
     100..300 steps to bound the run time) at swept Poisson arrival rates."""
@@ -641,6 +724,16 @@ def dsoa_arm(args):
         out["gol_4096"] = app_steps("gol", 20, flush, side=4096)
         out["traffic_64_rings"] = app_steps("traffic", 50, flush)
         out["serving"] = serving_leg()
+        nb = nbody_leg(flush)
+        clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak_ops = fp32_lane_peak(clk_mhz)
+        ach = nb["pair_terms_per_s_tiled"] * NBODY_OPS_PER_PAIR
+        nb["roofline"] = {"kernel": "k_force_tiled", "bound": "alu", "achieved": ach / 1e12,
+                          "peak": peak_ops / 1e12, "unit": "Tops/s", "frac": ach / peak_ops,
+                          "traffic": None, "ops_per_pair": NBODY_OPS_PER_PAIR,
+                          "peak_kind": f"derived: SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (median SM clock "
+                                       "of the headline run)"}
+        out["nbody_65536"] = nb
         # --- end to end through host buffers
         out["e2e"] = e2e_wator(seed, args.warmup, args.steps, flush)
         # --- oracle on the host cores
