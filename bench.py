@@ -277,6 +277,78 @@ def doall_sweep(log2n, holes, flush, iters=10, kernel="vec128"):
             "single_launch_ms": statistics.median(single), "err": err}
 
 
+def bitmap_legs(flush):
+    """BitmapAlloc (Sec. 6), the flat AOS bitmap allocator, on the same microbench
+    workloads as DynaSOAr: do-all HBM GB/s on 2^26 objects (full and 50 % holes),
+    the alloc/free storm at 2^24 and the heap utilisation of a 1 GiB heap."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import Micro
+    out = {}
+    for holes in (False, True):
+        n = 1 << 26
+        nbytes = int(n * 16 * 1.1) + (64 << 20)
+        m = Micro(nbytes, 0x5EED0001, n, heap=D.BitmapHeap(nbytes))
+        m.new(0)
+        if holes:
+            m.delete(0)
+        live = m.heap.count(m.type)
+        m.scale()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record()
+            m.scale()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        out[f"doall_2^26{'_holes' if holes else ''}"] = {
+            "objects": live, "ms": ms, "gbs": live * 12 / ms / 1e6, "err": m.heap.get_error(),
+            "note": "snapshot copy + do-all over the allocation bitmap, L2 flushed before each launch"}
+        m.heap.close()
+        del m
+        torch.cuda.empty_cache()
+    n = 1 << 24
+    nbytes = int(n * 16 * 1.2) + (64 << 20)
+    m = Micro(nbytes, 0x5EED0001, n, heap=D.BitmapHeap(nbytes))
+    res = []
+    for _ in range(3):
+        flush.zero_()
+        a, b, c = ev(), ev(), ev()
+        a.record()
+        m.new(0)
+        b.record()
+        m.heap.parallel_do(m.type, D.M_MICRO_DELETE_ALL, m.args())
+        c.record()
+        c.synchronize()
+        res.append((a.elapsed_time(b), b.elapsed_time(c)))
+    new_ms = statistics.median(r[0] for r in res)
+    del_ms = statistics.median(r[1] for r in res)
+    out["alloc_free_2^24"] = {"new_ms": new_ms, "delete_ms": del_ms, "ops_per_s": 2 * n / ((new_ms + del_ms) / 1e3),
+                              "left": m.heap.count(m.type), "err": m.heap.get_error()}
+    m.heap.close()
+    del m
+    torch.cuda.empty_cache()
+    heap_bytes = 1 << 30
+    m = Micro(heap_bytes, 0x5EED0001, 1 << 20, heap=D.BitmapHeap(heap_bytes))
+    cap = m.heap.info()["num_slots"]
+    rnd = 0
+    while True:
+        m.new(rnd)
+        rnd += 1
+        if m.heap.get_error() or rnd * (1 << 20) > cap + (1 << 20):
+            break
+    live = m.heap.count(m.type)
+    out["heap_utilisation"] = {"heap_bytes": heap_bytes, "objects": live, "object_bytes": 16,
+                               "utilisation": live * 16 / heap_bytes}
+    m.heap.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def alloc_free_storm(log2n, flush, iters=3):
     """parallel_new of 2^log2n objects into an empty heap, then delete-all."""
     import torch
@@ -719,6 +791,7 @@ def dsoa_arm(args):
         out["alloc_free_sweep"] = sweep
         out["alloc_roofline"] = alloc_roofline(storm, out["l2_atomic_peak"])
         out["heap_utilisation"] = heap_utilisation()
+        out["bitmapalloc"] = bitmap_legs(flush)
         # --- other apps (plain vs graph) and serving
         out["gol_512"] = app_steps("gol", 100, flush)
         out["gol_4096"] = app_steps("gol", 20, flush, side=4096)

@@ -224,6 +224,52 @@ int dsoa_heap_destroy(dsoa_heap* h);
 /* Human-readable name of an error code. */
 const char* dsoa_error_string(int code);
 
+/* ---- BitmapAlloc: the paper's second allocator (Sec. 6, "BitmapAlloc") ----
+ * The heap is one array of equal-size object records in array-of-structures
+ * layout (no blocks, no SOA columns), whose slots are managed by hierarchical
+ * bitmaps like DynaSOAr's blocks: one free-slot bitmap and one allocation
+ * bitmap per type (Sec. 4.1 operations over object slots).  new takes a free
+ * bit and sets it in the type's allocation bitmap; delete clears it and frees
+ * the slot; a do-all copies the allocation bitmap to an iteration snapshot and
+ * runs one thread per snapshot bit.  It measures pure bitmap allocation
+ * without DynaSOAr's block structure and SOA layout; every type occupies a
+ * record of the largest type's size (internal fragmentation).
+ *
+ * Same conventions as the DynaSOAr heap (return codes, stream order, sticky
+ * device error word).  Built in: the microbench's constructor and methods
+ * (dsoa_apps.h ids 100-107 except the handle-map method; the SCALE variants all
+ * run the plain per-object method) on types with fields {4, 4, 8}; any other
+ * id returns DSOA_ERR_UNKNOWN_METHOD. */
+typedef struct dsoa_bitmap_heap dsoa_bitmap_heap;
+/* cudaMalloc'd heap of `bytes`, records and bitmaps carved at freeze. */
+int dsoa_bitmap_heap_create(size_t bytes, void* stream, dsoa_bitmap_heap** out);
+/* A type of `nfields` fields (1, 2, 4, 8 or 16 bytes), laid out in declaration
+ * order at natural alignment inside a record; before the first allocation. */
+int dsoa_bitmap_register_type(dsoa_bitmap_heap* h, const uint32_t* field_bytes, int nfields, int* type_out);
+/* Freeze: record bytes = largest type (16-byte aligned above 8 bytes); slots =
+ * as many records as fit beside the bitmaps; every slot free. */
+int dsoa_bitmap_heap_freeze(dsoa_bitmap_heap* h);
+int dsoa_bitmap_heap_info(dsoa_bitmap_heap* h, uint64_t* num_slots, uint32_t* record_bytes,
+                          uint32_t* num_levels);
+/* parallel_new<T>(n): thread i takes a free slot (DSOA_DEV_OOM when none) and
+ * runs constructor `ctor_id` with index i. */
+int dsoa_bitmap_parallel_new(dsoa_bitmap_heap* h, int type, uint64_t n, int ctor_id,
+                             const void* args_host, size_t args_bytes);
+/* parallel_do<T, f>: snapshot of the allocation bitmap, then method `method_id`
+ * on every object of the snapshot. */
+int dsoa_bitmap_parallel_do(dsoa_bitmap_heap* h, int type, int method_id, const void* args_host,
+                            size_t args_bytes);
+/* Live objects of `type` (popcount of its allocation bitmap).  Synchronous. */
+int dsoa_bitmap_count(dsoa_bitmap_heap* h, int type, uint64_t* out_host);
+/* Invariants at quiescence into out_host[3]: hierarchy mismatches, slots not
+ * exactly one of {free, allocated to one type}, bits past the last slot.
+ * All zero when consistent.  Synchronous. */
+int dsoa_bitmap_check(dsoa_bitmap_heap* h, uint64_t* out_host);
+/* Read and clear the sticky device error word.  Synchronous. */
+int dsoa_bitmap_get_error(dsoa_bitmap_heap* h, int* bits_out);
+/* Waits for the heap's stream, frees the heap memory and the handle. */
+int dsoa_bitmap_heap_destroy(dsoa_bitmap_heap* h);
+
 /* ---- Enumeration without allocation (the paper has no counterpart) ----
  * For callers that cannot allocate device memory while they run: a host
  * program whose own allocator owns the GPU's memory under a fixed budget, a

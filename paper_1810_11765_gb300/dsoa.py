@@ -98,7 +98,11 @@ ABI_FUNCTIONS = [
     "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
     "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_set_lookups",
     "dsoa_type_stats", "dsoa_launch_count",
-    "dsoa_heap_destroy", "dsoa_error_string", "dsoa_enumerate_noalloc",
+    "dsoa_heap_destroy", "dsoa_error_string",
+    "dsoa_bitmap_heap_create", "dsoa_bitmap_register_type", "dsoa_bitmap_heap_freeze",
+    "dsoa_bitmap_heap_info", "dsoa_bitmap_parallel_new", "dsoa_bitmap_parallel_do",
+    "dsoa_bitmap_count", "dsoa_bitmap_check", "dsoa_bitmap_get_error", "dsoa_bitmap_heap_destroy",
+    "dsoa_enumerate_noalloc",
 ]
 
 _lib = None
@@ -135,6 +139,12 @@ def load(path: str | None = None):
         "dsoa_set_lookups": [vp, i32], "dsoa_type_stats": [vp, i32, vp],
         "dsoa_error_string": [i32],
         "dsoa_enumerate_noalloc": [vp, i32, vp, vp, vp, u64],
+        "dsoa_bitmap_heap_create": [sz, vp, vp], "dsoa_bitmap_register_type": [vp, vp, i32, vp],
+        "dsoa_bitmap_heap_freeze": [vp], "dsoa_bitmap_heap_info": [vp, vp, vp, vp],
+        "dsoa_bitmap_parallel_new": [vp, i32, u64, i32, vp, sz],
+        "dsoa_bitmap_parallel_do": [vp, i32, i32, vp, sz], "dsoa_bitmap_count": [vp, i32, vp],
+        "dsoa_bitmap_check": [vp, vp], "dsoa_bitmap_get_error": [vp, vp],
+        "dsoa_bitmap_heap_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -343,3 +353,65 @@ class Heap:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BitmapHeap:
+    """BitmapAlloc (dsoa_bitmap_heap): one array of equal-size AOS records managed by
+    a free-slot bitmap and one allocation bitmap per type.  Offers the subset of
+    ``Heap``'s methods that the microbench driver uses."""
+
+    def __init__(self, nbytes: int, stream=None):
+        self._h = ctypes.c_void_p()
+        self.stream = stream
+        _ok(load().dsoa_bitmap_heap_create(int(nbytes), _stream_ptr(stream), ctypes.byref(self._h)),
+            "dsoa_bitmap_heap_create")
+
+    def register_type(self, field_bytes) -> int:
+        fb = (ctypes.c_uint32 * len(field_bytes))(*field_bytes)
+        t = ctypes.c_int()
+        _ok(load().dsoa_bitmap_register_type(self._h, fb, len(field_bytes), ctypes.byref(t)),
+            "dsoa_bitmap_register_type")
+        return t.value
+
+    def freeze(self):
+        _ok(load().dsoa_bitmap_heap_freeze(self._h), "dsoa_bitmap_heap_freeze")
+
+    def info(self) -> dict:
+        n, rb, nl = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+        _ok(load().dsoa_bitmap_heap_info(self._h, ctypes.byref(n), ctypes.byref(rb), ctypes.byref(nl)),
+            "dsoa_bitmap_heap_info")
+        return {"num_slots": n.value, "record_bytes": rb.value, "num_levels": nl.value}
+
+    def parallel_new(self, t: int, n: int, ctor: int, args):
+        _ok(load().dsoa_bitmap_parallel_new(self._h, t, n, ctor, ctypes.byref(args), ctypes.sizeof(args)),
+            "dsoa_bitmap_parallel_new")
+
+    def parallel_do(self, t: int, method: int, args):
+        _ok(load().dsoa_bitmap_parallel_do(self._h, t, method, ctypes.byref(args), ctypes.sizeof(args)),
+            "dsoa_bitmap_parallel_do")
+
+    def count(self, t: int) -> int:
+        out = ctypes.c_uint64()
+        _ok(load().dsoa_bitmap_count(self._h, t, ctypes.byref(out)), "dsoa_bitmap_count")
+        return out.value
+
+    def get_error(self) -> int:
+        out = ctypes.c_int()
+        _ok(load().dsoa_bitmap_get_error(self._h, ctypes.byref(out)), "dsoa_bitmap_get_error")
+        return out.value
+
+    def check(self) -> dict:
+        out = (ctypes.c_uint64 * 3)()
+        _ok(load().dsoa_bitmap_check(self._h, out), "dsoa_bitmap_check")
+        return {"hier": out[0], "free_xor": out[1], "tail": out[2]}
+
+    def close(self):
+        if self._h:
+            load().dsoa_bitmap_heap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
