@@ -176,7 +176,8 @@ def run_wator(seed, warmup, steps, mode, flush, launch=None):
     err = heap.get_error()
     fs, ss = heap.type_stats(w.fish_type), heap.type_stats(w.shark_type)
     blocks = fs["blocks"] + ss["blocks"]
-    frag = {"blocks": blocks, "F": 1.0 - (fs["objects"] + ss["objects"]) / (64.0 * blocks) if blocks else 0.0}
+    slots = fs["slots"] + ss["slots"]
+    frag = {"blocks": blocks, "F": 1.0 - (fs["objects"] + ss["objects"]) / slots if slots else 0.0}
     if g:
         g.close()
     heap.close()

@@ -68,17 +68,36 @@ int dsoa_heap_create_from(void* dev_ptr, size_t bytes, void* stream, dsoa_heap**
  * layout froze. */
 int dsoa_register_type(dsoa_heap* h, const uint32_t* field_bytes, int nfields, int* type_out);
 
-/* Freeze the layout: block bytes = largest registered type's data segment;
- * M = blocks that fit with their metadata.  Initialises the bitmaps (every block
- * free, Sec. 3.4).  Called implicitly by the first allocating call. */
+/* Freeze the layout.  Uniform capacity (the default): every type has 64 slots
+ * per block and block bytes = the largest registered type's 64-slot data
+ * segment.  Per-type capacity (dsoa_set_capacity_mode): see below.  M = blocks
+ * that fit with their metadata.  Initialises the bitmaps (every block free,
+ * Sec. 3.4).  Called implicitly by the first allocating call. */
 int dsoa_heap_freeze(dsoa_heap* h);
 
 /* Query the frozen layout (any pointer may be NULL). */
 int dsoa_heap_info(dsoa_heap* h, uint64_t* num_blocks, uint32_t* block_bytes,
                    uint32_t* num_levels, uint64_t* metadata_bytes);
 
-/* Column byte offset of field `field` of `type` inside a block's data segment. */
+/* Column byte offset of field `field` of `type` inside a block's data segment
+ * (final once the layout froze; before that, the uniform-capacity offset). */
 int dsoa_field_offset(dsoa_heap* h, int type, int field, uint32_t* offset_out);
+
+/* Block capacity mode, before the layout freezes (DSOA_ERR_FROZEN after).
+ * DSOA_CAPACITY_PER_TYPE follows Sec. 3.2 "Block Capacity": a block holds 64
+ * objects of the smallest type T_s (by summed field bytes), so its data
+ * segment is T_s's 64 128-byte-aligned columns, and every type T gets
+ * N_T = floor(64 size(T_s) / size(T)) slots, lowered until its columns
+ * (16-byte aligned when N_T < 64) fit.  Smaller blocks for small types; larger
+ * types trade slots for bytes.  A type more than 64 times larger than T_s
+ * makes the freeze fail with DSOA_ERR_INVALID_ARG.  Slots at or above N_T stay
+ * marked free in the block's slot word and are never reserved. */
+#define DSOA_CAPACITY_UNIFORM 0
+#define DSOA_CAPACITY_PER_TYPE 1
+int dsoa_set_capacity_mode(dsoa_heap* h, int mode);
+
+/* Slots per block of `type` (64, or N_T), after the freeze. */
+int dsoa_type_capacity(dsoa_heap* h, int type, uint32_t* n_out);
 
 /* parallel_new<T>(n) (Sec. 2.1): one kernel, n logical threads; thread i
  * allocates one object of `type` and runs built-in constructor `ctor_id` with
@@ -155,7 +174,9 @@ int dsoa_get_error(dsoa_heap* h, int* bits_out);
 #define DSOA_CHECK_EMPTY_ALLOC 6   /* allocated block with no object               */
 #define DSOA_CHECK_ACTIVE_EXACT 7  /* active != (allocated and not full)           */
 #define DSOA_CHECK_TAIL_BITS 8     /* bits beyond M set                            */
-#define DSOA_CHECK_COUNT 9
+#define DSOA_CHECK_CAP_BITS 9      /* allocated block with a slot beyond its type's
+                                      capacity not marked free                      */
+#define DSOA_CHECK_COUNT 10
 int dsoa_check(dsoa_heap* h, uint64_t* out_host);
 
 /* Copy the raw allocator state to host memory (synchronous), for external

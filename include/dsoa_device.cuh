@@ -89,6 +89,11 @@ struct dsoa_ctx {
     uint32_t lookups;                    /* active-block lookups before the slow path
                                             (r of Sec. 4.2 / Fig. 11), >= 1           */
     uint16_t col_off[DSOA_MAX_TYPES][DSOA_MAX_FIELDS];
+    unsigned long long cap[DSOA_MAX_TYPES];  /* usable slots of a block of type t (Sec. 3.2
+                                            block capacity N_T): the low N_T bits.  The
+                                            slots above stay marked free in the slot word
+                                            and are never reserved, so occupancy (~word),
+                                            EMPTY and invalidation need no mask        */
 };
 
 /* Register cap of the generic do-all kernel.  Methods that allocate are chains
@@ -361,7 +366,7 @@ __device__ __forceinline__ void dsoa_block_release(const dsoa_ctx& c, uint32_t t
         bits &= ~before;
         if (!bits) return;
     }
-    if (before == 0ull) dsoa_block_first_free(c, t, bid);                    /* FIRST */
+    if ((before & c.cap[t]) == 0ull) dsoa_block_first_free(c, t, bid);       /* FIRST */
     if ((before | bits) == DSOA_ALL) dsoa_block_invalidate(c, bid);          /* EMPTY */
 }
 
@@ -435,10 +440,10 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
                 __nanosleep(256u);
                 continue;
             }
-            w = DSOA_ALL;              /* just initialised by this thread */
+            w = c.cap[t];              /* just initialised by this thread */
         }
         if (!w) {
-            w = dsoa_ld(&c.slot[bid]);
+            w = dsoa_ld(&c.slot[bid]) & c.cap[t];
             if (!w) continue;
         }
         const uint32_t r = rot ? (dsoa_hash(h + round) & 63u) : 0u;
@@ -447,12 +452,13 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
          * fence of dsoa_block_init whose slot-word store this RMW follows */
         const unsigned long long before = dsoa_and_acquire(&c.slot[bid], ~mask);
         const unsigned long long got = before & mask;
-        const unsigned long long left = before & ~mask;
         if (!got) {
+            const unsigned long long left = before & c.cap[t];
             if (hp) *hp = dsoa_hint{left, left ? (uint64_t)bid : DSOA_NO_HINT_BLOCK};
             continue;
         }
         const uint32_t bt = dsoa_ld32(&c.btype[bid]);
+        const unsigned long long left = before & ~mask & c.cap[bt < c.ntypes ? bt : t];
         const bool full = left == 0ull;
         if (full) dsoa_block_deactivate(c, bt, (uint64_t)bid);
         if (bt != t) {                 /* block replaced by another type: roll back */

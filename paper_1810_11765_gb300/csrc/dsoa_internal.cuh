@@ -18,6 +18,7 @@ struct dsoa_type_info {
     uint32_t field_bytes[DSOA_MAX_FIELDS];
     uint32_t col_off[DSOA_MAX_FIELDS];
     uint32_t data_bytes;  // 64-slot data segment of this type
+    uint32_t capacity;    // slots per block (64, or N_T in the per-type capacity mode)
 };
 
 struct dsoa_heap {
@@ -31,6 +32,7 @@ struct dsoa_heap {
     int ntypes = 0;
     dsoa_type_info types[DSOA_MAX_TYPES];
     bool frozen = false;
+    int capacity_mode = DSOA_CAPACITY_UNIFORM;
 
     // frozen layout
     dsoa_ctx ctx;

@@ -37,6 +37,50 @@ uint64_t hint_slots_for(uint64_t M) {
     return s;
 }
 
+// Block capacity per type (Sec. 3.2): the block holds 64 objects of the
+// smallest type T_s (128-byte columns), and a type T gets
+// N_T = floor(64 size(T_s) / size(T)) slots, lowered until its columns (each
+// 16-byte aligned, so that vector loads stay aligned) fit in that block.
+// Writes the block's data bytes; fails for a type more than 64 times larger
+// than T_s (the limitation the paper states).
+int per_type_capacity(dsoa_heap* h, uint32_t* block_bytes_out) {
+    int s = 0;
+    uint32_t size_s = ~0u;
+    for (int t = 0; t < h->ntypes; ++t) {
+        uint32_t size = 0;
+        for (int f = 0; f < h->types[t].nfields; ++f) size += h->types[t].field_bytes[f];
+        if (size < size_s || (size == size_s && h->types[t].data_bytes < h->types[s].data_bytes)) {
+            size_s = size;
+            s = t;
+        }
+    }
+    const uint32_t block = std::max<uint32_t>(128, h->types[s].data_bytes);
+    for (int t = 0; t < h->ntypes; ++t) {
+        dsoa_type_info& ti = h->types[t];
+        uint32_t size = 0;
+        for (int f = 0; f < ti.nfields; ++f) size += ti.field_bytes[f];
+        uint32_t n = std::min<uint32_t>(64, 64u * size_s / size);
+        for (; n > 0; --n) {
+            uint32_t off = 0;
+            for (int f = 0; f < ti.nfields; ++f)
+                off += (uint32_t)(n == 64 ? align_up(64ull * ti.field_bytes[f], 128)
+                                          : align_up((uint64_t)n * ti.field_bytes[f], 16));
+            if (off <= block) break;
+        }
+        if (n == 0) return DSOA_ERR_INVALID_ARG;
+        uint32_t off = 0;
+        for (int f = 0; f < ti.nfields; ++f) {
+            ti.col_off[f] = off;
+            off += (uint32_t)(n == 64 ? align_up(64ull * ti.field_bytes[f], 128)
+                                      : align_up((uint64_t)n * ti.field_bytes[f], 16));
+        }
+        ti.data_bytes = off;
+        ti.capacity = n;
+    }
+    *block_bytes_out = block;
+    return DSOA_OK;
+}
+
 bool make_layout(uint64_t M, uint32_t block_bytes, int ntypes, Layout* L) {
     const int nbm = 1 + 2 * ntypes;
     if (M == 0) return false;
@@ -391,7 +435,8 @@ __global__ void k_check(dsoa_ctx c, unsigned long long* v) {
             if (c.btype[bid] != talloc) loc[DSOA_CHECK_TYPE]++;
             if (w == DSOA_ALL) loc[DSOA_CHECK_EMPTY_ALLOC]++;
             const bool act = bit_at(dsoa_level(c, dsoa_bm_active(talloc), 0), bid);
-            if (act != (w != 0ull)) loc[DSOA_CHECK_ACTIVE_EXACT]++;
+            if (act != ((w & c.cap[talloc]) != 0ull)) loc[DSOA_CHECK_ACTIVE_EXACT]++;
+            if (~w & ~c.cap[talloc]) loc[DSOA_CHECK_CAP_BITS]++;
         }
     }
     // hierarchy consistency and tail bits, every bitmap and level
@@ -578,6 +623,7 @@ int dsoa_register_type(dsoa_heap* h, const uint32_t* field_bytes, int nfields, i
         off += (uint32_t)align_up((uint64_t)DSOA_SLOTS * fb, 128);
     }
     ti.data_bytes = off;
+    ti.capacity = DSOA_SLOTS;
     h->types[h->ntypes] = ti;
     *type_out = h->ntypes++;
     return DSOA_OK;
@@ -589,7 +635,12 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     if (h->ntypes == 0) return DSOA_ERR_INVALID_ARG;
     if (capturing(h->stream)) return DSOA_ERR_CAPTURE;
     uint32_t block_bytes = 128;
-    for (int t = 0; t < h->ntypes; ++t) block_bytes = std::max(block_bytes, h->types[t].data_bytes);
+    if (h->capacity_mode == DSOA_CAPACITY_PER_TYPE) {
+        const int rc = per_type_capacity(h, &block_bytes);
+        if (rc) return rc;
+    } else {
+        for (int t = 0; t < h->ntypes; ++t) block_bytes = std::max(block_bytes, h->types[t].data_bytes);
+    }
     const int nbm = 1 + 2 * h->ntypes;
     (void)nbm;
     // largest M whose layout fits in the byte budget
@@ -623,8 +674,11 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     c.nlevels = L.nlevels;
     c.block_bytes = block_bytes;
     c.ntypes = (uint32_t)h->ntypes;
-    for (int t = 0; t < h->ntypes; ++t)
+    for (int t = 0; t < h->ntypes; ++t) {
         for (int f = 0; f < h->types[t].nfields; ++f) c.col_off[t][f] = (uint16_t)h->types[t].col_off[f];
+        const uint32_t n = h->types[t].capacity;
+        c.cap[t] = n >= 64 ? DSOA_ALL : ((1ull << n) - 1ull);
+    }
     h->tiles = L.tiles;
     for (int t = 0; t < h->ntypes; ++t) {
         h->R[t] = (uint32_t*)(base + L.off_R) + (uint64_t)t * L.M;
@@ -908,6 +962,20 @@ int dsoa_type_stats(dsoa_heap* h, int type, uint64_t* out_host) {
     if (rc) return rc;
     DSOA_CUDA_TRY(cudaMemcpyAsync(out_host, sc + 8, 16, cudaMemcpyDeviceToHost, h->stream));
     DSOA_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DSOA_OK;
+}
+
+int dsoa_set_capacity_mode(dsoa_heap* h, int mode) {
+    if (!h || (mode != DSOA_CAPACITY_UNIFORM && mode != DSOA_CAPACITY_PER_TYPE)) return DSOA_ERR_INVALID_ARG;
+    if (h->frozen) return DSOA_ERR_FROZEN;
+    h->capacity_mode = mode;
+    return DSOA_OK;
+}
+
+int dsoa_type_capacity(dsoa_heap* h, int type, uint32_t* n_out) {
+    if (!h || !n_out || type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+    if (!h->frozen) return DSOA_ERR_NOT_FROZEN;
+    *n_out = h->types[type].capacity;
     return DSOA_OK;
 }
 

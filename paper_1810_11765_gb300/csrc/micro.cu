@@ -371,6 +371,11 @@ int dsoa_micro_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
     dsoa_micro_args args;
     int rc = dsoa_copy_args(&args, a, nb);
     if (rc) return rc;
+    // The column kernels stream whole 64-slot columns; a type with fewer slots
+    // per block (per-type capacity mode) runs the per-object method instead.
+    if ((method == DSOA_M_MICRO_SCALE || method == DSOA_M_MICRO_SCALE_TMA) && type >= 0 && type < h->ntypes &&
+        h->types[type].capacity != DSOA_SLOTS)
+        method = DSOA_M_MICRO_SCALE_SCALAR;
     switch (method) {
         case DSOA_M_MICRO_SCALE: {
             rc = dsoa_prepare_doall(h, type);

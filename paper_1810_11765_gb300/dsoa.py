@@ -23,7 +23,8 @@ ERRORS = {-1: "invalid argument", -2: "heap layout already frozen", -3: "too man
 DEV_OOM, DEV_SPIN, DEV_DOUBLE_FREE, DEV_BAD_HANDLE = 1, 2, 4, 8
 FLAG_NO_COALESCE, FLAG_NO_ROTATE, FLAG_NO_HINT, FLAG_FUSED, FLAG_PDL = 1, 2, 4, 8, 16
 CHECK_NAMES = ["hier", "free_xor", "multi_type", "active_subset", "type", "free_word",
-               "empty_alloc", "active_exact", "tail_bits"]
+               "empty_alloc", "active_exact", "tail_bits", "cap_bits"]
+CAPACITY_UNIFORM, CAPACITY_PER_TYPE = 0, 1
 
 # built-in ids (dsoa_apps.h)
 C_MICRO, M_MICRO_SCALE, M_MICRO_SCALE_SCALAR, M_MICRO_DELETE = 100, 101, 102, 103
@@ -97,7 +98,7 @@ ABI_FUNCTIONS = [
     "dsoa_free_blocks_async", "dsoa_get_error", "dsoa_check", "dsoa_export_state",
     "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
     "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_set_lookups",
-    "dsoa_type_stats", "dsoa_launch_count",
+    "dsoa_type_stats", "dsoa_launch_count", "dsoa_set_capacity_mode", "dsoa_type_capacity",
     "dsoa_heap_destroy", "dsoa_error_string",
     "dsoa_bitmap_heap_create", "dsoa_bitmap_register_type", "dsoa_bitmap_heap_freeze",
     "dsoa_bitmap_heap_info", "dsoa_bitmap_parallel_new", "dsoa_bitmap_parallel_do",
@@ -137,6 +138,7 @@ def load(path: str | None = None):
         "dsoa_graph_destroy": [vp], "dsoa_set_launch": [vp, i32, i32, i32, i32, i32],
         "dsoa_set_flags": [vp, u32], "dsoa_launch_count": [vp, vp], "dsoa_heap_destroy": [vp],
         "dsoa_set_lookups": [vp, i32], "dsoa_type_stats": [vp, i32, vp],
+        "dsoa_set_capacity_mode": [vp, i32], "dsoa_type_capacity": [vp, i32, vp],
         "dsoa_error_string": [i32],
         "dsoa_enumerate_noalloc": [vp, i32, vp, vp, vp, u64],
         "dsoa_bitmap_heap_create": [sz, vp, vp], "dsoa_bitmap_register_type": [vp, vp, i32, vp],
@@ -235,6 +237,15 @@ class Heap:
     def freeze(self):
         _ok(load().dsoa_heap_freeze(self._h), "dsoa_heap_freeze")
 
+    def set_capacity_mode(self, mode: int):
+        """CAPACITY_UNIFORM (64 slots for every type) or CAPACITY_PER_TYPE (Sec. 3.2 N_T)."""
+        _ok(load().dsoa_set_capacity_mode(self._h, mode), "dsoa_set_capacity_mode")
+
+    def capacity(self, t: int) -> int:
+        n = ctypes.c_uint32()
+        _ok(load().dsoa_type_capacity(self._h, t, ctypes.byref(n)), "dsoa_type_capacity")
+        return n.value
+
     def info(self) -> dict:
         M, bb, nl, meta = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
         _ok(load().dsoa_heap_info(self._h, ctypes.byref(M), ctypes.byref(bb), ctypes.byref(nl),
@@ -320,8 +331,9 @@ class Heap:
         out = (ctypes.c_uint64 * 2)()
         _ok(load().dsoa_type_stats(self._h, t, out), "dsoa_type_stats")
         blocks, objs = int(out[0]), int(out[1])
-        frag = 1.0 - objs / (64.0 * blocks) if blocks else 0.0
-        return {"blocks": blocks, "objects": objs, "fragmentation": frag}
+        cap = self.capacity(t)
+        frag = 1.0 - objs / (float(cap) * blocks) if blocks else 0.0
+        return {"blocks": blocks, "objects": objs, "fragmentation": frag, "slots": cap * blocks}
 
     @property
     def launches(self) -> int:

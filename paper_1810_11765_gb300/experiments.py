@@ -4,6 +4,7 @@
   python -m paper_1810_11765_gb300.experiments lookups   # F vs r            (Fig. 11)
   python -m paper_1810_11765_gb300.experiments ablation  # NoCoal / NoShift  (Fig. 10c)
   python -m paper_1810_11765_gb300.experiments heapsize  # time vs heap size (Fig. 12b)
+  python -m paper_1810_11765_gb300.experiments capacity  # uniform vs per-type block capacity (Sec. 3.2)
 
 Each prints one JSON line.  Workload: Wa-Tor 1024 x 1024, 30 % fish / 5 % sharks,
 seed 0x5EED0003.  Fragmentation F = unused slots / slots of allocated blocks
@@ -21,9 +22,10 @@ from . import build, dsoa as D, inputs
 from .apps import WatorWorld
 
 
-def _world(heap_bytes=512 << 20, flags=0, lookups=None):
+def _world(heap_bytes=512 << 20, flags=0, lookups=None, capacity_mode=D.CAPACITY_UNIFORM):
     heap = D.Heap(heap_bytes)
     w = WatorWorld(heap)
+    heap.set_capacity_mode(capacity_mode)
     heap.freeze()
     heap.set_flags(flags)
     if lookups is not None:
@@ -36,8 +38,9 @@ def _frag(heap, w):
     f, s = heap.type_stats(w.fish_type), heap.type_stats(w.shark_type)
     blocks = f["blocks"] + s["blocks"]
     objs = f["objects"] + s["objects"]
+    slots = f["slots"] + s["slots"]
     return {"fish": f["objects"], "sharks": s["objects"], "blocks": blocks,
-            "F": 1.0 - objs / (64.0 * blocks) if blocks else 0.0}
+            "F": 1.0 - objs / slots if slots else 0.0}
 
 
 def frag_over_time(steps=500, every=25):
@@ -104,15 +107,34 @@ def heap_size(sizes_gib=(0.5, 1, 2, 4, 8, 16), steps=100):
     return {"experiment": f"heap size vs step time, {steps} plain steps (Fig. 12b)", "rows": rows}
 
 
+def capacity(steps=300):
+    """Uniform 64-slot blocks vs per-type block capacity N_T (Sec. 3.2): block
+    bytes, capacities, step rate, fragmentation and the heap bytes held by
+    allocated blocks after `steps` plain steps."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rows = []
+    for name, mode in (("uniform", D.CAPACITY_UNIFORM), ("per_type", D.CAPACITY_PER_TYPE)):
+        heap, w = _world(heap_bytes=512 << 20, capacity_mode=mode)
+        t = _timed_steps(heap, w, steps, flush)
+        fr = _frag(heap, w)
+        bb = heap.info()["block_bytes"]
+        rows.append(dict(mode=name, block_bytes=bb, fish_capacity=heap.capacity(w.fish_type),
+                         shark_capacity=heap.capacity(w.shark_type), steps_per_s=steps / (sum(t) / 1e3),
+                         median_ms=statistics.median(t), bytes_in_blocks=fr["blocks"] * bb, **fr,
+                         device_errors=heap.get_error()))
+        heap.close()
+    return {"experiment": f"block capacity per type, Wa-Tor 1024^2, {steps} plain steps (Sec. 3.2)", "rows": rows}
+
+
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("which", choices=["frag", "lookups", "ablation", "heapsize"])
+    p.add_argument("which", choices=["frag", "lookups", "ablation", "heapsize", "capacity"])
     a = p.parse_args()
     build.build()
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         res = {"frag": frag_over_time, "lookups": frag_vs_lookups, "ablation": ablation,
-               "heapsize": heap_size}[a.which]()
+               "heapsize": heap_size, "capacity": capacity}[a.which]()
     print(json.dumps(res))
 
 

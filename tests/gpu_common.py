@@ -53,28 +53,28 @@ def host_check(heap, ntypes: int) -> dict:
                 bad["hier"] += int(np.sum(bits[:prev_n] != (lower != 0)))
             prev_n = nw
     free = L0[0]
+    # usable slots of a block of each type (block capacity N_T, Sec. 3.2); the
+    # slots above stay marked free in the slot word
+    caps = [heap.capacity(t) for t in range(ntypes)]
+    capmask = [np.uint64(2**64 - 1) if n >= 64 else np.uint64((1 << n) - 1) for n in caps]
     alloc = np.array([L0[1 + 2 * t] for t in range(ntypes)])
     active = np.array([L0[2 + 2 * t] for t in range(ntypes)])
     any_alloc = alloc.any(axis=0)
     bad["free_xor"] = int(np.sum(free == any_alloc)) + int(np.sum(alloc.sum(axis=0) > 1))
     bad["active_subset"] = int(np.sum(active & ~alloc))
     bad["free_word"] = int(np.sum(free & (slot != 0)))
+    bad["cap_bits"] = 0
     live = {}
+    free_slots, total_slots = 0, 0
     for t in range(ntypes):
         sel = alloc[t]
         bad["type"] += int(np.sum(btype[sel] != t))
         bad["empty_alloc"] += int(np.sum(slot[sel] == np.uint64(2**64 - 1)))
-        bad["active_exact"] += int(np.sum(active[t][sel] != (slot[sel] != 0)))
+        bad["active_exact"] += int(np.sum(active[t][sel] != ((slot[sel] & capmask[t]) != 0)))
+        bad["cap_bits"] += int(np.sum((~slot[sel] & ~capmask[t]) != 0))
         occ = ~slot[sel]
         live[t] = int(np.unpackbits(occ.view(np.uint8)).sum())
+        free_slots += int(np.unpackbits((slot[sel] & capmask[t]).view(np.uint8)).sum())
+        total_slots += caps[t] * int(sel.sum())
     return {"violations": bad, "live": live, "blocks_in_use": int(any_alloc.sum()),
-            "fragmentation": fragmentation(slot, any_alloc)}
-
-
-def fragmentation(slot, allocated) -> float:
-    """F of Sec. 6.4: unused slots over all slots of allocated blocks."""
-    n = int(allocated.sum())
-    if n == 0:
-        return 0.0
-    free_slots = int(np.unpackbits(slot[allocated].view(np.uint8)).sum())
-    return free_slots / (64.0 * n)
+            "fragmentation": free_slots / total_slots if total_slots else 0.0}
