@@ -146,7 +146,9 @@ typedef struct {
  * in.  G and the fixed-point scale S are powers of two; masses are integers.
  * The force fields are zero between steps (the constructor and MOVE clear them).
  * n-body step: FORCE (or FORCE_TILED), MOVE.  Collision step: FORCE, MOVE,
- * FIND, CLAIM, MERGE, DELETE (one enumeration; the others reuse its snapshot). */
+ * FIND, CLAIM, MERGE, DELETE (one enumeration; the others reuse its snapshot),
+ * or with DSOA_NBODY_KEYED_FIND: FORCE_TILED, MOVE, FIND_TILED, CLAIM, MERGE,
+ * DELETE. */
 #define DSOA_C_NBODY 500              /* ctor i: body id i from `init` (nullable, 5 floats
                                          px py vx vy m per id) or Philox(seed; 0xFFFFFFFF, i,
                                          k, 0) word 0, k = 0..4; handle_of[i] = handle      */
@@ -167,7 +169,13 @@ typedef struct {
                                          over the enumerated snapshot: CTAs take (256 bodies)
                                          x (a chunk of bodies) tiles staged in shared memory
                                          and add their integer partial sums atomically      */
+#define DSOA_M_COLL_FIND_TILED 509    /* FIND's result by the pairwise kernel, in two halves:
+                                         with DSOA_NBODY_KEYED_FIND, MOVE resets target,
+                                         incoming, merged and sets fx to all ones; this
+                                         method leaves min(bits(d2) << 32 | id) in fx; CLAIM
+                                         turns it into the target and clears fx             */
 #define DSOA_NBODY_NONE 0xFFFFFFFFu   /* no target / no incoming proposal                    */
+#define DSOA_NBODY_KEYED_FIND 1u      /* flags: the step uses FIND_TILED                     */
 typedef struct {
     uint64_t* handle_of;  /* [n_ids] id -> handle; needed by collisions (CLAIM, MERGE read
                              it, the ctor writes it, DELETE clears it); nullable for n-body */
@@ -185,7 +193,7 @@ typedef struct {
     float fscale;         /* fixed-point scale S (power of two)                           */
     float vscale;         /* initial velocities in [-vscale/2, vscale/2)                  */
     int32_t body_type;
-    uint32_t pad;
+    uint32_t flags;       /* DSOA_NBODY_KEYED_FIND (MOVE and CLAIM for FIND_TILED)       */
 } dsoa_nbody_args;
 
 #ifdef __cplusplus

@@ -320,6 +320,7 @@ class NBodyWorld:
         self.heap = heap
         self.cfg = cfg
         self.collide = collide
+        self.tiled = tiled
         self.force_method = D.M_NBODY_FORCE_TILED if tiled else D.M_NBODY_FORCE
         self.type = heap.register_type(self.BODY_FIELDS) if body_type is None else body_type
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -331,7 +332,8 @@ class NBodyWorld:
         c = self.cfg
         a = D.NBodyArgs(handle_of=D._addr(self.handle_of), seed=c.seed, n_ids=self.n,
                         mass_max=c.mass_max, G=c.G, dt=c.dt, eps2=c.eps2, rc2=c.rc2,
-                        fscale=c.fscale, vscale=c.vscale, body_type=self.type)
+                        fscale=c.fscale, vscale=c.vscale, body_type=self.type,
+                        flags=D.NBODY_KEYED_FIND if (self.collide and self.tiled) else 0)
         for k, v in kw.items():
             setattr(a, k, v)
         return a
@@ -352,12 +354,13 @@ class NBodyWorld:
         self.heap.parallel_do(self.type, self.force_method, a)
         self.heap.parallel_do_enumerated(self.type, D.M_NBODY_MOVE, a)
         if self.collide:
-            for m in (D.M_COLL_FIND, D.M_COLL_CLAIM, D.M_COLL_MERGE, D.M_COLL_DELETE):
+            find = D.M_COLL_FIND_TILED if self.tiled else D.M_COLL_FIND
+            for m in (find, D.M_COLL_CLAIM, D.M_COLL_MERGE, D.M_COLL_DELETE):
                 self.heap.parallel_do_enumerated(self.type, m, a)
 
     def force(self):
         """FORCE alone (adds the pair sums to the force fields, which MOVE clears)."""
-        self.heap.parallel_do(self.type, self.force_method, self.args())
+        self.heap.parallel_do(self.type, self.force_method, self.args(flags=0))
 
     def read(self, forces: bool = False):
         """(state float32[n, 5] by id: px py vx vy m, alive uint8[n]) and, with

@@ -1,9 +1,9 @@
 // nbody.cu -- n-body and particle collisions as SMMO applications (Table 1
 // "nbody" and "collision"; the n-body listing of Sec. 2).  One type, Body.
-// FORCE is the all-pairs method: in the paper's form every body runs a
-// device_do (Sec. 2.1) over all bodies in its own thread; FORCE_TILED computes
-// the same integers with a pairwise kernel over the enumerated snapshot whose
-// CTAs stage chunks of bodies in shared memory.
+// FORCE and FIND are all-pairs methods: in the paper's form every body runs a
+// device_do (Sec. 2.1) over all bodies in its own thread; FORCE_TILED and
+// FIND_TILED compute the same integers with a pairwise kernel over the
+// enumerated snapshot whose CTAs stage chunks of bodies in shared memory.
 //
 // Arithmetic: every float operation is one IEEE binary32 operation rounded to
 // nearest (the __f*_rn intrinsics, which the compiler never contracts into
@@ -126,8 +126,15 @@ struct Move {
         float& py = fld<float>(c, t, bid, s, kPy);
         px = __fadd_rn(px, __fmul_rn(vx, a.dt));
         py = __fadd_rn(py, __fmul_rn(vy, a.dt));
-        fx = 0ull;
         fy = 0ull;
+        if (a.flags & DSOA_NBODY_KEYED_FIND) {     // prepare FIND_TILED and CLAIM
+            fx = ~0ull;
+            fld<uint32_t>(c, t, bid, s, kTarget) = kNone;
+            fld<uint32_t>(c, t, bid, s, kIncoming) = kNone;
+            fld<uint32_t>(c, t, bid, s, kMerged) = 0u;
+        } else {
+            fx = 0ull;
+        }
     }
 };
 
@@ -168,7 +175,13 @@ struct Claim {
     using Args = dsoa_nbody_args;
     static constexpr bool kNoNewOfOwnType = true;
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
-        const uint32_t target = fld<uint32_t>(c, t, bid, s, kTarget);
+        uint32_t target = fld<uint32_t>(c, t, bid, s, kTarget);
+        if (a.flags & DSOA_NBODY_KEYED_FIND) {     // the key FIND_TILED left in fx
+            unsigned long long& key = fld<unsigned long long>(c, t, bid, s, kFx);
+            target = key == ~0ull ? kNone : (uint32_t)key;
+            fld<uint32_t>(c, t, bid, s, kTarget) = target;
+            key = 0ull;
+        }
         if (target == kNone || target >= a.n_ids) return;
         const dsoa_obj h = a.handle_of[target];
         if (!h) return;
@@ -238,19 +251,22 @@ struct Read {
 };
 
 // ---------------------------------------------------------------------------
-// Pairwise FORCE over the enumerated snapshot.  Bodies get a dense index: every
-// CTA first builds, in shared memory, the exclusive prefix of the occupied-slot
-// counts of the listed blocks (pre[q] bodies precede block R[q]), so dense
-// index d is the (d - pre[q])-th occupied slot of the block q found by binary
-// search.  A work item is (256 bodies, one per thread) x (a chunk of 1024
-// bodies): the CTA stages the chunk's (px, py, m, dense index) as float4 in
-// shared memory and every thread adds the chunk's pair terms to its registers;
-// all threads of a warp read the same body, so the shared loads are
-// broadcasts, and no thread computes an empty slot however sparse the blocks
-// are.  Each CTA takes a contiguous range of items (mostly one i tile) and adds
-// its integer partial sums to the force fields with one atomicAdd per body and
-// i tile.  Lists longer than kDenseMaxR blocks fall back to indexing slots
-// (64 per listed block; empty ones stage as mass 0, which adds exactly 0).
+// Pairwise do-alls over the enumerated snapshot (FORCE and FIND of every body
+// against every other body).  Bodies get a dense index: every CTA first builds,
+// in shared memory, the exclusive prefix of the occupied-slot counts of the
+// listed blocks (pre[q] bodies precede block R[q]), so dense index d is the
+// (d - pre[q])-th occupied slot of the block q found by binary search.  A work
+// item is (256 bodies, one per thread) x (a chunk of 1024 bodies): the CTA
+// stages the chunk's (px, py, m, id) as float4 in shared memory and every thread
+// folds the chunk into its register state; all threads of a warp read the same
+// body, so the shared loads are broadcasts, and no thread computes an empty
+// slot however sparse the blocks are.  Each CTA takes a contiguous range of
+// items (mostly one i tile) and folds its partial state into the body's fields
+// with one atomic per body and i tile.  The fold is an integer sum (FORCE) or
+// an integer minimum (FIND), so the partition does not change the result.
+// Lists longer than kDenseMaxR blocks fall back to indexing slots (64 per
+// listed block; empty ones stage as mass 0, which adds exactly 0 and is never
+// bigger than a body).
 // ---------------------------------------------------------------------------
 constexpr uint32_t kTile = 256;          // i bodies per item: one per thread
 constexpr uint32_t kChunkBodies = 1024;  // j bodies per item: 16 KB of float4
@@ -275,7 +291,58 @@ __device__ __forceinline__ bool locate(bool dense, const uint32_t* pre, uint32_t
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_force_tiled(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+// FORCE: integer sums of the pair terms, added to the force fields.
+struct ForceOp {
+    float px, py, gsm;
+    uint32_t id;
+    unsigned long long fx, fy;
+    __device__ void begin(const dsoa_ctx& c, uint32_t t, uint64_t b, uint32_t s, const dsoa_nbody_args& a) {
+        px = fld<float>(c, t, b, s, kPx);
+        py = fld<float>(c, t, b, s, kPy);
+        gsm = __fmul_rn(__fmul_rn(a.G, a.fscale), fld<float>(c, t, b, s, kM));
+        id = fld<uint32_t>(c, t, b, s, kId);
+        fx = fy = 0ull;
+    }
+    __device__ __forceinline__ void pair(const float4 q, const dsoa_nbody_args& a) {
+        if (__float_as_uint(q.w) != id) pair_term(px, py, gsm, q.x, q.y, q.z, a.eps2, fx, fy);
+    }
+    __device__ void end(const dsoa_ctx& c, uint32_t t, uint64_t b, uint32_t s) {
+        if (fx) atomicAdd(&fld<unsigned long long>(c, t, b, s, kFx), fx);
+        if (fy) atomicAdd(&fld<unsigned long long>(c, t, b, s, kFy), fy);
+    }
+};
+
+// FIND (keyed): the nearest bigger body within reach as the minimum of the key
+// (bits of d2 << 32 | id) -- the bits of a non-negative float order like its
+// value, so the minimum key is the smallest distance, ties to the lower id.
+// The key lives in the fx field, which MOVE set to all ones for this purpose;
+// CLAIM turns it into the target and clears the field.
+struct FindOp {
+    float px, py, m;
+    uint32_t id;
+    unsigned long long key;
+    __device__ void begin(const dsoa_ctx& c, uint32_t t, uint64_t b, uint32_t s, const dsoa_nbody_args&) {
+        px = fld<float>(c, t, b, s, kPx);
+        py = fld<float>(c, t, b, s, kPy);
+        m = fld<float>(c, t, b, s, kM);
+        id = fld<uint32_t>(c, t, b, s, kId);
+        key = ~0ull;
+    }
+    __device__ __forceinline__ void pair(const float4 q, const dsoa_nbody_args& a) {
+        const uint32_t qid = __float_as_uint(q.w);
+        const float dx = __fsub_rn(q.x, px), dy = __fsub_rn(q.y, py);
+        const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        const bool bigger = q.z > m || (q.z == m && qid < id);
+        const unsigned long long k = ((unsigned long long)__float_as_uint(d2) << 32) | qid;
+        if (qid != id && d2 < a.rc2 && bigger && k < key) key = k;
+    }
+    __device__ void end(const dsoa_ctx& c, uint32_t t, uint64_t b, uint32_t s) {
+        if (key != ~0ull) atomicMin(&fld<unsigned long long>(c, t, b, s, kFx), key);
+    }
+};
+
+template <class Op>
+__global__ void __launch_bounds__(256) k_pairs_tiled(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                                      const unsigned long long* __restrict__ occ,
                                                      const uint32_t* __restrict__ r_dev, dsoa_nbody_args a) {
     __shared__ float4 sj[kChunkBodies];
@@ -314,30 +381,21 @@ __global__ void __launch_bounds__(256) k_force_tiled(dsoa_ctx c, uint32_t t, con
     const uint64_t n_i = (nb + kTile - 1) / kTile, n_j = (nb + kChunkBodies - 1) / kChunkBodies;
     const uint64_t items = n_i * n_j;
     const uint64_t wb = items * blockIdx.x / gridDim.x, we = items * (blockIdx.x + 1) / gridDim.x;
-    const float gs = __fmul_rn(a.G, a.fscale);
     uint64_t cur = ~0ull, bi = 0;
     bool mine = false;
-    float px = 0.f, py = 0.f, gsm = 0.f;
-    uint32_t me = kNone, si = 0;
-    unsigned long long fx = 0ull, fy = 0ull;
+    uint32_t si = 0;
+    Op op;
     for (uint64_t w = wb; w < we; ++w) {
         const uint64_t it = w / n_j, jt = w % n_j;
         if (it != cur) {
-            if (mine) {
-                if (fx) atomicAdd(&fld<unsigned long long>(c, t, bi, si, kFx), fx);
-                if (fy) atomicAdd(&fld<unsigned long long>(c, t, bi, si, kFy), fy);
-            }
+            if (mine) op.end(c, t, bi, si);
             cur = it;
-            fx = fy = 0ull;
             const uint32_t d = (uint32_t)(it * kTile) + tid;
             uint32_t q = 0;
             mine = d < nb && locate(dense, pre, r, occ, d, q, si);
             if (mine) {
                 bi = __ldg(&R[q]);
-                px = fld<float>(c, t, bi, si, kPx);
-                py = fld<float>(c, t, bi, si, kPy);
-                gsm = __fmul_rn(gs, fld<float>(c, t, bi, si, kM));
-                me = d;
+                op.begin(c, t, bi, si, a);
             }
         }
         const uint32_t j0 = (uint32_t)(jt * kChunkBodies);
@@ -351,23 +409,17 @@ __global__ void __launch_bounds__(256) k_force_tiled(dsoa_ctx c, uint32_t t, con
                 v.x = fld<float>(c, t, bj, sl, kPx);
                 v.y = fld<float>(c, t, bj, sl, kPy);
                 v.z = fld<float>(c, t, bj, sl, kM);
-                v.w = __uint_as_float(j0 + k);
+                v.w = __uint_as_float(fld<uint32_t>(c, t, bj, sl, kId));
             }
             sj[k] = v;
         }
         __syncthreads();
         if (mine) {
 #pragma unroll 4
-            for (uint32_t k = 0; k < jn; ++k) {
-                const float4 q = sj[k];
-                if (__float_as_uint(q.w) != me) pair_term(px, py, gsm, q.x, q.y, q.z, a.eps2, fx, fy);
-            }
+            for (uint32_t k = 0; k < jn; ++k) op.pair(sj[k], a);
         }
     }
-    if (mine) {
-        if (fx) atomicAdd(&fld<unsigned long long>(c, t, bi, si, kFx), fx);
-        if (fy) atomicAdd(&fld<unsigned long long>(c, t, bi, si, kFy), fy);
-    }
+    if (mine) op.end(c, t, bi, si);
 }
 
 // Body's field sizes in bytes (id, px, py, vx, vy, m, fx, fy, target, incoming, merged)
@@ -414,11 +466,12 @@ int dsoa_nbody_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
         case DSOA_M_NBODY_READ:
             if (!args.out || !args.alive_out) return DSOA_ERR_INVALID_ARG;
             return dsoa_run_doall<Read>(h, type, args);
-        case DSOA_M_NBODY_FORCE_TILED: {
-            if (h->ctx.M * 64ull >= 0xFFFFFFFFull) return DSOA_ERR_INVALID_ARG;  // 32-bit slot ids
+        case DSOA_M_NBODY_FORCE_TILED:
+        case DSOA_M_COLL_FIND_TILED: {
+            if (h->ctx.M * 64ull >= 0xFFFFFFFFull) return DSOA_ERR_INVALID_ARG;  // 32-bit slot indices
             rc = dsoa_prepare_doall(h, type);
             if (rc) return rc;
-            auto* k = &k_force_tiled;
+            auto* k = method == DSOA_M_NBODY_FORCE_TILED ? &k_pairs_tiled<ForceOp> : &k_pairs_tiled<FindOp>;
             const unsigned grid = (unsigned)(dsoa_resident_ctas(reinterpret_cast<const void*>(k), 256) * h->num_sms);
             k<<<grid ? grid : 1u, 256, 0, h->stream>>>(dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type],
                                                      h->r_dev[type], args);

@@ -40,7 +40,8 @@ M_TRAFFIC_MOVE, M_TRAFFIC_READ = 401, 402
 K_TRAFFIC_INIT, K_TRAFFIC_CLEAR, K_TRAFFIC_ONRAMP, K_TRAFFIC_ADVANCE = 450, 451, 452, 453
 C_NBODY, M_NBODY_FORCE, M_NBODY_MOVE = 500, 501, 502
 M_COLL_FIND, M_COLL_CLAIM, M_COLL_MERGE, M_COLL_DELETE = 503, 504, 505, 506
-M_NBODY_READ, M_NBODY_FORCE_TILED = 507, 508
+M_NBODY_READ, M_NBODY_FORCE_TILED, M_COLL_FIND_TILED = 507, 508, 509
+NBODY_KEYED_FIND = 1
 
 INST_IDLE, INST_RUN, INST_KILL = 0, 1, 2
 
@@ -87,7 +88,7 @@ class NBodyArgs(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("n_ids", ctypes.c_uint32), ("mass_max", ctypes.c_uint32),
                 ("G", ctypes.c_float), ("dt", ctypes.c_float), ("eps2", ctypes.c_float),
                 ("rc2", ctypes.c_float), ("fscale", ctypes.c_float), ("vscale", ctypes.c_float),
-                ("body_type", ctypes.c_int32), ("pad", ctypes.c_uint32)]
+                ("body_type", ctypes.c_int32), ("flags", ctypes.c_uint32)]
 
 
 # exported names of include/dsoa.h, in declaration order

@@ -76,7 +76,7 @@ int main(void) {
   S(dsoa_wator_args) O(dsoa_wator_args, shark_type)
   S(dsoa_traffic_args) O(dsoa_traffic_args, seed) O(dsoa_traffic_args, car_type)
   S(dsoa_nbody_args) O(dsoa_nbody_args, seed) O(dsoa_nbody_args, n_ids) O(dsoa_nbody_args, G)
-  O(dsoa_nbody_args, vscale) O(dsoa_nbody_args, body_type)
+  O(dsoa_nbody_args, vscale) O(dsoa_nbody_args, body_type) O(dsoa_nbody_args, flags)
   return 0;
 }
 """
