@@ -8,11 +8,19 @@
 
 namespace {
 
-__device__ __forceinline__ uint32_t torus(uint32_t c, uint32_t w, uint32_t h, int dx, int dy) {
-    const uint32_t x = c % w, y = c / w;
-    const uint32_t nx = (x + (uint32_t)((int)w + dx)) % w;
-    const uint32_t ny = (y + (uint32_t)((int)h + dy)) % h;
-    return ny * w + nx;
+// The 8 torus neighbours of cell c (Moore neighbourhood): one division for the
+// coordinates, wrap-around by compare-and-select (the same cells as the
+// modular formulas, also on 1- and 2-wide tori).
+__device__ __forceinline__ void moore(uint32_t c, uint32_t w, uint32_t h, uint32_t nb[8]) {
+    const uint32_t y = c / w, x = c - y * w;
+    const uint32_t xs[3] = {x == 0u ? w - 1u : x - 1u, x, x + 1u == w ? 0u : x + 1u};
+    const uint32_t rs[3] = {(y == 0u ? h - 1u : y - 1u) * w, y * w, (y + 1u == h ? 0u : y + 1u) * w};
+    uint32_t k = 0;
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+            if (dx != 1 || dy != 1) nb[k++] = rs[dy] + xs[dx];
 }
 
 struct CellCtor {
@@ -46,14 +54,14 @@ struct Spread {
         const dsoa_inst I = a.inst[k];
         if (I.state != DSOA_INST_RUN) return;
         const uint32_t cell = dsoa_column<uint32_t>(c, t, bid, 1)[s];
+        uint32_t nc[8];
+        moore(cell, I.w, I.h, nc);
+        dsoa_obj nb[8];
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
+        for (int k = 0; k < 8; ++k) nb[k] = I.cellmap[nc[k]];
 #pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (dx == 0 && dy == 0) continue;
-                const dsoa_obj nb = I.cellmap[torus(cell, I.w, I.h, dx, dy)];
-                if (nb) atomicAdd(&dsoa_field<uint32_t>(c, nb, 2), 1u);
-            }
+        for (int k = 0; k < 8; ++k)
+            if (nb[k]) atomicAdd(&dsoa_field<uint32_t>(c, nb[k], 2), 1u);
     }
 };
 

@@ -23,12 +23,23 @@ constexpr uint32_t kFishBreed = 3u, kSharkBreed = 10u, kSharkEnergy = 3u;
 constexpr uint32_t kFishThr = 1288490188u;   // floor(0.30 * 2^32)
 constexpr uint32_t kSharkThr = 1503238553u;  // floor(0.35 * 2^32): fish or shark
 
+// Torus neighbours of cell c: one division for the coordinates, wrap-around
+// by compare-and-select (the same cells as the modular formulas).
 __device__ __forceinline__ void neighbours(uint32_t c, uint32_t w, uint32_t h, uint32_t nb[4]) {
-    const uint32_t x = c % w, y = c / w;
-    nb[0] = ((y + h - 1u) % h) * w + x;  // N
-    nb[1] = y * w + (x + 1u) % w;        // E
-    nb[2] = ((y + 1u) % h) * w + x;      // S
-    nb[3] = y * w + (x + w - 1u) % w;    // W
+    const uint32_t y = c / w, x = c - y * w;
+    const uint32_t row = y * w;
+    nb[0] = (y == 0u ? h - 1u : y - 1u) * w + x;        // N
+    nb[1] = row + (x + 1u == w ? 0u : x + 1u);          // E
+    nb[2] = (y + 1u == h ? 0u : y + 1u) * w + x;        // S
+    nb[3] = row + (x == 0u ? w - 1u : x - 1u);          // W
+}
+
+// Index of the chosen candidate among k >= 1: Philox word 0 modulo k.  With
+// one candidate the draw cannot matter, so it is not computed.
+__device__ __forceinline__ uint32_t pick(uint32_t k, uint64_t seed, uint32_t t, uint32_t cell, uint32_t stream) {
+    if (k == 1u) return 0u;
+    const uint32_t u = dsoa_philox_w0(seed, t, cell, stream, 0u);
+    return k == 2u ? (u & 1u) : (k == 4u ? (u & 3u) : u % 3u);
 }
 
 struct FishChoose {
@@ -45,7 +56,7 @@ struct FishChoose {
             if (I.occ[nb[d]] == 0) cand[k++] = nb[d];
         uint32_t tg = kNone;
         if (k) {
-            tg = cand[dsoa_philox_w0(I.seed, I.t, cell, 1u, 0u) % k];
+            tg = cand[pick(k, I.seed, I.t, cell, 1u)];
             atomicMin(&I.claim[tg], cell);
         }
         dsoa_column<uint32_t>(c, t, bid, 3)[s] = tg;
@@ -108,7 +119,7 @@ struct SharkChoose {
         }
         uint32_t tg = kNone;
         if (k) {
-            tg = cand[dsoa_philox_w0(I.seed, I.t, cell, 2u, 0u) % k];
+            tg = cand[pick(k, I.seed, I.t, cell, 2u)];
             atomicMin(&I.claim[tg], cell);
         }
         dsoa_column<uint32_t>(c, t, bid, 4)[s] = tg;
