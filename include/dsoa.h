@@ -147,6 +147,14 @@ int dsoa_delete_handles(dsoa_heap* h, const dsoa_obj* handles_dev, uint64_t n);
 int dsoa_enumerate(dsoa_heap* h, int type, const uint32_t** R_dev,
                    const uint64_t** occ_dev, const uint32_t** r_dev);
 
+/* Enumerate several types at once (`ntypes` distinct ids at types_host): the
+ * same result as one dsoa_enumerate per type issued back to back, but the
+ * single-pass enumeration serves all of them with one launch (each type keeps
+ * its own block list and snapshot).  Meant for step loops whose later do-alls
+ * (dsoa_parallel_do_enumerated) visit types that the earlier methods of the
+ * step do not create or delete.  Asynchronous. */
+int dsoa_enumerate_many(dsoa_heap* h, const int* types_host, int ntypes);
+
 /* Number of live objects of `type` (popcounts of the slot bitmaps of the
  * blocks in the type's allocated-block bitmap).  Synchronous: waits for the
  * heap's stream.  Not allowed during stream capture. */

@@ -366,7 +366,9 @@ __device__ __forceinline__ void dsoa_block_release(const dsoa_ctx& c, uint32_t t
         bits &= ~before;
         if (!bits) return;
     }
-    if ((before & c.cap[t]) == 0ull) dsoa_block_first_free(c, t, bid);       /* FIRST */
+    /* FIRST: real slots (below the capacity) freed in a block that had none free;
+     * a rollback that only returns slots beyond the capacity changes nothing */
+    if ((before & c.cap[t]) == 0ull && (bits & c.cap[t]) != 0ull) dsoa_block_first_free(c, t, bid);
     if ((before | bits) == DSOA_ALL) dsoa_block_invalidate(c, bid);          /* EMPTY */
 }
 
@@ -458,8 +460,12 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
             continue;
         }
         const uint32_t bt = dsoa_ld32(&c.btype[bid]);
-        const unsigned long long left = before & ~mask & c.cap[bt < c.ntypes ? bt : t];
-        const bool full = left == 0ull;
+        /* FULL: this reservation took the last free real slots of the block's type
+         * (a reservation of another type may take only slots beyond that type's
+         * capacity, which leaves the block's state unchanged) */
+        const unsigned long long capb = c.cap[bt < c.ntypes ? bt : t];
+        const unsigned long long left = before & ~mask & capb;
+        const bool full = left == 0ull && (before & capb) != 0ull;
         if (full) dsoa_block_deactivate(c, bt, (uint64_t)bid);
         if (bt != t) {                 /* block replaced by another type: roll back */
             if (hp) *hp = dsoa_hint{0ull, DSOA_NO_HINT_BLOCK};

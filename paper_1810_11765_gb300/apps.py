@@ -161,13 +161,25 @@ class GolWorld:
             self.bufs[slot] = (cellmap, occ, ini)   # keep alive until the kernel ran
         return slot
 
+    batch_enumeration = True
+
     def step(self):
         """One generation.  Spread neither creates nor deletes Alive objects, so
-        Reap runs on Spread's snapshot without enumerating again."""
+        Reap runs on Spread's snapshot without enumerating again; Cells are never
+        created or deleted during a generation, so their snapshot is taken at its
+        start together with the Alive snapshot, in one enumeration launch."""
         a = self.args()
-        self.heap.parallel_do(self.alive_type, D.M_GOL_SPREAD, a)
+        batch = self.batch_enumeration and self.heap.separate_enumeration()
+        if batch:
+            self.heap.enumerate_many([self.alive_type, self.cell_type])
+            self.heap.parallel_do_enumerated(self.alive_type, D.M_GOL_SPREAD, a)
+        else:
+            self.heap.parallel_do(self.alive_type, D.M_GOL_SPREAD, a)
         self.heap.parallel_do_enumerated(self.alive_type, D.M_GOL_REAP, a)
-        self.heap.parallel_do(self.cell_type, D.M_GOL_DECIDE, a)
+        if batch:
+            self.heap.parallel_do_enumerated(self.cell_type, D.M_GOL_DECIDE, a)
+        else:
+            self.heap.parallel_do(self.cell_type, D.M_GOL_DECIDE, a)
         self.heap.run_kernel(D.K_GOL_ADVANCE, self.table.capacity, a)
 
     def read(self, slot: int) -> np.ndarray:
@@ -225,13 +237,25 @@ class WatorWorld:
         self.heap.run_kernel(D.K_WATOR_INIT, n, self.args(slot, ini))
         return slot
 
+    batch_enumeration = True
+
     def step(self):
         """One step.  The choose methods neither create nor delete agents of their
-        own type, so each move method runs on its choose method's snapshot."""
+        own type, so each move method runs on its choose method's snapshot; and the
+        fish methods neither create nor delete sharks, so the shark snapshot can be
+        taken at the start of the step together with the fish snapshot, in one
+        enumeration launch."""
         a = self.args()
-        self.heap.parallel_do(self.fish_type, D.M_WATOR_FISH_CHOOSE, a)
+        if self.batch_enumeration and self.heap.separate_enumeration():
+            self.heap.enumerate_many([self.fish_type, self.shark_type])
+            self.heap.parallel_do_enumerated(self.fish_type, D.M_WATOR_FISH_CHOOSE, a)
+        else:
+            self.heap.parallel_do(self.fish_type, D.M_WATOR_FISH_CHOOSE, a)
         self.heap.parallel_do_enumerated(self.fish_type, D.M_WATOR_FISH_MOVE, a)
-        self.heap.parallel_do(self.shark_type, D.M_WATOR_SHARK_CHOOSE, a)
+        if self.batch_enumeration and self.heap.separate_enumeration():
+            self.heap.parallel_do_enumerated(self.shark_type, D.M_WATOR_SHARK_CHOOSE, a)
+        else:
+            self.heap.parallel_do(self.shark_type, D.M_WATOR_SHARK_CHOOSE, a)
         self.heap.parallel_do_enumerated(self.shark_type, D.M_WATOR_SHARK_MOVE, a)
         self.heap.run_kernel(D.K_WATOR_ADVANCE, self.table.capacity, a)
 

@@ -58,9 +58,9 @@ struct dsoa_heap {
     int scan_tiles_per_cta = 0;      // 0 = single-pass look-back; 1, 2 = tile-count + compaction kernels
     bool stream_enum = false;        // enumerate inside methods that create no objects of their own type
     uint32_t* stream_ctl = nullptr;  // ticket, finished CTAs, R length of the streamed do-all
-    unsigned long long* lb_state = nullptr;  // [tiles] look-back state words (epoch, status, value)
-    uint32_t* lb_ctl = nullptr;              // ticket, done counter, epoch of the look-back kernel
-    int lb_fits = -1;                        // 1: every look-back CTA resident at once (tile = blockIdx)
+    unsigned long long* lb_state = nullptr;  // [ntypes][tiles] look-back state words (epoch, status, value)
+    uint32_t* lb_ctl = nullptr;              // [ntypes][4]: ticket, done counter, epoch of the look-back kernel
+    int lb_fits = -1;                        // look-back CTAs resident per SM (-1: not queried yet)
 
     uint32_t flags = 0;              // DSOA_FLAG_* applied to every launch
     uint32_t lookups = DSOA_LOOKUP_ATTEMPTS;  // r: active-block lookups before the slow path

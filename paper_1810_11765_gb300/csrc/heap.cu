@@ -109,7 +109,7 @@ bool make_layout(uint64_t M, uint32_t block_bytes, int ntypes, Layout* L) {
     L->off_Rocc = p;  p = align_up(p + M * 8 * (uint64_t)ntypes, kAlign);
     L->off_tcnt = p;  p = align_up(p + L->tiles * 4, kAlign);
     L->off_toff = p;  p = align_up(p + L->tiles * 4, kAlign);
-    L->off_lb = p;    p = align_up(p + L->tiles * 8, kAlign);
+    L->off_lb = p;    p = align_up(p + L->tiles * 8 * (uint64_t)ntypes + 16 * (uint64_t)ntypes, kAlign);
     L->hint_slots = hint_slots_for(M);
     L->off_hint = p;  p = align_up(p + L->hint_slots * (uint64_t)ntypes * sizeof(dsoa_hint), kAlign);
     L->off_grid = p;  p = align_up(p + (uint64_t)DSOA_GRID_SCRATCH * 4, kAlign);
@@ -259,12 +259,29 @@ __device__ __forceinline__ unsigned long long lb_word(uint32_t ep, unsigned long
     return ((unsigned long long)(ep & 0xFFFFFFu) << 40) | (st << 38) | (v & ((1ull << 38) - 1ull));
 }
 
-__global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint32_t b, uint64_t tiles,
-                                                      unsigned long long* __restrict__ state,
-                                                      uint32_t* __restrict__ ctl, uint32_t* __restrict__ R,
-                                                      unsigned long long* __restrict__ Rocc,
-                                                      uint32_t* __restrict__ r_dev, uint32_t use_ticket) {
+// Several types can be enumerated by one launch (each type's snapshot taken at
+// the same point): CTAs [q * tiles, (q + 1) * tiles) serve the q-th type of the
+// batch, with that type's own look-back state, ticket and epoch.
+struct EnumBatch {
+    uint32_t n;                                   // types in the batch
+    uint32_t b[DSOA_MAX_TYPES];                   // allocated-bitmap index of each
+    uint32_t* R[DSOA_MAX_TYPES];
+    unsigned long long* Rocc[DSOA_MAX_TYPES];
+    uint32_t* r_dev[DSOA_MAX_TYPES];
+    unsigned long long* state[DSOA_MAX_TYPES];    // [tiles] look-back state words
+    uint32_t* ctl[DSOA_MAX_TYPES];                // ticket, done, epoch
+};
+
+__global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint64_t tiles, EnumBatch eb,
+                                                      uint32_t use_ticket) {
     __shared__ uint32_t list[4096];
+    const uint32_t qt = (uint32_t)(blockIdx.x / tiles);          /* the batch's type slot */
+    const uint32_t b = eb.b[qt];
+    unsigned long long* __restrict__ state = eb.state[qt];
+    uint32_t* __restrict__ ctl = eb.ctl[qt];
+    uint32_t* __restrict__ R = eb.R[qt];
+    unsigned long long* __restrict__ Rocc = eb.Rocc[qt];
+    uint32_t* __restrict__ r_dev = eb.r_dev[qt];
     constexpr uint32_t kSnap = 2048;                 /* snapshot words staged by warp 1 */
     __shared__ unsigned long long snap[kSnap];
     __shared__ uint32_t wsum[2];
@@ -289,7 +306,7 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint32_t b, ui
         t = s_tile;
         if (t * 64 + j < w0) w = L0[t * 64 + j];
     } else {
-        t = blockIdx.x;
+        t = blockIdx.x - (uint64_t)qt * tiles;
         if (t * 64 + j < w0) w = L0[t * 64 + j];              /* in flight with the epoch read */
         if (j == 0) s_ep = dsoa_ld32(epoch) + 1u;
         __syncthreads();
@@ -540,22 +557,41 @@ int dsoa_ensure_frozen(dsoa_heap* h) {
     return dsoa_heap_freeze(h);
 }
 
+// One look-back launch for n types (validated by the caller).
+static int enumerate_lookback(dsoa_heap* h, const int* types, int n) {
+    if (h->lb_fits < 0) {              // CTAs of k_enum_lookback resident per SM
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enum_lookback, 64, 0);
+        h->lb_fits = per_sm;
+    }
+    // tile = blockIdx when every CTA of the launch is resident at once
+    const bool fits = (uint64_t)h->lb_fits * (uint64_t)h->num_sms >= h->tiles * (uint64_t)n;
+    EnumBatch eb;
+    std::memset(&eb, 0, sizeof(eb));
+    eb.n = (uint32_t)n;
+    for (int q = 0; q < n; ++q) {
+        const int t = types[q];
+        eb.b[q] = dsoa_bm_alloc((uint32_t)t);
+        eb.R[q] = h->R[t];
+        eb.Rocc[q] = h->Rocc[t];
+        eb.r_dev[q] = h->r_dev[t];
+        eb.state[q] = h->lb_state + (uint64_t)t * h->tiles;
+        eb.ctl[q] = h->lb_ctl + 4 * t;
+    }
+    const int rc = dsoa_launch_step(h, k_enum_lookback, (unsigned)(h->tiles * (uint64_t)n), 64u, h->ctx, h->tiles,
+                                    eb, fits ? 0u : 1u);
+    if (rc == DSOA_OK)
+        for (int q = 0; q < n; ++q) h->enumerated[types[q]] = true;
+    return rc;
+}
+
 int dsoa_enumerate_internal(dsoa_heap* h, int type) {
     int rc = dsoa_ensure_frozen(h);
     if (rc) return rc;
     if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
     const uint32_t b = dsoa_bm_alloc((uint32_t)type);
-    if (h->scan_tiles_per_cta == 0) {      // single-pass look-back enumeration (default)
-        if (h->lb_fits < 0) {          // can every tile's CTA be resident at once?
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enum_lookback, 64, 0);
-            h->lb_fits = (uint64_t)per_sm * (uint64_t)h->num_sms >= h->tiles ? 1 : 0;
-        }
-        rc = dsoa_launch_step(h, k_enum_lookback, (unsigned)h->tiles, 64u, h->ctx, b, h->tiles, h->lb_state,
-                              h->lb_ctl, h->R[type], h->Rocc[type], h->r_dev[type], h->lb_fits ? 0u : 1u);
-        if (rc == DSOA_OK) h->enumerated[type] = true;
-        return rc;
-    }
+    if (h->scan_tiles_per_cta == 0)        // single-pass look-back enumeration (default)
+        return enumerate_lookback(h, &type, 1);
     const int tpb = 256;
     const uint64_t warps = h->tiles;
     const unsigned g1 = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 7) / 8, (uint64_t)h->num_sms * 8));
@@ -662,8 +698,8 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     c.err = (int*)(small + 0);
     c.hint = (dsoa_hint*)(base + L.off_hint);
     c.hint_mask = (uint32_t)(L.hint_slots - 1);
-    h->lb_state = (unsigned long long*)(base + L.off_lb);
-    h->lb_ctl = (uint32_t*)(small + 4);      // ticket, done, epoch
+    h->lb_state = (unsigned long long*)(base + L.off_lb);              // [ntypes][tiles]
+    h->lb_ctl = (uint32_t*)(h->lb_state + L.tiles * (uint64_t)h->ntypes);  // [ntypes][4]: ticket, done, epoch
     c.grid_scratch = (uint32_t*)(base + L.off_grid);
     h->done = (uint32_t*)(small + 1);
     h->scratch64 = (unsigned long long*)(small + 32);
@@ -696,7 +732,8 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     DSOA_CUDA_TRY(cudaMemsetAsync(c.hint, 0xFF, ((uint64_t)c.hint_mask + 1) * (uint64_t)h->ntypes * sizeof(dsoa_hint),
                                   h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(c.grid_scratch, 0, (uint64_t)DSOA_GRID_SCRATCH * 4, h->stream));
-    DSOA_CUDA_TRY(cudaMemsetAsync(h->lb_state, 0, L.tiles * 8, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(h->lb_state, 0, L.tiles * 8 * (uint64_t)h->ntypes + 16 * (uint64_t)h->ntypes,
+                                  h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(h->R[0], 0, L.M * 4 * (uint64_t)h->ntypes, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(h->Rocc[0], 0, L.M * 8 * (uint64_t)h->ntypes, h->stream));
     k_init_free<<<std::max(1, h->num_sms * 4), 256, 0, h->stream>>>(c);
@@ -781,6 +818,23 @@ int dsoa_enumerate(dsoa_heap* h, int type, const uint32_t** R_dev, const uint64_
     if (R_dev) *R_dev = h->R[type];
     if (occ_dev) *occ_dev = (const uint64_t*)h->Rocc[type];
     if (r_dev) *r_dev = h->r_dev[type];
+    return DSOA_OK;
+}
+
+int dsoa_enumerate_many(dsoa_heap* h, const int* types_host, int ntypes) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (!types_host || ntypes < 1 || ntypes > h->ntypes) return DSOA_ERR_INVALID_ARG;
+    for (int q = 0; q < ntypes; ++q) {
+        if (types_host[q] < 0 || types_host[q] >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+        for (int p = 0; p < q; ++p)
+            if (types_host[p] == types_host[q]) return DSOA_ERR_INVALID_ARG;
+    }
+    if (h->scan_tiles_per_cta == 0) return enumerate_lookback(h, types_host, ntypes);
+    for (int q = 0; q < ntypes; ++q) {
+        rc = dsoa_enumerate_internal(h, types_host[q]);
+        if (rc) return rc;
+    }
     return DSOA_OK;
 }
 

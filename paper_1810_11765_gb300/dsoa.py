@@ -95,7 +95,8 @@ class NBodyArgs(ctypes.Structure):
 ABI_FUNCTIONS = [
     "dsoa_heap_create", "dsoa_heap_create_from", "dsoa_register_type", "dsoa_heap_freeze",
     "dsoa_heap_info", "dsoa_field_offset", "dsoa_parallel_new", "dsoa_parallel_do",
-    "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_delete_handles", "dsoa_enumerate", "dsoa_count", "dsoa_count_async",
+    "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_delete_handles", "dsoa_enumerate",
+    "dsoa_enumerate_many", "dsoa_count", "dsoa_count_async",
     "dsoa_free_blocks_async", "dsoa_get_error", "dsoa_check", "dsoa_export_state",
     "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
     "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_set_lookups",
@@ -131,6 +132,7 @@ def load(path: str | None = None):
         "dsoa_parallel_new": [vp, i32, u64, i32, vp, sz], "dsoa_parallel_do": [vp, i32, i32, vp, sz],
         "dsoa_parallel_do_enumerated": [vp, i32, i32, vp, sz],
         "dsoa_run_kernel": [vp, i32, u64, vp, sz], "dsoa_enumerate": [vp, i32, vp, vp, vp],
+        "dsoa_enumerate_many": [vp, vp, i32],
         "dsoa_delete_handles": [vp, vp, u64],
         "dsoa_count": [vp, i32, vp], "dsoa_count_async": [vp, i32, vp],
         "dsoa_free_blocks_async": [vp, vp], "dsoa_get_error": [vp, vp], "dsoa_check": [vp, vp],
@@ -278,6 +280,11 @@ class Heap:
     def delete_handles(self, handles_dev, n: int):
         _ok(load().dsoa_delete_handles(self._h, _addr(handles_dev), n), "dsoa_delete_handles")
 
+    def enumerate_many(self, types):
+        """One enumeration launch for several types (dsoa_enumerate_many)."""
+        arr = (ctypes.c_int * len(types))(*types)
+        _ok(load().dsoa_enumerate_many(self._h, arr, len(types)), "dsoa_enumerate_many")
+
     def enumerate(self, t: int):
         R, occ, r = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
         _ok(load().dsoa_enumerate(self._h, t, ctypes.byref(R), ctypes.byref(occ), ctypes.byref(r)),
@@ -321,9 +328,18 @@ class Heap:
     def set_launch(self, tpb=0, ctas_per_sm=0, slots_per_thread=0, scan_tiles=0, waves=0):
         _ok(load().dsoa_set_launch(self._h, tpb, ctas_per_sm, slots_per_thread, scan_tiles, waves),
             "dsoa_set_launch")
+        if scan_tiles:
+            self._scan_tiles = scan_tiles
 
     def set_flags(self, flags: int):
         _ok(load().dsoa_set_flags(self._h, flags), "dsoa_set_flags")
+        self._flags = flags
+
+    def separate_enumeration(self) -> bool:
+        """True unless the do-alls enumerate inside their own kernels (the fused
+        cooperative do-all or the streamed enumeration), i.e. when an up-front
+        dsoa_enumerate_many serves the following enumerated do-alls."""
+        return not (getattr(self, "_flags", 0) & FLAG_FUSED) and getattr(self, "_scan_tiles", 0) != 4
 
     def set_lookups(self, r: int):
         _ok(load().dsoa_set_lookups(self._h, r), "dsoa_set_lookups")

@@ -125,3 +125,47 @@ def test_enumeration_modes_agree(scan):
     ref, _ = oracle.wator_run(160, 120, 40, seed=55)
     assert np.array_equal(w.read(s), ref)
     assert heap.get_error() == 0
+
+
+class _Dev:
+    """A device buffer given by pointer, for torch.as_tensor."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3}
+
+
+def _enumeration(heap, t, ptrs):
+    import torch
+    R, occ, r = ptrs
+    torch.cuda.synchronize()
+    n = int(torch.as_tensor(_Dev(r, 1, "<i4"), device="cuda").cpu()[0])
+    lst = torch.as_tensor(_Dev(R, max(n, 1), "<i4"), device="cuda")[:n].cpu().numpy().copy()
+    snap = torch.as_tensor(_Dev(occ, max(n, 1), "<i8"), device="cuda")[:n].cpu().numpy().copy()
+    return lst, snap
+
+
+@pytest.mark.parametrize("scan_tiles", [1, 3])
+def test_enumerate_many_equals_separate_enumerations(scan_tiles):
+    """One launch enumerating Fish and Shark gives, per type, the block list and
+    occupancy snapshot of a separate dsoa_enumerate (same per-type buffers)."""
+    heap, w = world(64 << 20)
+    heap.set_launch(scan_tiles=scan_tiles)
+    w.add(200, 100, 9)
+    for _ in range(15):
+        w.step()
+    types = (w.fish_type, w.shark_type)
+    ptrs = {t: heap.enumerate(t) for t in types}
+    sep = {t: _enumeration(heap, t, ptrs[t]) for t in types}
+    assert all(len(sep[t][0]) > 0 for t in types)
+    for order in ([w.fish_type, w.shark_type], [w.shark_type, w.fish_type]):
+        for _ in range(3):            # repeated launches: epochs advance per type
+            heap.enumerate_many(order)
+            for t in types:
+                lst, snap = _enumeration(heap, t, ptrs[t])
+                assert np.array_equal(lst, sep[t][0]) and np.array_equal(snap, sep[t][1])
+    heap.enumerate(w.fish_type)        # a single-type launch after batched ones
+    lst, snap = _enumeration(heap, w.fish_type, ptrs[w.fish_type])
+    assert np.array_equal(lst, sep[w.fish_type][0])
+    assert heap.get_error() == 0
+    heap.close()
