@@ -190,6 +190,13 @@ WATOR_KERNELS = [  # (type attr, method, reuses the previous snapshot, algorithm
     ("shark_type", "M_WATOR_SHARK_CHOOSE", False, 28),
     ("shark_type", "M_WATOR_SHARK_MOVE", True, 32),
 ]
+WATOR_KERNELS_DEFERRED = [  # the same step with births created by the births kernel
+    ("fish_type", "M_WATOR_FISH_CHOOSE", False, 24),
+    ("fish_type", "M_WATOR_FISH_MOVE_DEFER", True, 20),
+    ("fish_type", "K_WATOR_BIRTHS", None, 0),
+    ("shark_type", "M_WATOR_SHARK_CHOOSE", False, 28),
+    ("shark_type", "M_WATOR_SHARK_MOVE", True, 32),
+]
 
 
 def wator_kernel_profile(seed, warmup, steps, flush, launch=None):
@@ -208,11 +215,13 @@ def wator_kernel_profile(seed, warmup, steps, flush, launch=None):
     for _ in range(steps):
         fish, sharks = w.counts()
         flush.zero_()
-        for tattr, meth, reuse, bpa in WATOR_KERNELS:
+        for tattr, meth, reuse, bpa in (WATOR_KERNELS_DEFERRED if w.defer_births else WATOR_KERNELS):
             t = getattr(w, tattr)
             e0, e1 = ev(), ev()
             e0.record()
-            if reuse:
+            if reuse is None:                             # plain kernel over the instances
+                heap.run_kernel(getattr(D, meth), 1, a)
+            elif reuse:
                 heap.parallel_do_enumerated(t, getattr(D, meth), a)
             else:
                 heap.parallel_do(t, getattr(D, meth), a)
@@ -221,7 +230,9 @@ def wator_kernel_profile(seed, warmup, steps, flush, launch=None):
             n_agents = fish if tattr == "fish_type" else sharks
             blocks = n_agents / 64.0
             alg = n_agents * bpa + blocks * 12            # fields + R / snapshot read
-            if not reuse:                                 # enumeration inside the kernel
+            if reuse is None:                             # births: the occupancy grid scanned once
+                alg = 1024 * 1024
+            elif not reuse:                               # enumeration inside the kernel
                 alg += M / 8.0 + blocks * (12 + 8)        # level-0 bitmap, R/snapshot write, slot words
             r = acc.setdefault(meth, {"ms": [], "bytes": [], "units": []})
             r["ms"].append(e0.elapsed_time(e1))

@@ -99,10 +99,15 @@ typedef struct {
 #define DSOA_M_WATOR_SHARK_CHOOSE 303  /* prefer a fish neighbour, else an empty one     */
 #define DSOA_M_WATOR_SHARK_MOVE 304    /* eat (energy 3) or lose 1; breed at 10; starve  */
 #define DSOA_M_WATOR_KILL 305          /* agent of a KILL instance: delete this          */
+#define DSOA_M_WATOR_FISH_MOVE_DEFER 306 /* FISH_MOVE whose newborns are only marked (occ 3
+                                          at the old cell); K_WATOR_BIRTHS creates them  */
 #define DSOA_K_WATOR_INIT 350          /* n = w*h of `target`: agents from `init` (nullable,
                                           0/1/2) or Philox(seed; 0xFFFFFFFF, c, 0, 0) vs
                                           0.30 / 0.35 thresholds                          */
 #define DSOA_K_WATOR_ADVANCE 351       /* n = n_inst: t += 1 for RUN instances            */
+#define DSOA_K_WATOR_BIRTHS 352        /* n = n_inst: a Fish (age 0) at every cell marked
+                                          3 by FISH_MOVE_DEFER in RUN instances; the cell
+                                          becomes 1 (0 if the heap is full)              */
 typedef struct {
     dsoa_inst* inst;
     const uint8_t* init;

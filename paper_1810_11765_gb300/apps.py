@@ -238,20 +238,26 @@ class WatorWorld:
         return slot
 
     batch_enumeration = True
+    defer_births = False        # measured slower: the births kernel is an allocation burst
 
     def step(self):
         """One step.  The choose methods neither create nor delete agents of their
         own type, so each move method runs on its choose method's snapshot; and the
         fish methods neither create nor delete sharks, so the shark snapshot can be
         taken at the start of the step together with the fish snapshot, in one
-        enumeration launch."""
+        enumeration launch.  Newborn fish are created by the births kernel after
+        Fish.move (``defer_births``) or inside it."""
         a = self.args()
         if self.batch_enumeration and self.heap.separate_enumeration():
             self.heap.enumerate_many([self.fish_type, self.shark_type])
             self.heap.parallel_do_enumerated(self.fish_type, D.M_WATOR_FISH_CHOOSE, a)
         else:
             self.heap.parallel_do(self.fish_type, D.M_WATOR_FISH_CHOOSE, a)
-        self.heap.parallel_do_enumerated(self.fish_type, D.M_WATOR_FISH_MOVE, a)
+        if self.defer_births:
+            self.heap.parallel_do_enumerated(self.fish_type, D.M_WATOR_FISH_MOVE_DEFER, a)
+            self.heap.run_kernel(D.K_WATOR_BIRTHS, self.table.capacity, a)
+        else:
+            self.heap.parallel_do_enumerated(self.fish_type, D.M_WATOR_FISH_MOVE, a)
         if self.batch_enumeration and self.heap.separate_enumeration():
             self.heap.parallel_do_enumerated(self.shark_type, D.M_WATOR_SHARK_CHOOSE, a)
         else:

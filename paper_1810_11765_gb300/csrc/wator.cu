@@ -6,7 +6,8 @@
 //   Fish.choose   pick an empty N/E/S/W neighbour with Philox(seed; t, c, 1, 0),
 //                 claim it with atomicMin(source cell)
 //   Fish.move     age + 1; the lowest claimant moves; a mover of age >= 3
-//                 leaves a newborn fish and restarts its age
+//                 leaves a newborn fish and restarts its age (allocated in place,
+//                 or marked and allocated afterwards by the births kernel)
 //   Shark.choose  prefer fish neighbours, else empty ones, Philox(seed; t, c, 2, 0)
 //   Shark.move    age + 1; a winner eats (deletes the Fish object: cross-type
 //                 delete) and refills energy to 3, else loses 1; breeds at 10;
@@ -93,6 +94,39 @@ struct FishMove {
         }
         I.occ[old] = nf ? 1 : 0;
         I.cellmap[old] = nf;
+    }
+};
+
+// Fish.move with deferred births: a mover of breeding age marks its old cell
+// kBirth ("fish to be born") instead of allocating the newborn in place; the
+// births kernel below creates all newborns of the step in full warps.  Nothing
+// reads the old cell before that kernel: no fish can have claimed it, since it
+// was occupied when the claims were made.
+constexpr uint8_t kBirth = 3;
+
+struct FishMoveDeferred {
+    using Args = dsoa_wator_args;
+    static constexpr bool kNoNewOfOwnType = true;   /* streamable */
+    static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
+        const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        const dsoa_inst I = a.inst[k];
+        if (I.state != DSOA_INST_RUN) return;
+        uint32_t* cellp = dsoa_column<uint32_t>(c, t, bid, 1) + s;
+        uint32_t* agep = dsoa_column<uint32_t>(c, t, bid, 2) + s;
+        const uint32_t tg = dsoa_column<uint32_t>(c, t, bid, 3)[s];
+        uint32_t age = *agep + 1u;
+        const uint32_t old = *cellp;
+        if (tg != kNone && I.claim[tg] == old) {
+            I.claim[tg] = kNone;
+            I.occ[tg] = 1;
+            I.cellmap[tg] = dsoa_make_handle(t, bid, s);
+            *cellp = tg;
+            const bool breed = age >= kFishBreed;
+            if (breed) age = 0u;
+            I.occ[old] = breed ? kBirth : 0;
+            I.cellmap[old] = 0;
+        }
+        *agep = age;
     }
 };
 
@@ -226,6 +260,71 @@ __global__ void k_init(dsoa_ctx c, dsoa_wator_args a, uint64_t n) {
     }
 }
 
+// Births of the step: every CTA scans tiles of 2048 cells of each running
+// instance for kBirth marks, compacts them in shared memory and allocates the
+// newborn fish with full warps (so one warp leader reserves up to 32 slots at
+// once), then writes the handle map and the occupancy (0 if the heap is full).
+constexpr uint32_t kBirthTile = 2048;
+
+__global__ void __launch_bounds__(256) k_births(dsoa_ctx c, dsoa_wator_args a) {
+    __shared__ uint32_t list[kBirthTile];
+    __shared__ uint32_t wcount[8];
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    dsoa_pdl_wait();                 /* under programmatic dependent launch: Fish.move done */
+    dsoa_pdl_release();
+    for (uint32_t k = 0; k < a.n_inst; ++k) {
+        const dsoa_inst I = a.inst[k];
+        if (I.state != DSOA_INST_RUN) continue;                    /* uniform */
+        const uint64_t cells = (uint64_t)I.w * I.h;
+        const uint64_t tiles = (cells + kBirthTile - 1) / kBirthTile;
+        for (uint64_t tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
+            const uint64_t c0 = tl * kBirthTile + (uint64_t)tid * 8u;
+            uint8_t b[8];
+            if (c0 + 8 <= cells) {
+                const uint2 v = *reinterpret_cast<const uint2*>(I.occ + c0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) { b[i] = (uint8_t)(v.x >> (8 * i)); b[4 + i] = (uint8_t)(v.y >> (8 * i)); }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) b[i] = c0 + i < cells ? I.occ[c0 + i] : 0;
+            }
+            uint32_t own = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) own += b[i] == kBirth;
+            uint32_t x = own;                                     /* inclusive warp scan */
+#pragma unroll
+            for (uint32_t o = 1; o < 32u; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31u) wcount[warp] = x;
+            __syncthreads();
+            uint32_t pos = x - own, total = 0;
+            for (uint32_t w = 0; w < 8u; ++w) {
+                if (w < warp) pos += wcount[w];
+                total += wcount[w];
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (b[i] == kBirth) list[pos++] = (uint32_t)(c0 + i);
+            __syncthreads();
+            for (uint32_t i = tid; i < total; i += blockDim.x) {
+                const uint32_t cell = list[i];
+                const dsoa_obj o = dsoa_new(c, (uint32_t)a.fish_type);
+                if (o) {
+                    dsoa_field<uint32_t>(c, o, 0) = k;
+                    dsoa_field<uint32_t>(c, o, 1) = cell;
+                    dsoa_field<uint32_t>(c, o, 2) = 0u;
+                    dsoa_field<uint32_t>(c, o, 3) = kNone;
+                }
+                I.cellmap[cell] = o;
+                I.occ[cell] = o ? 1 : 0;
+            }
+            __syncthreads();                                      /* list and counts reused */
+        }
+    }
+}
+
 __global__ void k_advance(dsoa_inst* inst, uint32_t n) {
     dsoa_pdl_wait();
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,6 +342,8 @@ int dsoa_wator_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
     switch (method) {
         case DSOA_M_WATOR_FISH_CHOOSE: return fish ? dsoa_run_doall<FishChoose>(h, type, args) : DSOA_ERR_INVALID_ARG;
         case DSOA_M_WATOR_FISH_MOVE: return fish ? dsoa_run_doall<FishMove>(h, type, args) : DSOA_ERR_INVALID_ARG;
+        case DSOA_M_WATOR_FISH_MOVE_DEFER:
+            return fish ? dsoa_run_doall<FishMoveDeferred>(h, type, args) : DSOA_ERR_INVALID_ARG;
         case DSOA_M_WATOR_SHARK_CHOOSE: return shark ? dsoa_run_doall<SharkChoose>(h, type, args) : DSOA_ERR_INVALID_ARG;
         case DSOA_M_WATOR_SHARK_MOVE: return shark ? dsoa_run_doall<SharkMove>(h, type, args) : DSOA_ERR_INVALID_ARG;
         case DSOA_M_WATOR_KILL: return (fish || shark) ? dsoa_run_doall<Kill>(h, type, args) : DSOA_ERR_INVALID_ARG;
@@ -264,6 +365,14 @@ int dsoa_wator_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_
             const int tpb = 256;
             k_init<<<dsoa_new_grid(h, n, tpb), tpb, 0, h->stream>>>(dsoa_launch_ctx(h), args, n);
             return dsoa_check_launch(h);
+        }
+        case DSOA_K_WATOR_BIRTHS: {
+            if (n > args.n_inst || args.fish_type < 0 || args.fish_type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+            args.n_inst = (uint32_t)n;
+            auto* k = &k_births;
+            const unsigned grid = (unsigned)(std::max(1, dsoa_resident_ctas(reinterpret_cast<const void*>(k), 256)) *
+                                             h->num_sms);
+            return dsoa_launch_step(h, k, grid, 256u, dsoa_launch_ctx(h), args);
         }
         case DSOA_K_WATOR_ADVANCE:
             if (n > args.n_inst) return DSOA_ERR_INVALID_ARG;

@@ -169,3 +169,23 @@ def test_enumerate_many_equals_separate_enumerations(scan_tiles):
     assert np.array_equal(lst, sep[w.fish_type][0])
     assert heap.get_error() == 0
     heap.close()
+
+
+@pytest.mark.parametrize("defer", [False, True])
+def test_births_in_place_or_deferred_match_oracle(defer):
+    """Newborn fish allocated inside Fish.move or by the births kernel after it:
+    both give the oracle's populations per step and final grid."""
+    W, H, steps, seed = 96, 64, 60, 12
+    heap, w = world(32 << 20)
+    w.defer_births = defer
+    s = w.add(W, H, seed)
+    _, st = oracle.wator_run(W, H, steps, seed=seed)
+    for k in range(steps):
+        w.step()
+        assert w.counts() == (st[k]["fish"], st[k]["sharks"]), k
+    ref, _ = oracle.wator_run(W, H, steps, seed=seed)
+    assert np.array_equal(w.read(s), ref)
+    assert heap.get_error() == 0
+    host = host_check(heap, 2)
+    assert all(v == 0 for v in host["violations"].values()), host
+    heap.close()
