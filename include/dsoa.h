@@ -163,6 +163,10 @@ int dsoa_count(dsoa_heap* h, int type, uint64_t* out_host);
 /* Same, written to device memory `out_dev` (uint64); graph-capturable. */
 int dsoa_count_async(dsoa_heap* h, int type, uint64_t* out_dev);
 
+/* Live objects of `ntypes` distinct types (ids at types_host) in one launch:
+ * out_dev[q] (uint64) = live objects of types_host[q].  Graph-capturable. */
+int dsoa_count_many_async(dsoa_heap* h, const int* types_host, int ntypes, uint64_t* out_dev);
+
 /* Number of free blocks (popcount of the free-block bitmap) to `out_dev`
  * (uint64); graph-capturable.  Used for admission control. */
 int dsoa_free_blocks_async(dsoa_heap* h, uint64_t* out_dev);

@@ -414,6 +414,35 @@ __global__ void k_count(dsoa_ctx c, uint32_t b, uint64_t tiles, unsigned long lo
     if (lane == 0 && cnt) atomicAdd(out, (unsigned long long)cnt);
 }
 
+// Live objects of several types in one launch: CTA-tiles over (type, level-1
+// tile) pairs, the same per-tile work as k_count, into out[q] (pre-zeroed).
+struct CountBatch {
+    uint32_t n;
+    uint32_t b[DSOA_MAX_TYPES];
+};
+__global__ void k_count_many(dsoa_ctx c, uint64_t tiles, CountBatch cb, unsigned long long* out) {
+    const uint32_t lane = threadIdx.x & 31u, wpc = blockDim.x >> 5;
+    const uint64_t total = tiles * cb.n;
+    for (uint64_t g = (uint64_t)blockIdx.x * wpc + (threadIdx.x >> 5); g < total; g += (uint64_t)gridDim.x * wpc) {
+        const uint32_t q = (uint32_t)(g / tiles);
+        const uint64_t t = g - (uint64_t)q * tiles;
+        const unsigned long long* L0 = dsoa_level(c, cb.b[q], 0);
+        const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, cb.b[q], 1) : nullptr;
+        uint32_t cnt = 0;
+        unsigned long long sel = L1 ? L1[t] : 1ull;
+        for (; sel; sel &= sel - 1ull) {
+            const uint64_t wi = t * 64 + (uint64_t)(__ffsll((long long)sel) - 1);
+            if (wi >= c.lvl_words[0]) break;
+            const unsigned long long w = L0[wi];
+            const uint64_t bid = wi * 64 + lane;
+            if ((w >> lane) & 1ull) cnt += __popcll(~c.slot[bid]);
+            if ((w >> (lane + 32)) & 1ull) cnt += __popcll(~c.slot[bid + 32]);
+        }
+        cnt = warp_sum(cnt);
+        if (lane == 0 && cnt) atomicAdd(&out[q], (unsigned long long)cnt);
+    }
+}
+
 __global__ void k_popc_level0(dsoa_ctx c, uint32_t b, unsigned long long* out) {
     const unsigned long long* L0 = dsoa_level(c, b, 0);
     uint32_t cnt = 0;
@@ -845,6 +874,24 @@ int dsoa_count_async(dsoa_heap* h, int type, uint64_t* out_dev) {
     DSOA_CUDA_TRY(cudaMemsetAsync(out_dev, 0, 8, h->stream));
     const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((h->tiles + 7) / 8, (uint64_t)h->num_sms * 8));
     k_count<<<g, 256, 0, h->stream>>>(h->ctx, dsoa_bm_alloc((uint32_t)type), h->tiles, (unsigned long long*)out_dev);
+    return dsoa_check_launch(h);
+}
+
+int dsoa_count_many_async(dsoa_heap* h, const int* types_host, int ntypes, uint64_t* out_dev) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (!types_host || !out_dev || ntypes < 1 || ntypes > h->ntypes) return DSOA_ERR_INVALID_ARG;
+    CountBatch cb;
+    std::memset(&cb, 0, sizeof(cb));
+    cb.n = (uint32_t)ntypes;
+    for (int q = 0; q < ntypes; ++q) {
+        if (types_host[q] < 0 || types_host[q] >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+        cb.b[q] = dsoa_bm_alloc((uint32_t)types_host[q]);
+    }
+    DSOA_CUDA_TRY(cudaMemsetAsync(out_dev, 0, 8 * (size_t)ntypes, h->stream));
+    const uint64_t warps = h->tiles * (uint64_t)ntypes;
+    const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 7) / 8, (uint64_t)h->num_sms * 8));
+    k_count_many<<<g, 256, 0, h->stream>>>(h->ctx, h->tiles, cb, (unsigned long long*)out_dev);
     return dsoa_check_launch(h);
 }
 

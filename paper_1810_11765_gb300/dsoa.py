@@ -97,7 +97,7 @@ ABI_FUNCTIONS = [
     "dsoa_heap_create", "dsoa_heap_create_from", "dsoa_register_type", "dsoa_heap_freeze",
     "dsoa_heap_info", "dsoa_field_offset", "dsoa_parallel_new", "dsoa_parallel_do",
     "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_delete_handles", "dsoa_enumerate",
-    "dsoa_enumerate_many", "dsoa_count", "dsoa_count_async",
+    "dsoa_enumerate_many", "dsoa_count", "dsoa_count_async", "dsoa_count_many_async",
     "dsoa_free_blocks_async", "dsoa_get_error", "dsoa_check", "dsoa_export_state",
     "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
     "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_set_lookups",
@@ -133,7 +133,7 @@ def load(path: str | None = None):
         "dsoa_parallel_new": [vp, i32, u64, i32, vp, sz], "dsoa_parallel_do": [vp, i32, i32, vp, sz],
         "dsoa_parallel_do_enumerated": [vp, i32, i32, vp, sz],
         "dsoa_run_kernel": [vp, i32, u64, vp, sz], "dsoa_enumerate": [vp, i32, vp, vp, vp],
-        "dsoa_enumerate_many": [vp, vp, i32],
+        "dsoa_enumerate_many": [vp, vp, i32], "dsoa_count_many_async": [vp, vp, i32, vp],
         "dsoa_delete_handles": [vp, vp, u64],
         "dsoa_count": [vp, i32, vp], "dsoa_count_async": [vp, i32, vp],
         "dsoa_free_blocks_async": [vp, vp], "dsoa_get_error": [vp, vp], "dsoa_check": [vp, vp],
@@ -296,6 +296,11 @@ class Heap:
         out = ctypes.c_uint64()
         _ok(load().dsoa_count(self._h, t, ctypes.byref(out)), "dsoa_count")
         return out.value
+
+    def count_many_async(self, types, out_dev):
+        """Live objects of each type into out_dev[0..len(types)) (uint64), one launch."""
+        arr = (ctypes.c_int * len(types))(*types)
+        _ok(load().dsoa_count_many_async(self._h, arr, len(types), _addr(out_dev)), "dsoa_count_many_async")
 
     def count_async(self, t: int, out_dev):
         _ok(load().dsoa_count_async(self._h, t, _addr(out_dev)), "dsoa_count_async")

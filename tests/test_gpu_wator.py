@@ -189,3 +189,27 @@ def test_births_in_place_or_deferred_match_oracle(defer):
     host = host_check(heap, 2)
     assert all(v == 0 for v in host["violations"].values()), host
     heap.close()
+
+
+def test_count_many_matches_count_and_is_capturable():
+    """Populations of both types in one launch, inside a captured step graph."""
+    import torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        heap, w = world(64 << 20)
+        w.add(128, 96, 21)
+        out = torch.zeros(2, dtype=torch.int64, device="cuda")
+        heap.graph_begin()
+        w.step()
+        heap.count_many_async([w.fish_type, w.shark_type], out)
+        g = heap.graph_end()
+        _, st = oracle.wator_run(128, 96, 12, seed=21)
+        for k in range(12):
+            g.launch()
+            got = out.cpu().tolist()
+            assert got == [st[k]["fish"], st[k]["sharks"]], k
+            assert got == [heap.count(w.fish_type), heap.count(w.shark_type)]
+        heap.count_many_async([w.shark_type], out[1:])
+        assert int(out[1].item()) == heap.count(w.shark_type)
+        g.close()
+        heap.close()
