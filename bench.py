@@ -814,7 +814,10 @@ def dsoa_arm(args):
         ach = nb["pair_terms_per_s_tiled"] * NBODY_OPS_PER_PAIR
         nb["roofline"] = {"kernel": "k_force_tiled", "bound": "alu", "achieved": ach / 1e12,
                           "peak": peak_ops / 1e12, "unit": "Tops/s", "frac": ach / peak_ops,
-                          "traffic": None, "ops_per_pair": NBODY_OPS_PER_PAIR,
+                          "traffic": ncu_traffic("k_force_tiled", 1 << 16),
+                          "traffic_unit": "DRAM bytes per launch (ncu, scaled per body from a 16,384-body "
+                                          "capture: the bodies stay in L2, DRAM traffic grows with n)",
+                          "ops_per_pair": NBODY_OPS_PER_PAIR,
                           "peak_kind": f"derived: SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (median SM clock "
                                        "of the headline run)"}
         out["nbody_65536"] = nb
