@@ -471,6 +471,55 @@ def heap_utilisation(heap_bytes=1 << 30):
             "utilisation": live * 16 / heap_bytes}
 
 
+def largest_instance(kind, heap_bytes=64 << 20, steps=40, mode=0, lo=64, hi=4096):
+    """Largest torus side (a multiple of 32) of a game-of-life or Wa-Tor instance
+    whose objects fit in a heap of `heap_bytes` for `steps` steps without an
+    allocation failure, by bisection (the grids live outside the heap)."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D, inputs
+    from paper_1810_11765_gb300.apps import GolWorld, WatorWorld
+
+    def fits(side):
+        heap = D.Heap(heap_bytes)
+        w = GolWorld(heap) if kind == "gol" else WatorWorld(heap)
+        heap.set_capacity_mode(mode)
+        heap.freeze()
+        seed = inputs.GolConfig().seed if kind == "gol" else inputs.WatorConfig().seed
+        ok = True
+        try:
+            w.add(side, side, seed)
+            for _ in range(steps):
+                w.step()
+            ok = heap.get_error() == 0
+        finally:
+            heap.close()
+            del w
+            torch.cuda.empty_cache()
+        return ok
+
+    lo_s, hi_s = lo // 32, hi // 32 + 1          # fits(lo) assumed, fits(hi + 32) not
+    if not fits(lo):
+        return 0
+    while hi_s - lo_s > 1:
+        mid = (lo_s + hi_s) // 2
+        if fits(mid * 32):
+            lo_s = mid
+        else:
+            hi_s = mid
+    return lo_s * 32
+
+
+def largest_instance_leg(heap_bytes=64 << 20, steps=40):
+    from paper_1810_11765_gb300 import dsoa as D
+    out = {"heap_bytes": heap_bytes, "steps": steps,
+           "method": "bisection over the torus side (multiples of 32); fits = no allocation failure"}
+    for kind in ("wator", "gol"):
+        for name, mode in (("uniform", D.CAPACITY_UNIFORM), ("per_type", D.CAPACITY_PER_TYPE)):
+            side = largest_instance(kind, heap_bytes, steps, mode)
+            out[f"{kind}_{name}"] = {"side": side, "cells": side * side}
+    return out
+
+
 def e2e_wator(seed, warmup, steps, flush, launch=None):
     """Whole job through the public API with host buffers: initial grid uploaded
     from pinned host memory, K graph steps, per-step populations read back to
@@ -803,6 +852,7 @@ def dsoa_arm(args):
         out["alloc_roofline"] = alloc_roofline(storm, out["l2_atomic_peak"])
         out["heap_utilisation"] = heap_utilisation()
         out["bitmapalloc"] = bitmap_legs(flush)
+        out["largest_instance"] = largest_instance_leg()
         # --- other apps (plain vs graph) and serving
         out["gol_512"] = app_steps("gol", 100, flush)
         out["gol_4096"] = app_steps("gol", 20, flush, side=4096)
