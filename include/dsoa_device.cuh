@@ -480,6 +480,16 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
     return 0ull;
 }
 
+/* Prefetch into L1 the warp's block hint for type t (advisory: a method that
+ * may allocate calls it early, so that the leader's hint load in dsoa_new
+ * overlaps with the method's own loads instead of starting its chain). */
+__device__ __forceinline__ void dsoa_prefetch_hint(const dsoa_ctx& c, uint32_t t) {
+    if (!c.hint || (c.flags & DSOA_FLAG_NO_HINT)) return;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const dsoa_hint* hp = c.hint + (gwarp & c.hint_mask) * c.ntypes + t;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(hp));
+}
+
 /* new(d_allocator) T (Sec. 2.1; Alg. 1): callable from any kernel, any
  * divergence.  Same-type requests of a warp are coalesced (__match_any_sync):
  * the lowest lane of each group reserves slots for the whole group, block by

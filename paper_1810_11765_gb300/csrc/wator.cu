@@ -67,6 +67,7 @@ struct FishChoose {
 struct FishMove {
     using Args = dsoa_wator_args;
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
+        dsoa_prefetch_hint(c, t);
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
         const dsoa_inst I = a.inst[k];
         if (I.state != DSOA_INST_RUN) return;
@@ -164,6 +165,7 @@ struct SharkChoose {
 struct SharkMove {
     using Args = dsoa_wator_args;
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
+        dsoa_prefetch_hint(c, t);
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
         const dsoa_inst I = a.inst[k];
         if (I.state != DSOA_INST_RUN) return;
