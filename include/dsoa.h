@@ -199,6 +199,20 @@ int dsoa_check(dsoa_heap* h, uint64_t* out_host);
 int dsoa_export_state(dsoa_heap* h, void* out_host, size_t capacity, size_t* bytes_needed,
                       uint64_t* bitmap_words);
 
+/* Checkpoint / resume (the paper has no counterpart).  dsoa_heap_save copies
+ * the whole heap -- blocks, slot words, type ids, bitmaps, block lists -- behind
+ * a header that records the layout into host memory `out_host` (capacity bytes,
+ * at least *bytes_needed = header + heap bytes; pass out_host = NULL to query).
+ * dsoa_heap_load copies such an image into a heap created with the same byte
+ * size and the same registered types and capacity mode (the layout must match
+ * exactly, else DSOA_ERR_INVALID_ARG); it freezes the heap first if needed.
+ * References inside the heap are indices, so the image is valid at any device
+ * address; object handles saved elsewhere (e.g. cell maps) stay valid.  Both
+ * are synchronous and not allowed during stream capture.  Work still queued on
+ * other streams must be finished by the caller. */
+int dsoa_heap_save(dsoa_heap* h, void* out_host, size_t capacity, size_t* bytes_needed);
+int dsoa_heap_load(dsoa_heap* h, const void* in_host, size_t bytes);
+
 /* Device-side view of the heap for user kernels built with dsoa_device.cuh:
  * copies the struct dsoa_ctx (size ctx_bytes must match) to ctx_out_host. */
 int dsoa_get_ctx(dsoa_heap* h, void* ctx_out_host, size_t ctx_bytes);

@@ -961,6 +961,66 @@ int dsoa_export_state(dsoa_heap* h, void* out_host, size_t capacity, size_t* byt
     return DSOA_OK;
 }
 
+// Checkpoint image: a header that pins the layout, then the heap's bytes.  Every
+// reference inside the heap (handles, block lists, bitmaps) is an index, not an
+// address, so the bytes are valid in any heap with the same layout.
+struct dsoa_image_header {
+    uint64_t magic, version, bytes, M, meta;
+    uint32_t block_bytes, nlevels, ntypes, capacity_mode;
+    uint32_t nfields[DSOA_MAX_TYPES];
+    uint32_t field_bytes[DSOA_MAX_TYPES][DSOA_MAX_FIELDS];
+    uint32_t capacity[DSOA_MAX_TYPES];
+};
+static const uint64_t kImageMagic = 0x31304D4941534F44ull;   // "DOSAIM01"
+
+static void image_header(const dsoa_heap* h, dsoa_image_header* H) {
+    std::memset(H, 0, sizeof(*H));
+    H->magic = kImageMagic;
+    H->version = 1;
+    H->bytes = h->bytes;
+    H->M = h->ctx.M;
+    H->meta = h->meta_bytes;
+    H->block_bytes = h->ctx.block_bytes;
+    H->nlevels = h->ctx.nlevels;
+    H->ntypes = (uint32_t)h->ntypes;
+    H->capacity_mode = (uint32_t)h->capacity_mode;
+    for (int t = 0; t < h->ntypes; ++t) {
+        H->nfields[t] = (uint32_t)h->types[t].nfields;
+        for (int f = 0; f < h->types[t].nfields; ++f) H->field_bytes[t][f] = h->types[t].field_bytes[f];
+        H->capacity[t] = h->types[t].capacity;
+    }
+}
+
+int dsoa_heap_save(dsoa_heap* h, void* out_host, size_t capacity, size_t* bytes_needed) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    const size_t need = sizeof(dsoa_image_header) + h->bytes;
+    if (bytes_needed) *bytes_needed = need;
+    if (!out_host) return DSOA_OK;
+    if (capacity < need) return DSOA_ERR_INVALID_ARG;
+    if (capturing(h->stream)) return DSOA_ERR_CAPTURE;
+    image_header(h, (dsoa_image_header*)out_host);
+    DSOA_CUDA_TRY(cudaMemcpyAsync((char*)out_host + sizeof(dsoa_image_header), h->base, h->bytes,
+                                  cudaMemcpyDeviceToHost, h->stream));
+    DSOA_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return DSOA_OK;
+}
+
+int dsoa_heap_load(dsoa_heap* h, const void* in_host, size_t bytes) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (!in_host || bytes != sizeof(dsoa_image_header) + h->bytes) return DSOA_ERR_INVALID_ARG;
+    if (capturing(h->stream)) return DSOA_ERR_CAPTURE;
+    dsoa_image_header mine;
+    image_header(h, &mine);
+    if (std::memcmp(&mine, in_host, sizeof(mine)) != 0) return DSOA_ERR_INVALID_ARG;
+    DSOA_CUDA_TRY(cudaMemcpyAsync(h->base, (const char*)in_host + sizeof(dsoa_image_header), h->bytes,
+                                  cudaMemcpyHostToDevice, h->stream));
+    DSOA_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (int t = 0; t < h->ntypes; ++t) h->enumerated[t] = false;   // enumerate again before reuse
+    return DSOA_OK;
+}
+
 int dsoa_get_ctx(dsoa_heap* h, void* out, size_t nb) {
     if (!h || !out || nb != sizeof(dsoa_ctx)) return DSOA_ERR_INVALID_ARG;
     int rc = dsoa_ensure_frozen(h);

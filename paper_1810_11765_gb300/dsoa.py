@@ -99,6 +99,7 @@ ABI_FUNCTIONS = [
     "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_delete_handles", "dsoa_enumerate",
     "dsoa_enumerate_many", "dsoa_count", "dsoa_count_async", "dsoa_count_many_async",
     "dsoa_free_blocks_async", "dsoa_get_error", "dsoa_check", "dsoa_export_state",
+    "dsoa_heap_save", "dsoa_heap_load",
     "dsoa_get_ctx", "dsoa_graph_begin", "dsoa_graph_end", "dsoa_graph_launch",
     "dsoa_graph_destroy", "dsoa_set_launch", "dsoa_set_flags", "dsoa_set_lookups",
     "dsoa_type_stats", "dsoa_launch_count", "dsoa_set_capacity_mode", "dsoa_type_capacity",
@@ -138,6 +139,7 @@ def load(path: str | None = None):
         "dsoa_count": [vp, i32, vp], "dsoa_count_async": [vp, i32, vp],
         "dsoa_free_blocks_async": [vp, vp], "dsoa_get_error": [vp, vp], "dsoa_check": [vp, vp],
         "dsoa_export_state": [vp, vp, sz, vp, vp], "dsoa_get_ctx": [vp, vp, sz],
+        "dsoa_heap_save": [vp, vp, sz, vp], "dsoa_heap_load": [vp, vp, sz],
         "dsoa_graph_begin": [vp], "dsoa_graph_end": [vp, vp], "dsoa_graph_launch": [vp, vp],
         "dsoa_graph_destroy": [vp], "dsoa_set_launch": [vp, i32, i32, i32, i32, i32],
         "dsoa_set_flags": [vp, u32], "dsoa_launch_count": [vp, vp], "dsoa_heap_destroy": [vp],
@@ -330,6 +332,20 @@ class Heap:
         btype = buf[M * 8:M * 12].view(np.uint32)
         bm = buf[M * 12:].view(np.uint64).reshape(-1, words.value)
         return {"slot": slot, "btype": btype, "bitmaps": bm}
+
+    def save(self) -> np.ndarray:
+        """Checkpoint image of the heap (header + heap bytes) in host memory."""
+        need = ctypes.c_size_t()
+        L = load()
+        _ok(L.dsoa_heap_save(self._h, None, 0, ctypes.byref(need)), "dsoa_heap_save")
+        buf = np.empty(need.value, dtype=np.uint8)
+        _ok(L.dsoa_heap_save(self._h, buf.ctypes.data, need.value, ctypes.byref(need)), "dsoa_heap_save")
+        return buf
+
+    def load_image(self, image: np.ndarray):
+        """Restore a checkpoint image taken from a heap of the same layout."""
+        img = np.ascontiguousarray(image, dtype=np.uint8)
+        _ok(load().dsoa_heap_load(self._h, img.ctypes.data, img.size), "dsoa_heap_load")
 
     def set_launch(self, tpb=0, ctas_per_sm=0, slots_per_thread=0, scan_tiles=0, waves=0):
         _ok(load().dsoa_set_launch(self._h, tpb, ctas_per_sm, slots_per_thread, scan_tiles, waves),
