@@ -694,20 +694,28 @@ def nbody_leg(flush, steps=5, collide_steps=10):
     return out
 
 
-def serving_leg(n_req=24, rates=(50.0, 200.0)):
+def serving_leg(n_req=24, multiples=(0.25, 0.5, 1.0, 2.0)):
     """Continuous batching of game-of-life / wa-tor instances (sides 2^8..2^10 and
-    100..300 steps to bound the run time) at swept Poisson arrival rates."""
+    100..300 steps to bound the run time).  The service rate is measured first with
+    every request arriving at once (requests / wall time); Poisson arrival rates are
+    then swept as multiples of it."""
     from paper_1810_11765_gb300 import inputs
     from paper_1810_11765_gb300.serving import Server
-    out = []
-    for rate in rates:
+
+    def run(rate):
         reqs = inputs.serving_requests(n_req, rate_per_s=rate, side_log2_min=8, side_log2_max=10,
                                        steps_min=100, steps_max=300)
         srv = Server(8 << 30, capacity=32)
         _, summary = srv.run(reqs)
         srv.close()
         summary.pop("rejected", None)
-        out.append({"rate_per_s": rate, **summary})
+        return summary
+
+    burst = run(1e9)                               # all arrivals at t = 0
+    service_rate = n_req / burst["wall_s"]
+    out = [{"rate_per_s": None, "arrivals": "all at once", "service_rate_per_s": service_rate, **burst}]
+    for m in multiples:
+        out.append({"rate_per_s": m * service_rate, "rate_vs_service": m, **run(m * service_rate)})
     return out
 
 
