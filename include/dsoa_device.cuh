@@ -319,7 +319,7 @@ __device__ inline void dsoa_block_init(const dsoa_ctx& c, uint64_t bid, uint32_t
     dsoa_st(&c.slot[bid], DSOA_ALL);
 }
 
-/* invalidate + delete an emptied block (Alg. 2 lines 7-11 with Alg. 10):
+/* invalidate + delete an emptied block (Alg. 2's deletion branch with Alg. 10):
  * take every slot with one atomicAnd(0).  Success iff all 64 were free; then
  * the block leaves active[t] and allocated[t] and returns to the free bitmap.
  * Otherwise give back exactly the slots taken (atomicOr(before)); if another
@@ -372,19 +372,26 @@ __device__ __forceinline__ void dsoa_block_release(const dsoa_ctx& c, uint32_t t
     if ((before | bits) == DSOA_ALL) dsoa_block_invalidate(c, bid);          /* EMPTY */
 }
 
-/* Slow path of Alg. 1 (lines 3-6): take a free block, initialise it for type
- * t, enter it into allocated[t] and active[t].  -1 = no free block, -2 = every
- * attempt lost its race. */
-static __device__ __noinline__ int64_t dsoa_block_new(const dsoa_ctx& c, uint32_t t, uint32_t h) {
+/* Slow path of Alg. 1 (a new block) with the reservation folded in: take a free
+ * block and initialise it for type t with the `mask` slots already taken (type first,
+ * fence, then the slot word), enter it into allocated[t], and into active[t]
+ * unless the reservation filled it.  Slots are only ever taken from the word,
+ * so nobody can take these, and a block with reserved slots cannot be emptied,
+ * invalidated or retyped: no reservation atomic and no type re-check are needed.
+ * -1 = no free block, -2 = every attempt lost its race. */
+static __device__ __noinline__ int64_t dsoa_block_new_reserved(const dsoa_ctx& c, uint32_t t, uint32_t h,
+                                                               unsigned long long mask) {
     const int64_t bid = dsoa_bm_take(c, dsoa_bm_free(), h);
     if (bid < 0) return bid;
-    dsoa_block_init(c, (uint64_t)bid, t);
+    dsoa_st32(&c.btype[bid], t);
+    __threadfence();
+    dsoa_st(&c.slot[bid], DSOA_ALL & ~mask);
     dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid);
-    dsoa_bm_set(c, dsoa_bm_active(t), (uint64_t)bid);
+    if (c.cap[t] & ~mask) dsoa_bm_set(c, dsoa_bm_active(t), (uint64_t)bid);
     return bid;
 }
 
-/* Roll back slots reserved in a block whose type changed (Alg. 1, line 14). */
+/* Roll back slots reserved in a block whose type changed (Alg. 1's type check). */
 static __device__ __noinline__ void dsoa_rollback(const dsoa_ctx& c, uint32_t bt, uint64_t bid, unsigned long long got) {
     dsoa_block_release(c, bt, bid, got);
 }
@@ -431,7 +438,8 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
         for (uint32_t a = 0; search && a < c.lookups && bid < 0; ++a)
             bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
         if (bid < 0) {
-            bid = dsoa_block_new(c, t, h ^ round);
+            const unsigned long long fmask = dsoa_lowest_k(c.cap[t], want);
+            bid = dsoa_block_new_reserved(c, t, h ^ round, fmask);
             if (bid == -2) continue;
             if (bid < 0) {
                 /* No free block.  Blocks that other warps initialised in the
@@ -442,7 +450,10 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
                 __nanosleep(256u);
                 continue;
             }
-            w = c.cap[t];              /* just initialised by this thread */
+            const unsigned long long left = c.cap[t] & ~fmask;    /* fresh block: reserved on init */
+            if (hp) *hp = dsoa_hint{left, left ? (uint64_t)bid : DSOA_NO_HINT_BLOCK};
+            *bid_out = (uint64_t)bid;
+            return fmask;
         }
         if (!w) {
             w = dsoa_ld(&c.slot[bid]) & c.cap[t];
