@@ -386,8 +386,21 @@ static __device__ __noinline__ int64_t dsoa_block_new_reserved(const dsoa_ctx& c
     dsoa_st32(&c.btype[bid], t);
     __threadfence();
     dsoa_st(&c.slot[bid], DSOA_ALL & ~mask);
-    dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid);
-    if (c.cap[t] & ~mask) dsoa_bm_set(c, dsoa_bm_active(t), (uint64_t)bid);
+    /* allocated[t] and active[t]: both level-0 RMWs in flight together; each
+     * falls back to dsoa_bm_set's retry loop if its bit was already set, and
+     * propagates upwards if its container was empty */
+    const unsigned long long m = 1ull << ((uint64_t)bid & 63u);
+    const bool act = (c.cap[t] & ~mask) != 0ull;
+    unsigned long long* wa = dsoa_level(c, dsoa_bm_alloc(t), 0) + ((uint64_t)bid >> 6);
+    unsigned long long* wv = dsoa_level(c, dsoa_bm_active(t), 0) + ((uint64_t)bid >> 6);
+    const unsigned long long pa = atomicOr(wa, m);
+    const unsigned long long pv = act ? atomicOr(wv, m) : m;
+    if (pa & m) dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid);
+    else if (pa == 0ull && c.nlevels > 1) dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid >> 6, 1);
+    if (act) {
+        if (pv & m) dsoa_bm_set(c, dsoa_bm_active(t), (uint64_t)bid);
+        else if (pv == 0ull && c.nlevels > 1) dsoa_bm_set(c, dsoa_bm_active(t), (uint64_t)bid >> 6, 1);
+    }
     return bid;
 }
 
