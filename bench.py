@@ -719,6 +719,29 @@ def serving_leg(n_req=24, multiples=(0.25, 0.5, 1.0, 2.0)):
     return out
 
 
+def cpu_baselines_secondary():
+    """The oracle on bounded samples of the secondary workloads (single-threaded):
+    n-body pair terms/s and microbench objects/s (new + do-all + delete per round)."""
+    import oracle
+    from paper_1810_11765_gb300 import inputs
+    c = inputs.NBodyConfig()
+    n = 4096
+    t0 = time.perf_counter()
+    oracle.nbody_run(n, 1, c.seed, G=c.G, dt=c.dt, eps2=c.eps2, rc2=c.rc2, fscale=c.fscale,
+                     vscale=c.vscale, mass_max=c.mass_max)
+    dt_nb = time.perf_counter() - t0
+    m = inputs.MicroConfig()
+    t0 = time.perf_counter()
+    oracle.micro_run(m.seed, m.n_per_round, m.rounds)
+    dt_mi = time.perf_counter() - t0
+    return {"nbody": {"value": n * (n - 1) / dt_nb, "unit": "pair terms/s", "cores": 1, "kind": "oracle",
+                      "sample": f"one FORCE + MOVE step of {n} bodies of the n-body workload"},
+            "microbench": {"value": m.n_per_round * m.rounds / dt_mi, "unit": "objects/s", "cores": 1,
+                           "kind": "oracle",
+                           "sample": f"the configured microbench: {m.rounds} rounds of {m.n_per_round} new, "
+                                     "do-all, parity delete"}}
+
+
 def cpu_baseline(seed, sample_steps=100):
     import oracle
     t0 = time.perf_counter()
@@ -883,6 +906,7 @@ def dsoa_arm(args):
         out["e2e"] = e2e_wator(seed, args.warmup, args.steps, flush, launch)
         # --- oracle on the host cores
         out["cpu_baseline"] = cpu_baseline(seed)
+        out["cpu_baselines_secondary"] = cpu_baselines_secondary()
     dist.barrier()
     if dist.rank == 0:
         print(json.dumps(out), flush=True)
