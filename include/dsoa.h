@@ -248,8 +248,11 @@ int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
  * enumeration and do-all kernels, and DSOA_FLAG_PDL (16) launches the
  * enumeration, do-all and step-counter kernels with programmatic dependent
  * launch, so that each may be scheduled while its predecessor finishes (the
- * last three are not in the paper).  Returns DSOA_ERR_INVALID_ARG for an
- * unknown bit.  Takes effect for launches issued after the call. */
+ * last three are not in the paper); DSOA_FLAG_ENUM_TICKETS (32) makes the
+ * single-pass enumeration hand tiles out by a ticket counter instead of
+ * ordering them by CTA index (which relies on every CTA of the launch being
+ * resident: true on an otherwise idle GPU).  Returns DSOA_ERR_INVALID_ARG for
+ * an unknown bit.  Takes effect for launches issued after the call. */
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags);
 
 /* r of Sec. 4.2 / Fig. 11: attempts to find an active block (try_find_set on

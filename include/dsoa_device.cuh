@@ -111,6 +111,11 @@ struct dsoa_ctx {
 #define DSOA_HINT_SLOTS 8192u             /* max hint-table warp slots per type     */
 #define DSOA_FLAG_FUSED 8u                /* one cooperative enumerate+do-all launch */
 #define DSOA_FUSED_MAX_CTAS 2048u         /* grid limit of the fused do-all         */
+#define DSOA_FLAG_ENUM_TICKETS 32u        /* single-pass enumeration: hand tiles out by a
+                                             ticket counter instead of relying on every
+                                             CTA of the launch being resident (for heaps
+                                             enumerated while other kernels occupy the
+                                             GPU); slower on large heaps                */
 #define DSOA_FLAG_PDL 16u                 /* programmatic dependent launch of the
                                              enumeration, do-all and step kernels  */
 #define DSOA_GRID_SCRATCH (DSOA_FUSED_MAX_CTAS + 64u)

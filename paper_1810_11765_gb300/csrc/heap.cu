@@ -391,6 +391,129 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint64_t tiles
     }
 }
 
+// The same enumeration for heaps whose tiles do not fit on the GPU as one
+// resident wave of CTAs: each CTA takes G consecutive level-1 tiles (G <=
+// kEnumGMax), publishes the aggregate of all of them and looks back over the
+// preceding CTAs of its type (so every CTA of the launch is resident and the
+// CTA index orders the chain); it then writes its tiles' blocks in order, one
+// tile of block ids staged in shared memory at a time.  R stays sorted.
+constexpr uint32_t kEnumGMax = 16;
+
+__global__ void __launch_bounds__(64) k_enum_lookback_multi(dsoa_ctx c, uint64_t tiles, uint32_t G, uint32_t ctas,
+                                                            EnumBatch eb) {
+    __shared__ uint32_t list[4096];
+    __shared__ uint32_t tsum[kEnumGMax][2];
+    __shared__ uint32_t s_ep;
+    __shared__ unsigned long long s_prefix;
+    const uint32_t qt = blockIdx.x / ctas;
+    const uint32_t cta = blockIdx.x - qt * ctas;
+    const uint32_t b = eb.b[qt];
+    unsigned long long* __restrict__ state = eb.state[qt];
+    uint32_t* __restrict__ ctl = eb.ctl[qt];
+    uint32_t* __restrict__ R = eb.R[qt];
+    unsigned long long* __restrict__ Rocc = eb.Rocc[qt];
+    uint32_t* __restrict__ r_dev = eb.r_dev[qt];
+    uint32_t* ticket = ctl;
+    uint32_t* done = ctl + 1;
+    uint32_t* epoch = ctl + 2;
+    const uint32_t j = threadIdx.x, lane = j & 31u, warp = j >> 5;
+    dsoa_pdl_wait();
+    dsoa_pdl_release();
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    const uint64_t w0 = c.lvl_words[0];
+    const uint64_t t0 = (uint64_t)cta * G;
+    unsigned long long w[kEnumGMax];
+#pragma unroll
+    for (uint32_t g = 0; g < kEnumGMax; ++g) {
+        const uint64_t wi = (t0 + g) * 64 + j;
+        w[g] = (g < G && t0 + g < tiles && wi < w0) ? L0[wi] : 0ull;
+    }
+    if (j == 0) s_ep = dsoa_ld32(epoch) + 1u;
+    uint32_t excl[kEnumGMax];
+#pragma unroll
+    for (uint32_t g = 0; g < kEnumGMax; ++g) {
+        const uint32_t cnt = (uint32_t)__popcll(w[g]);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += v;
+        }
+        excl[g] = incl - cnt;
+        if (lane == 31u && g < G) tsum[g][warp] = incl;
+    }
+    __syncthreads();
+    const uint32_t ep = s_ep;
+    unsigned long long agg = 0ull;
+    for (uint32_t g = 0; g < G; ++g) agg += tsum[g][0] + tsum[g][1];
+    if (j == 0) dsoa_st(&state[cta], lb_word(ep, cta == 0 ? kLbP : kLbA, agg));
+    if (j < 32) {
+        /* warp 0: look back over the preceding CTAs of this type */
+        unsigned long long prefix = 0ull;
+        bool ok = true;
+        if (cta > 0) {
+            int64_t base = (int64_t)cta - 1;
+            for (;;) {
+                const int64_t q = base - (int64_t)lane;
+                unsigned long long sw = 0ull;
+                uint32_t spins = 0;
+                if (q >= 0) {
+                    for (;;) {
+                        sw = dsoa_ld(&state[q]);
+                        if ((uint32_t)(sw >> 40) == (ep & 0xFFFFFFu) && ((sw >> 38) & 3ull)) break;
+                        if (++spins >= DSOA_SPIN_LIMIT) { ok = false; break; }
+                        if (spins > 8) __nanosleep(32u);
+                    }
+                }
+                if (!__all_sync(0xffffffffu, ok)) { ok = false; break; }
+                const bool isP = q >= 0 && ((sw >> 38) & 3ull) == kLbP;
+                const uint32_t pmask = __ballot_sync(0xffffffffu, isP);
+                const uint32_t stop = pmask ? (uint32_t)(__ffs((int)pmask) - 1) : 32u;
+                unsigned long long v = (q >= 0 && lane <= stop) ? (sw & ((1ull << 38) - 1ull)) : 0ull;
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                prefix += v;
+                if (pmask || base - 32 < 0) break;
+                base -= 32;
+            }
+        }
+        if (j == 0) {
+            if (!ok) dsoa_raise(c, DSOA_DEV_SPIN);
+            s_prefix = prefix;
+            if (cta > 0) dsoa_st(&state[cta], lb_word(ep, kLbP, prefix + agg));
+            if (cta == ctas - 1) *r_dev = (uint32_t)(prefix + agg);
+        }
+    }
+    __syncthreads();
+    unsigned long long base = s_prefix;
+#pragma unroll
+    for (uint32_t g = 0; g < kEnumGMax; ++g) {
+        if (g >= G) break;                                   /* uniform */
+        const uint32_t total = tsum[g][0] + tsum[g][1];
+        uint32_t k = excl[g] + (warp ? tsum[g][0] : 0u);
+        const uint64_t bid0 = ((t0 + g) * 64 + j) * 64;
+        for (unsigned long long x = w[g]; x; x &= x - 1ull)
+            list[k++] = (uint32_t)(bid0 + (uint32_t)(__ffsll((long long)x) - 1));
+        __syncthreads();
+        for (uint32_t i = j; i < total; i += 64) {
+            const uint32_t bid = list[i];
+            R[base + i] = bid;
+            Rocc[base + i] = ~c.slot[bid];
+        }
+        base += total;
+        __syncthreads();
+    }
+    /* the last CTA of the type to finish closes the epoch */
+    if (j == 0) {
+        __threadfence();
+        if (atomicAdd(done, 1u) == ctas - 1u) {
+            dsoa_st32(ticket, 0u);
+            dsoa_st32(done, 0u);
+            __threadfence();
+            dsoa_st32(epoch, ep);
+        }
+    }
+}
+
 // Live objects of one type: warp per tile; for every non-empty level-0
 // container the warp reads the 64 slot words coalesced.
 __global__ void k_count(dsoa_ctx c, uint32_t b, uint64_t tiles, unsigned long long* out) {
@@ -594,7 +717,8 @@ static int enumerate_lookback(dsoa_heap* h, const int* types, int n) {
         h->lb_fits = per_sm;
     }
     // tile = blockIdx when every CTA of the launch is resident at once
-    const bool fits = (uint64_t)h->lb_fits * (uint64_t)h->num_sms >= h->tiles * (uint64_t)n;
+    const uint64_t cap = (uint64_t)h->lb_fits * (uint64_t)h->num_sms;
+    const bool fits = cap >= h->tiles * (uint64_t)n;
     EnumBatch eb;
     std::memset(&eb, 0, sizeof(eb));
     eb.n = (uint32_t)n;
@@ -607,8 +731,31 @@ static int enumerate_lookback(dsoa_heap* h, const int* types, int n) {
         eb.state[q] = h->lb_state + (uint64_t)t * h->tiles;
         eb.ctl[q] = h->lb_ctl + 4 * t;
     }
-    const int rc = dsoa_launch_step(h, k_enum_lookback, (unsigned)(h->tiles * (uint64_t)n), 64u, h->ctx, h->tiles,
-                                    eb, fits ? 0u : 1u);
+    int rc;
+    const bool tickets = (h->flags & DSOA_FLAG_ENUM_TICKETS) != 0u;
+    if (!fits && !tickets) {
+        // several tiles per CTA, so that the whole launch is resident (else tickets)
+        static int multi_per_sm = -1;
+        if (multi_per_sm < 0) {
+            int ps = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_enum_lookback_multi, 64, 0);
+            multi_per_sm = ps;
+        }
+        const uint64_t mcap = (uint64_t)multi_per_sm * (uint64_t)h->num_sms;
+        if (mcap > (uint64_t)n) {
+            const uint64_t G = (h->tiles * (uint64_t)n + (mcap - n) - 1) / (mcap - n);
+            if (G <= kEnumGMax) {
+                const uint64_t ctas = (h->tiles + G - 1) / G;
+                rc = dsoa_launch_step(h, k_enum_lookback_multi, (unsigned)(ctas * (uint64_t)n), 64u, h->ctx,
+                                      h->tiles, (uint32_t)G, (uint32_t)ctas, eb);
+                if (rc == DSOA_OK)
+                    for (int q = 0; q < n; ++q) h->enumerated[types[q]] = true;
+                return rc;
+            }
+        }
+    }
+    rc = dsoa_launch_step(h, k_enum_lookback, (unsigned)(h->tiles * (uint64_t)n), 64u, h->ctx, h->tiles,
+                          eb, (fits && !tickets) ? 0u : 1u);
     if (rc == DSOA_OK)
         for (int q = 0; q < n; ++q) h->enumerated[types[q]] = true;
     return rc;
@@ -1095,7 +1242,7 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
 
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags) {
     if (!h || (flags & ~(DSOA_FLAG_NO_COALESCE | DSOA_FLAG_NO_ROTATE | DSOA_FLAG_NO_HINT | DSOA_FLAG_FUSED |
-                         DSOA_FLAG_PDL)))
+                         DSOA_FLAG_PDL | DSOA_FLAG_ENUM_TICKETS)))
         return DSOA_ERR_INVALID_ARG;
     h->flags = flags;
     return DSOA_OK;

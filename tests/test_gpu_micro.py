@@ -320,15 +320,17 @@ def test_atomic_peak_probe_final_words():
     assert m.heap.get_error() == 0
 
 
-@pytest.mark.parametrize("scan", [3, 1])
-def test_heap_beyond_one_wave_of_enumeration_ctas(scan):
-    """A 5 GiB heap has more level-1 tiles (~1200) than look-back CTAs fit on the
-    GPU at once (~900), so tiles are handed out by the ticket counter instead of
-    blockIdx; the rounds still match the oracle.  The two-kernel enumeration runs
-    the same heap."""
+@pytest.mark.parametrize("scan,flags", [(3, 0), (3, 32), (1, 0)])
+def test_heap_beyond_one_wave_of_enumeration_ctas(scan, flags):
+    """A 5 GiB heap has more level-1 tiles (~1200) than single-tile look-back CTAs
+    fit on the GPU at once (~900): the enumeration runs the multi-tile kernel (CTA
+    index orders the look-back), or with DSOA_FLAG_ENUM_TICKETS (32) hands tiles
+    out by the ticket counter; the rounds still match the oracle.  The two-kernel
+    enumeration runs the same heap."""
     n, rounds = 1 << 18, 3
     ref, _, _ = oracle.micro_run(SEED, n, rounds)
     m = make(heap_bytes=5 << 30, n=n, scan_tiles=scan)
+    m.heap.set_flags(flags)
     assert m.heap.info()["num_blocks"] > 4096 * 1100
     for r in range(rounds):
         m.round(r)
