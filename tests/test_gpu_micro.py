@@ -338,3 +338,26 @@ def test_heap_beyond_one_wave_of_enumeration_ctas(scan, flags):
     assert m.heap.get_error() == 0
     assert all(v == 0 for v in m.heap.check().values())
     m.heap.close()
+
+
+def test_doall_at_benchmark_size_every_object():
+    """The do-all sweep's size (2^26 objects, > L2) with the vectorised kernel the
+    benchmark times: after two do-alls every x equals (id * 1.5f) + id with each
+    operation rounded once, checked for all 2^26 objects."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import Micro
+    n = 1 << 26
+    m = Micro(int(n * 16 * 1.3) + (64 << 20), SEED, n)
+    m.new(0)
+    m.heap.parallel_do(m.type, D.M_MICRO_SCALE, m.args())
+    m.heap.parallel_do_enumerated(m.type, D.M_MICRO_SCALE, m.args())
+    x, live = m.gather(n)
+    assert live.all()
+    ids = np.arange(n, dtype=np.float32)
+    want = (ids * np.float32(1.5)).astype(np.float32) + ids
+    assert np.array_equal(x.view(np.uint32), want.astype(np.float32).view(np.uint32))
+    assert m.heap.get_error() == 0
+    m.heap.close()
+    del m
+    torch.cuda.empty_cache()

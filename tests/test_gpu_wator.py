@@ -52,11 +52,21 @@ def test_random_grids_per_step(W, H, steps, seed):
     assert all(v == 0 for v in host["violations"].values()), host
 
 
-def test_full_config_1024_500():
-    """1024 x 1024 torus, 30 % fish / 5 % sharks, 500 steps (the configured workload)."""
+_FULL_REF = {}
+
+
+def full_reference():
+    """The oracle's run of the configured workload (computed once per session)."""
     from paper_1810_11765_gb300 import inputs
     cfg = inputs.WatorConfig()
-    ref, st = oracle.wator_run(cfg.width, cfg.height, cfg.steps, seed=cfg.seed)
+    if "ref" not in _FULL_REF:
+        _FULL_REF["ref"] = oracle.wator_run(cfg.width, cfg.height, cfg.steps, seed=cfg.seed)
+    return cfg, _FULL_REF["ref"]
+
+
+def test_full_config_1024_500():
+    """1024 x 1024 torus, 30 % fish / 5 % sharks, 500 steps (the configured workload)."""
+    cfg, (ref, st) = full_reference()
     heap, w = world(256 << 20)
     s = w.add(cfg.width, cfg.height, cfg.seed)
     for k in range(cfg.steps):
@@ -211,5 +221,34 @@ def test_count_many_matches_count_and_is_capturable():
             assert got == [heap.count(w.fish_type), heap.count(w.shark_type)]
         heap.count_many_async([w.shark_type], out[1:])
         assert int(out[1].item()) == heap.count(w.shark_type)
+        g.close()
+        heap.close()
+
+
+def test_full_config_in_the_benchmarked_launch_configuration():
+    """The configured workload (1024 x 1024, 500 steps) exactly as the benchmark
+    runs it: 512 MiB heap, the autotuned launch shape, each step one captured CUDA
+    graph replayed; final grid and populations equal the oracle's."""
+    import torch
+    from paper_1810_11765_gb300 import autotune, dsoa as D
+    from paper_1810_11765_gb300.apps import WatorWorld
+    cfg, (ref, st) = full_reference()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        launch = autotune.best_wator_launch(cfg.seed)
+        heap = D.Heap(512 << 20)
+        w = WatorWorld(heap)
+        heap.freeze()
+        autotune.apply(heap, launch)
+        slot = w.add(cfg.width, cfg.height, cfg.seed)
+        heap.graph_begin()
+        w.step()
+        g = heap.graph_end()
+        for _ in range(cfg.steps):
+            g.launch()
+        assert np.array_equal(w.read(slot), ref)
+        assert w.counts() == (st[-1]["fish"], st[-1]["sharks"])
+        assert heap.get_error() == 0
+        assert all(v == 0 for v in heap.check().values())
         g.close()
         heap.close()
