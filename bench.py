@@ -391,12 +391,13 @@ def alloc_free_storm(log2n, flush, iters=3):
 
 # Minimum bitmap atomics of the method for the storm's pattern (full warps of one
 # type into an empty heap, then delete-all), per 64-object block:
-#   new:    free-bitmap take, allocated set, active set, 2 warp reservations,
-#           active clear when full                                       = 6
+#   new:    free-bitmap take, allocated set, active set, 1 warp reservation (the
+#           other is folded into the block's initialisation), active clear
+#           when full                                                     = 5
 #   delete: 2 warp-combined releases, active set at the first free,
 #           invalidate, active clear, allocated clear, free set           = 7
 # (upper-level propagation, once per 64 blocks per bitmap, not counted).
-ALG_ATOMICS_PER_OBJECT = {"new": 6 / 64, "delete": 7 / 64}
+ALG_ATOMICS_PER_OBJECT = {"new": 5 / 64, "delete": 7 / 64}
 
 
 def l2_atomic_peak(iters=64, reps=5, words=1 << 22):
