@@ -5,6 +5,7 @@
   python -m paper_1810_11765_gb300.experiments ablation  # NoCoal / NoShift  (Fig. 10c)
   python -m paper_1810_11765_gb300.experiments heapsize  # time vs heap size (Fig. 12b)
   python -m paper_1810_11765_gb300.experiments capacity  # uniform vs per-type block capacity (Sec. 3.2)
+  python -m paper_1810_11765_gb300.experiments problemsize  # time vs problem size (Fig. 10b)
 
 Each prints one JSON line.  Workload: Wa-Tor 1024 x 1024, 30 % fish / 5 % sharks,
 seed 0x5EED0003.  Fragmentation F = unused slots / slots of allocated blocks
@@ -107,6 +108,25 @@ def heap_size(sizes_gib=(0.5, 1, 2, 4, 8, 16), steps=100):
     return {"experiment": f"heap size vs step time, {steps} plain steps (Fig. 12b)", "rows": rows}
 
 
+def problem_size(sides=(256, 512, 768, 1024, 1536, 2048, 2560), steps=100):
+    """Wa-Tor in a fixed 1 GiB heap at growing torus sides (Fig. 10b): time per
+    step and per cell (the paper finds the running time linear in problem size)."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rows = []
+    for side in sides:
+        heap = D.Heap(1 << 30)
+        w = WatorWorld(heap)
+        heap.freeze()
+        w.add(side, side, inputs.WatorConfig().seed)
+        t = _timed_steps(heap, w, steps, flush)
+        ms = sum(t) / steps
+        rows.append(dict(side=side, cells=side * side, ms_per_step=ms, ns_per_cell=ms * 1e6 / (side * side),
+                         **_frag(heap, w), device_errors=heap.get_error()))
+        heap.close()
+        torch.cuda.empty_cache()
+    return {"experiment": f"problem size in a 1 GiB heap, {steps} plain steps (Fig. 10b)", "rows": rows}
+
+
 def capacity(steps=300):
     """Uniform 64-slot blocks vs per-type block capacity N_T (Sec. 3.2): block
     bytes, capacities, step rate, fragmentation and the heap bytes held by
@@ -128,13 +148,13 @@ def capacity(steps=300):
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("which", choices=["frag", "lookups", "ablation", "heapsize", "capacity"])
+    p.add_argument("which", choices=["frag", "lookups", "ablation", "heapsize", "capacity", "problemsize"])
     a = p.parse_args()
     build.build()
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         res = {"frag": frag_over_time, "lookups": frag_vs_lookups, "ablation": ablation,
-               "heapsize": heap_size, "capacity": capacity}[a.which]()
+               "heapsize": heap_size, "capacity": capacity, "problemsize": problem_size}[a.which]()
     print(json.dumps(res))
 
 
