@@ -612,10 +612,11 @@ def app_steps(kind, steps, flush, warmup=3, side=None, heap_bytes=1 << 30):
     return res
 
 
-# Algorithmic operations of one pair term of the n-body force: dx, dy (2 sub),
-# d2 (2 mul, 2 add), sqrt, reciprocal, d^-3 (2 mul), G S m_i m_j (1 mul), k (1 mul),
-# k dx, k dy (2 mul), two conversions to the fixed-point grid, two 64-bit adds.
-NBODY_OPS_PER_PAIR = 19
+# Algorithmic operations of one unordered pair of the n-body force (both bodies'
+# terms): dx, dy (2 sub), d2 (2 mul, 2 add), sqrt, reciprocal, d^-3 (2 mul), the two
+# coefficients (G S m_i) m_j d^-3 and (G S m_j) m_i d^-3 (4 mul), k dx and k dy for
+# each body (4 mul), four conversions to the fixed-point grid, four 64-bit adds.
+NBODY_OPS_PER_UNORDERED_PAIR = 26
 
 
 def fp32_lane_peak(clock_mhz):
@@ -627,8 +628,9 @@ def fp32_lane_peak(clock_mhz):
 
 def nbody_leg(flush, steps=5, collide_steps=10):
     """n-body (65,536 bodies, the listing's size): FORCE by the pairwise tiled
-    kernel and by the per-thread device_do walk, steps/s plain vs graph;
-    particle collisions on the same bodies (six do-alls per step)."""
+    kernel over unordered pairs (the default) and over ordered pairs, and by the
+    per-thread device_do walk; steps/s plain vs graph; particle collisions on the
+    same bodies (six do-alls per step)."""
     import torch
     from paper_1810_11765_gb300 import dsoa as D, inputs
     from paper_1810_11765_gb300.apps import NBodyWorld
@@ -636,9 +638,9 @@ def nbody_leg(flush, steps=5, collide_steps=10):
     n = cfg.n
     out = {"workload": f"n-body {n} bodies in [-1,1)^2, integer masses 1..{cfg.mass_max}, G=2^-30, dt=1/4",
            "pairs_per_force": n * (n - 1)}
-    for tiled in (True, False):
+    for key, tiled, all_pairs in (("tiled", True, False), ("tiled_ordered", True, True), ("device_do", False, False)):
         heap = D.Heap(256 << 20)
-        w = NBodyWorld(heap, cfg, tiled=tiled)
+        w = NBodyWorld(heap, cfg, tiled=tiled, all_pairs=all_pairs)
         heap.freeze()
         w.create(n)
         w.step()
@@ -653,10 +655,9 @@ def nbody_leg(flush, steps=5, collide_steps=10):
         b.synchronize()
         force_ms = a.elapsed_time(b) / k
         w.step()          # apply (and clear) the forces accumulated above
-        key = "tiled" if tiled else "device_do"
         out[f"force_ms_{key}"] = force_ms
         out[f"pair_terms_per_s_{key}"] = n * (n - 1) / (force_ms / 1e3)
-        if tiled:
+        if key == "tiled":
             for mode in ("plain", "graph"):
                 g = None
                 if mode == "graph":
@@ -893,13 +894,13 @@ def dsoa_arm(args):
         nb = nbody_leg(flush)
         clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
         peak_ops = fp32_lane_peak(clk_mhz)
-        ach = nb["pair_terms_per_s_tiled"] * NBODY_OPS_PER_PAIR
-        nb["roofline"] = {"kernel": "k_force_tiled", "bound": "alu", "achieved": ach / 1e12,
+        ach = nb["pair_terms_per_s_tiled"] / 2 * NBODY_OPS_PER_UNORDERED_PAIR
+        nb["roofline"] = {"kernel": "k_force_sym", "bound": "alu", "achieved": ach / 1e12,
                           "peak": peak_ops / 1e12, "unit": "Tops/s", "frac": ach / peak_ops,
-                          "traffic": ncu_traffic("k_force_tiled", 1 << 16),
+                          "traffic": ncu_traffic("k_force_sym", 1 << 16),
                           "traffic_unit": "DRAM bytes per launch (ncu, scaled per body from a 16,384-body "
                                           "capture: the bodies stay in L2, DRAM traffic grows with n)",
-                          "ops_per_pair": NBODY_OPS_PER_PAIR,
+                          "ops_per_unordered_pair": NBODY_OPS_PER_UNORDERED_PAIR,
                           "peak_kind": f"derived: SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (median SM clock "
                                        "of the headline run)"}
         out["nbody_65536"] = nb

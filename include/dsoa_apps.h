@@ -171,9 +171,14 @@ typedef struct {
 #define DSOA_M_NBODY_READ 507         /* out[5 id + 0..4] = px py vx vy m; alive_out[id] = 1;
                                          force_out[2 id + 0..1] = fx fy when non-null         */
 #define DSOA_M_NBODY_FORCE_TILED 508  /* FORCE's result (bit for bit) from a pairwise kernel
-                                         over the enumerated snapshot: CTAs take (256 bodies)
-                                         x (a chunk of bodies) tiles staged in shared memory
-                                         and add their integer partial sums atomically      */
+                                         over the enumerated snapshot: CTAs take tiles of
+                                         bodies staged in shared memory and add their integer
+                                         partial sums atomically.  By default each unordered
+                                         pair is evaluated once and gives both bodies their
+                                         terms (Newton's third law, exact in fixed point);
+                                         with DSOA_NBODY_ALL_PAIRS every ordered pair is
+                                         evaluated for its first body only.  Needs
+                                         eps2 >= 2^-80 (else DSOA_ERR_INVALID_ARG)           */
 #define DSOA_M_COLL_FIND_TILED 509    /* FIND's result by the pairwise kernel, in two halves:
                                          with DSOA_NBODY_KEYED_FIND, MOVE resets target,
                                          incoming, merged and sets fx to all ones; this
@@ -181,6 +186,7 @@ typedef struct {
                                          turns it into the target and clears fx             */
 #define DSOA_NBODY_NONE 0xFFFFFFFFu   /* no target / no incoming proposal                    */
 #define DSOA_NBODY_KEYED_FIND 1u      /* flags: the step uses FIND_TILED                     */
+#define DSOA_NBODY_ALL_PAIRS 2u       /* flags: FORCE_TILED over ordered pairs                */
 typedef struct {
     uint64_t* handle_of;  /* [n_ids] id -> handle; needed by collisions (CLAIM, MERGE read
                              it, the ctor writes it, DELETE clears it); nullable for n-body */
@@ -198,7 +204,8 @@ typedef struct {
     float fscale;         /* fixed-point scale S (power of two)                           */
     float vscale;         /* initial velocities in [-vscale/2, vscale/2)                  */
     int32_t body_type;
-    uint32_t flags;       /* DSOA_NBODY_KEYED_FIND (MOVE and CLAIM for FIND_TILED)       */
+    uint32_t flags;       /* DSOA_NBODY_KEYED_FIND (MOVE and CLAIM for FIND_TILED),
+                             DSOA_NBODY_ALL_PAIRS (FORCE_TILED)                           */
 } dsoa_nbody_args;
 
 #ifdef __cplusplus

@@ -342,15 +342,18 @@ class NBodyWorld:
     """n-body (``collide=False``: FORCE, MOVE) or particle collisions (FORCE, MOVE,
     FIND, CLAIM, MERGE, DELETE) over one Body type.  ``tiled`` selects the pairwise
     shared-memory FORCE kernel instead of the per-thread device_do walk (same
-    integers)."""
+    integers); ``all_pairs`` makes that kernel evaluate every ordered pair instead
+    of every unordered pair once (same integers again)."""
 
     BODY_FIELDS = [4, 4, 4, 4, 4, 4, 8, 8, 4, 4, 4]   # id px py vx vy m fx fy target incoming merged
 
-    def __init__(self, heap: D.Heap, cfg, collide: bool = False, tiled: bool = True, body_type=None):
+    def __init__(self, heap: D.Heap, cfg, collide: bool = False, tiled: bool = True, body_type=None,
+                 all_pairs: bool = False):
         self.heap = heap
         self.cfg = cfg
         self.collide = collide
         self.tiled = tiled
+        self.pair_flags = D.NBODY_ALL_PAIRS if all_pairs else 0
         self.force_method = D.M_NBODY_FORCE_TILED if tiled else D.M_NBODY_FORCE
         self.type = heap.register_type(self.BODY_FIELDS) if body_type is None else body_type
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -363,7 +366,7 @@ class NBodyWorld:
         a = D.NBodyArgs(handle_of=D._addr(self.handle_of), seed=c.seed, n_ids=self.n,
                         mass_max=c.mass_max, G=c.G, dt=c.dt, eps2=c.eps2, rc2=c.rc2,
                         fscale=c.fscale, vscale=c.vscale, body_type=self.type,
-                        flags=D.NBODY_KEYED_FIND if (self.collide and self.tiled) else 0)
+                        flags=self.pair_flags | (D.NBODY_KEYED_FIND if (self.collide and self.tiled) else 0))
         for k, v in kw.items():
             setattr(a, k, v)
         return a
@@ -390,7 +393,7 @@ class NBodyWorld:
 
     def force(self):
         """FORCE alone (adds the pair sums to the force fields, which MOVE clears)."""
-        self.heap.parallel_do(self.type, self.force_method, self.args(flags=0))
+        self.heap.parallel_do(self.type, self.force_method, self.args(flags=self.pair_flags))
 
     def read(self, forces: bool = False):
         """(state float32[n, 5] by id: px py vx vy m, alive uint8[n]) and, with

@@ -341,6 +341,40 @@ struct FindOp {
     }
 };
 
+// Dense mode (r <= kDenseMaxR): writes pre[] (the exclusive prefix of the
+// occupied-slot counts of the listed blocks, and the total at pre[r]) and
+// returns the number of bodies; otherwise returns the number of listed slots.
+// Called by every thread of the CTA.
+__device__ uint32_t index_space(bool dense, uint32_t r, const unsigned long long* __restrict__ occ,
+                                uint32_t* pre, uint32_t* wsum) {
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    if (!dense) return r * 64u;
+    const uint32_t per = (r + 255u) / 256u;
+    const uint32_t q0 = min(r, tid * per), q1 = min(r, q0 + per);
+    uint32_t own = 0;
+    for (uint32_t q = q0; q < q1; ++q) own += (uint32_t)__popcll(__ldg(&occ[q]));
+    uint32_t x = own;                                       // inclusive scan over the warp
+#pragma unroll
+    for (uint32_t o = 1; o < 32u; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31u) wsum[warp] = x;
+    __syncthreads();
+    uint32_t run = x - own, total = 0;
+    for (uint32_t w = 0; w < 8u; ++w) {
+        if (w < warp) run += wsum[w];
+        total += wsum[w];
+    }
+    for (uint32_t q = q0; q < q1; ++q) {
+        pre[q] = run;
+        run += (uint32_t)__popcll(__ldg(&occ[q]));
+    }
+    if (tid == 0) pre[r] = total;
+    __syncthreads();
+    return total;
+}
+
 template <class Op>
 __global__ void __launch_bounds__(256) k_pairs_tiled(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                                      const unsigned long long* __restrict__ occ,
@@ -349,35 +383,9 @@ __global__ void __launch_bounds__(256) k_pairs_tiled(dsoa_ctx c, uint32_t t, con
     __shared__ uint32_t pre[kDenseMaxR + 1];
     __shared__ uint32_t wsum[8];
     const uint32_t r = __ldg(r_dev);
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t tid = threadIdx.x;
     const bool dense = r <= kDenseMaxR;
-    uint32_t nb = r * 64u;                                  // indices: bodies (dense) or slots
-    if (dense) {
-        const uint32_t per = (r + 255u) / 256u;
-        const uint32_t q0 = min(r, tid * per), q1 = min(r, q0 + per);
-        uint32_t own = 0;
-        for (uint32_t q = q0; q < q1; ++q) own += (uint32_t)__popcll(__ldg(&occ[q]));
-        uint32_t x = own;                                   // inclusive scan over the warp
-#pragma unroll
-        for (uint32_t o = 1; o < 32u; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31u) wsum[warp] = x;
-        __syncthreads();
-        uint32_t run = x - own, total = 0;
-        for (uint32_t w = 0; w < 8u; ++w) {
-            if (w < warp) run += wsum[w];
-            total += wsum[w];
-        }
-        for (uint32_t q = q0; q < q1; ++q) {
-            pre[q] = run;
-            run += (uint32_t)__popcll(__ldg(&occ[q]));
-        }
-        if (tid == 0) pre[r] = total;
-        __syncthreads();
-        nb = total;
-    }
+    const uint32_t nb = index_space(dense, r, occ, pre, wsum);   // indices: bodies (dense) or slots
     const uint64_t n_i = (nb + kTile - 1) / kTile, n_j = (nb + kChunkBodies - 1) / kChunkBodies;
     const uint64_t items = n_i * n_j;
     const uint64_t wb = items * blockIdx.x / gridDim.x, we = items * (blockIdx.x + 1) / gridDim.x;
@@ -420,6 +428,164 @@ __global__ void __launch_bounds__(256) k_pairs_tiled(dsoa_ctx c, uint32_t t, con
         }
     }
     if (mine) op.end(c, t, bi, si);
+}
+
+// ---------------------------------------------------------------------------
+// FORCE over unordered pairs (Newton's third law in the fixed-point sums).  The
+// terms of j on i and of i on j share dx, dy, d2 and the inverse cube: with
+// k_ij = ((G S m_i) m_j) / d^3 and k_ji = ((G S m_j) m_i) / d^3, i gets
+// fix(k_ij dx) and j gets fix(k_ji (-dx)) = -fix(k_ji dx), because rounding to
+// nearest commutes with negation (x_i - x_j is exactly -(x_j - x_i)).  So one
+// evaluation per unordered pair gives the very integers of the all-pairs sum.
+//
+// Work: square tiles of kTile indices on both sides; the items are the tile
+// pairs (I, J) with J >= I, row-major, split evenly over the CTAs.  Warp w holds
+// i group 8 I + w (one body per lane) and pairs it with the 8 groups of 32 j
+// bodies of tile J in shared memory.  Within a group the pairs go round a
+// rotation: at step s lane l pairs its i with j = (l + s) mod 32, adds the i
+// term to its register sum and subtracts the j term from a running j sum that
+// moves one lane down after the step, so after the 32 steps every lane holds a
+// whole warp's sum for one j.  Warps take the groups in rotated order, their j
+// sums meet in shared memory (64-bit shared atomics) and leave with one global
+// atomic per body and item; the i sums leave when the CTA moves to the next
+// row.  In a diagonal tile (I = J) warp w pairs its group only with the groups
+// after it and, within its own group, takes the 31 other bodies for its i side
+// alone.  Every j group is staged twice in a row, so step s reads entry
+// lane + s without wrapping.  Indices past the last body (and, beyond
+// kDenseMaxR listed blocks, empty slots) stage as mass 0, whose terms are
+// exactly 0 either way (the inverse cube is finite for eps2 >= 2^-80).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSymGroups = kTile / 32u;
+
+__device__ __forceinline__ float4 stage_body(const dsoa_ctx& c, uint32_t t, bool dense, const uint32_t* pre,
+                                             uint32_t r, const unsigned long long* __restrict__ occ,
+                                             const uint32_t* __restrict__ R, uint32_t nb, uint64_t d, float gs,
+                                             bool& ok, uint64_t& b, uint32_t& slot) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t q = 0;
+    slot = 0;
+    ok = d < nb && locate(dense, pre, r, occ, (uint32_t)d, q, slot);
+    if (ok) {
+        b = __ldg(&R[q]);
+        v.x = fld<float>(c, t, b, slot, kPx);
+        v.y = fld<float>(c, t, b, slot, kPy);
+        v.z = fld<float>(c, t, b, slot, kM);
+        v.w = __fmul_rn(gs, v.z);
+    }
+    return v;
+}
+
+// items in the rows before row I of the triangle (I + 1 .. nt items per row)
+__device__ __forceinline__ uint64_t tri_start(uint64_t I, uint64_t nt) { return I * nt - I * (I - 1) / 2; }
+
+__global__ void __launch_bounds__(256) k_force_sym(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+                                                   const unsigned long long* __restrict__ occ,
+                                                   const uint32_t* __restrict__ r_dev, dsoa_nbody_args a) {
+    __shared__ float4 sj[2 * kTile];                 // group g at [64 g, 64 g + 64): its 32 bodies twice
+    __shared__ unsigned long long sacc[2][kTile];    // j sums of the item
+    __shared__ uint32_t pre[kDenseMaxR + 1];
+    __shared__ uint32_t wsum[8];
+    const uint32_t r = __ldg(r_dev);
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const bool dense = r <= kDenseMaxR;
+    const uint32_t nb = index_space(dense, r, occ, pre, wsum);
+    const float gs = __fmul_rn(a.G, a.fscale), eps2 = a.eps2;
+    const uint64_t nt = (nb + kTile - 1) / kTile, items = nt * (nt + 1) / 2;
+    const uint64_t wb = items * blockIdx.x / gridDim.x, we = items * (blockIdx.x + 1) / gridDim.x;
+    sacc[0][tid] = 0ull;
+    sacc[1][tid] = 0ull;
+    uint64_t I = 0, J = 0;
+    if (wb < we) {                                   // the row holding item wb
+        uint64_t lo = 0, hi = nt;                    // tri_start(lo) <= wb < tri_start(hi)
+        while (hi - lo > 1u) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (tri_start(mid, nt) <= wb) lo = mid; else hi = mid;
+        }
+        I = lo;
+        J = I + (wb - tri_start(I, nt));
+    }
+    uint64_t cur = ~0ull, bi = 0;
+    uint32_t si = 0;
+    bool imine = false;
+    float px = 0.f, py = 0.f, m = 0.f, gsm = 0.f;
+    unsigned long long fx = 0ull, fy = 0ull;
+    const uint32_t src = (lane + 1u) & 31u;
+    for (uint64_t w = wb; w < we; ++w) {
+        if (I != cur) {
+            if (imine) {
+                if (fx) atomicAdd(&fld<unsigned long long>(c, t, bi, si, kFx), fx);
+                if (fy) atomicAdd(&fld<unsigned long long>(c, t, bi, si, kFy), fy);
+            }
+            cur = I;
+            const float4 v = stage_body(c, t, dense, pre, r, occ, R, nb, I * kTile + tid, gs, imine, bi, si);
+            px = v.x;
+            py = v.y;
+            m = v.z;
+            gsm = v.w;
+            fx = fy = 0ull;
+        }
+        bool jmine;
+        uint64_t bj = 0;
+        uint32_t sl;
+        const float4 v = stage_body(c, t, dense, pre, r, occ, R, nb, J * kTile + tid, gs, jmine, bj, sl);
+        __syncthreads();                             // readers of the previous tile are done
+        sj[2u * tid - lane] = v;                     // = 64 warp + lane
+        sj[2u * tid - lane + 32u] = v;
+        __syncthreads();
+        const bool diag = I == J;
+#pragma unroll 1
+        for (uint32_t k = 0; k < kSymGroups; ++k) {
+            const uint32_t g = (warp + k) & (kSymGroups - 1u);
+            if (diag && g < warp) continue;
+            const float4* col = sj + 64u * g + lane;
+            if (diag && g == warp) {
+#pragma unroll
+                for (uint32_t s = 1; s < 32u; ++s) {
+                    const float4 q = col[s];
+                    pair_term(px, py, gsm, q.x, q.y, q.z, eps2, fx, fy);
+                }
+                continue;
+            }
+            unsigned long long gx = 0ull, gy = 0ull;
+#pragma unroll
+            for (uint32_t s = 0; s < 32u; ++s) {
+                const float4 q = col[s];
+                const float dx = __fsub_rn(q.x, px), dy = __fsub_rn(q.y, py);
+                const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), eps2);
+                const float inv = __frcp_rn(__fsqrt_rn(d2));
+                const float inv3 = __fmul_rn(__fmul_rn(inv, inv), inv);
+                const float kij = __fmul_rn(__fmul_rn(gsm, q.z), inv3);
+                const float kji = __fmul_rn(__fmul_rn(q.w, m), inv3);
+                fx += fix(__fmul_rn(kij, dx));
+                fy += fix(__fmul_rn(kij, dy));
+                gx -= fix(__fmul_rn(kji, dx));
+                gy -= fix(__fmul_rn(kji, dy));
+                if (s < 31u) {
+                    gx = __shfl_sync(0xFFFFFFFFu, gx, src);
+                    gy = __shfl_sync(0xFFFFFFFFu, gy, src);
+                }
+            }
+            const uint32_t j = 32u * g + ((lane + 31u) & 31u);   // the sum lane l holds after step 31
+            if (gx) atomicAdd(&sacc[0][j], gx);
+            if (gy) atomicAdd(&sacc[1][j], gy);
+        }
+        __syncthreads();                             // every j sum of the item is in
+        const unsigned long long jx = sacc[0][tid], jy = sacc[1][tid];
+        sacc[0][tid] = 0ull;
+        sacc[1][tid] = 0ull;
+        if (jmine) {
+            if (jx) atomicAdd(&fld<unsigned long long>(c, t, bj, sl, kFx), jx);
+            if (jy) atomicAdd(&fld<unsigned long long>(c, t, bj, sl, kFy), jy);
+        }
+        if (++J == nt) {
+            ++I;
+            J = I;
+        }
+    }
+    if (imine) {
+        if (fx) atomicAdd(&fld<unsigned long long>(c, t, bi, si, kFx), fx);
+        if (fy) atomicAdd(&fld<unsigned long long>(c, t, bi, si, kFy), fy);
+    }
 }
 
 // Body's field sizes in bytes (id, px, py, vx, vy, m, fx, fy, target, incoming, merged)
@@ -469,9 +635,13 @@ int dsoa_nbody_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
         case DSOA_M_NBODY_FORCE_TILED:
         case DSOA_M_COLL_FIND_TILED: {
             if (h->ctx.M * 64ull >= 0xFFFFFFFFull) return DSOA_ERR_INVALID_ARG;  // 32-bit slot indices
+            // mass-0 placeholders add exactly 0 only while the inverse cube is finite
+            if (method == DSOA_M_NBODY_FORCE_TILED && !(args.eps2 >= 0x1p-80f)) return DSOA_ERR_INVALID_ARG;
             rc = dsoa_prepare_doall(h, type);
             if (rc) return rc;
-            auto* k = method == DSOA_M_NBODY_FORCE_TILED ? &k_pairs_tiled<ForceOp> : &k_pairs_tiled<FindOp>;
+            auto* k = method == DSOA_M_COLL_FIND_TILED ? &k_pairs_tiled<FindOp>
+                      : (args.flags & DSOA_NBODY_ALL_PAIRS) ? &k_pairs_tiled<ForceOp>
+                                                            : &k_force_sym;
             const unsigned grid = (unsigned)(dsoa_resident_ctas(reinterpret_cast<const void*>(k), 256) * h->num_sms);
             k<<<grid ? grid : 1u, 256, 0, h->stream>>>(dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type],
                                                      h->r_dev[type], args);

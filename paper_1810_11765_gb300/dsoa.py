@@ -44,6 +44,7 @@ C_NBODY, M_NBODY_FORCE, M_NBODY_MOVE = 500, 501, 502
 M_COLL_FIND, M_COLL_CLAIM, M_COLL_MERGE, M_COLL_DELETE = 503, 504, 505, 506
 M_NBODY_READ, M_NBODY_FORCE_TILED, M_COLL_FIND_TILED = 507, 508, 509
 NBODY_KEYED_FIND = 1
+NBODY_ALL_PAIRS = 2
 
 INST_IDLE, INST_RUN, INST_KILL = 0, 1, 2
 

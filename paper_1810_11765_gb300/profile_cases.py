@@ -104,13 +104,14 @@ def case_atomic(iters: int):
     m.heap.close()
 
 
-def case_nbody(n: int, walk: bool, iters: int):
+def case_nbody(n: int, walk: bool, iters: int, all_pairs: bool = False):
     """FORCE over n bodies of the configured n-body workload: the pairwise tiled
-    kernel, or (walk) the per-thread device_do walk."""
+    kernel (over unordered pairs, or ordered ones with ``all_pairs``), or (walk)
+    the per-thread device_do walk."""
     from . import inputs
     cfg = inputs.NBodyConfig()
     heap = D.Heap(max(64 << 20, n * 256))
-    w = NBodyWorld(heap, cfg, tiled=not walk)
+    w = NBodyWorld(heap, cfg, tiled=not walk, all_pairs=all_pairs)
     heap.freeze()
     w.create(n)
     for _ in range(iters):
@@ -120,7 +121,8 @@ def case_nbody(n: int, walk: bool, iters: int):
         b.record()
         b.synchronize()
         ms = a.elapsed_time(b)
-        print(f"nbody[{'walk' if walk else 'tiled'}] n={n}: FORCE {ms:.4f} ms, "
+        kind = "walk" if walk else ("tiled ordered" if all_pairs else "tiled")
+        print(f"nbody[{kind}] n={n}: FORCE {ms:.4f} ms, "
               f"{n * (n - 1) / ms / 1e6:.2f} G pair terms/s")
     print("err", heap.get_error())
     heap.close()
@@ -131,6 +133,7 @@ def main():
     p.add_argument("case", choices=["doall", "wator", "alloc", "atomic", "nbody"])
     p.add_argument("--n", type=int, default=16384)
     p.add_argument("--walk", action="store_true")
+    p.add_argument("--all-pairs", action="store_true")
     p.add_argument("--log2n", type=int, default=24)
     p.add_argument("--holes", action="store_true")
     p.add_argument("--iters", type=int, default=3)
@@ -146,7 +149,7 @@ def main():
     elif a.case == "atomic":
         case_atomic(a.iters)
     elif a.case == "nbody":
-        case_nbody(a.n, a.walk, a.iters)
+        case_nbody(a.n, a.walk, a.iters, a.all_pairs)
     else:
         case_alloc(a.log2n)
 

@@ -103,28 +103,90 @@ def test_merge_chain_hand_case():
 
 
 def test_forces_sum_to_zero_and_match_sampled_bodies_at_full_size():
-    """65,536 bodies (the configured size): one FORCE by the tiled kernel and by the
-    device_do walk; Newton's third law holds exactly over all bodies, and sampled
-    bodies (first, last, a ragged spread) match the oracle one by one."""
+    """65,536 bodies (the configured size): one FORCE by the unordered-pair and the
+    ordered-pair tiled kernels and by the device_do walk; Newton's third law holds
+    exactly over all bodies, and sampled bodies (first, last, a ragged spread)
+    match the oracle one by one."""
     from paper_1810_11765_gb300 import inputs
     c = inputs.NBodyConfig()
     ids = np.unique(np.concatenate([[0, 1, 63, 64, c.n - 1], np.random.default_rng(5).integers(0, c.n, 27)]))
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import NBodyWorld
     got = {}
-    for tiled in (True, False):
-        heap, w = world(c, False, tiled, 512 << 20)
+    for scheme in ("unordered", "ordered", "walk"):
+        heap = D.Heap(512 << 20)
+        w = NBodyWorld(heap, c, tiled=scheme != "walk", all_pairs=scheme == "ordered")
+        heap.freeze()
         w.create(c.n)
         st0, _ = w.read()
         w.force()
         _, _, F = w.read(forces=True)
         assert np.all(F.sum(0) == 0)
-        got[tiled] = F
+        got[scheme] = F
         assert heap.get_error() == 0
         heap.close()
-    assert np.array_equal(got[True], got[False])
+    assert np.array_equal(got["unordered"], got["walk"])
+    assert np.array_equal(got["ordered"], got["walk"])
     ref0, _, _, _ = oracle_run(c, c.n, 0, False)
     assert np.array_equal(st0, ref0)
     want = oracle.nbody_force_on(ref0, ids, G=c.G, eps2=c.eps2, fscale=c.fscale)
-    assert np.array_equal(got[True][ids], want)
+    assert np.array_equal(got["unordered"][ids], want)
+
+
+def _general_init(n, seed):
+    """Positions in [-1, 1)^2, masses in [0.5, 20) with fractional parts, so the
+    two terms of a pair have different coefficients ((G S m_i) m_j vs (G S m_j) m_i)."""
+    rng = np.random.default_rng(seed)
+    init = np.zeros((n, 5), np.float32)
+    init[:, 0:2] = rng.uniform(-1.0, 1.0, (n, 2))
+    init[:, 2:4] = rng.uniform(-2.0 ** -9, 2.0 ** -9, (n, 2))
+    init[:, 4] = rng.uniform(0.5, 20.0, n)
+    return init
+
+
+def _forces(c, init, tiled, all_pairs=False, four_slot_blocks=False):
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import NBodyWorld
+    heap = D.Heap(64 << 20)
+    if four_slot_blocks:
+        heap.register_type([4])                   # 256-byte blocks: four Bodies per block
+        heap.set_capacity_mode(D.CAPACITY_PER_TYPE)
+    w = NBodyWorld(heap, c, tiled=tiled, all_pairs=all_pairs)
+    heap.freeze()
+    if four_slot_blocks:
+        assert heap.capacity(w.type) == 4
+    w.create(init.shape[0], init)
+    w.force()
+    st, alive, F = w.read(forces=True)
+    assert np.array_equal(st, init) and alive.all()
+    assert heap.get_error() == 0
+    heap.close()
+    return F
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 255, 257, 700, 2100])
+def test_force_pair_schemes_with_unequal_pair_coefficients(n):
+    """G not a power of two and fractional masses: the unordered-pair kernel (one
+    evaluation per pair, both bodies' terms), the ordered-pair kernel and the
+    device_do walk give the oracle's integers for every body, ragged last tiles
+    and single-group cases included."""
+    c = cfg(G=float(np.float32(3.1e-7)), fscale=2.0 ** 36)
+    init = _general_init(n, 1000 + n)
+    want = oracle.nbody_force_on(init, np.arange(n), G=c.G, eps2=c.eps2, fscale=c.fscale)
+    for tiled, all_pairs in ((True, False), (True, True), (False, False)):
+        assert np.array_equal(_forces(c, init, tiled, all_pairs), want), (tiled, all_pairs)
+
+
+@pytest.mark.parametrize("n", [12000, 17000])
+def test_force_over_four_slot_blocks(n):
+    """Four Bodies per block (per-type capacity behind a 4-byte type): 3000 listed
+    blocks are indexed densely, 4250 by slot (60 of every 64 indices are empty
+    slots staged as mass 0).  Both pair schemes give the oracle's integers."""
+    c = cfg(G=float(np.float32(3.1e-7)), fscale=2.0 ** 36)
+    init = _general_init(n, 77 + n)
+    want = oracle.nbody_force_on(init, np.arange(n), G=c.G, eps2=c.eps2, fscale=c.fscale)
+    for all_pairs in (False, True):
+        assert np.array_equal(_forces(c, init, True, all_pairs, four_slot_blocks=True), want), all_pairs
 
 
 def test_collision_graph_replay_matches_plain():
@@ -168,4 +230,6 @@ def test_rejects_bad_arguments():
         heap.parallel_do(w.type, D.M_NBODY_MOVE, w.args(eps2=0.0))        # no softening
     with pytest.raises(D.DsoaError):
         heap.parallel_do(w.type, D.M_COLL_CLAIM, w.args(handle_of=None))  # claims need the id map
+    with pytest.raises(D.DsoaError):
+        heap.parallel_do(w.type, D.M_NBODY_FORCE_TILED, w.args(eps2=2.0 ** -81))   # inverse cube may overflow
     heap.close()
