@@ -68,6 +68,23 @@ int dsoa_heap_create_from(void* dev_ptr, size_t bytes, void* stream, dsoa_heap**
  * layout froze. */
 int dsoa_register_type(dsoa_heap* h, const uint32_t* field_bytes, int nfields, int* type_out);
 
+/* Register a subtype of `base` (Sec. 1 "Subclassing/Inheritance", Sec. 3.1):
+ * its fields are base's fields followed by `n_extra` new ones of
+ * `extra_field_bytes[i]` bytes (n_extra may be 0), so the data segment of its
+ * blocks begins with the inherited SOA columns at the same field indices and a
+ * method written for base reads and writes them unchanged (the handle carries
+ * the runtime type, which fixes the column offsets and, in the per-type
+ * capacity mode, the block capacity: Sec. 3.3).  The subtype has its own
+ * blocks and its own allocated / active bitmaps: blocks of a subtype are not in
+ * the bitmaps of its base (Sec. 3.4).  dsoa_parallel_do on base also visits
+ * the objects of every subtype (Sec. 2.1).  Errors: DSOA_ERR_INVALID_ARG (unknown base, more than
+ * DSOA_MAX_FIELDS fields in all, a bad field size), DSOA_ERR_FROZEN,
+ * DSOA_ERR_TOO_MANY_TYPES. */
+int dsoa_register_subtype(dsoa_heap* h, int base, const uint32_t* extra_field_bytes, int n_extra, int* type_out);
+
+/* The type `type` extends (-1 for a type registered by dsoa_register_type). */
+int dsoa_type_base(dsoa_heap* h, int type, int* base_out);
+
 /* Freeze the layout.  Uniform capacity (the default): every type has 64 slots
  * per block and block bytes = the largest registered type's 64-slot data
  * segment.  Per-type capacity (dsoa_set_capacity_mode): see below.  M = blocks
@@ -112,7 +129,9 @@ int dsoa_parallel_new(dsoa_heap* h, int type, uint64_t n, int ctor_id,
  * block bitmap (hierarchical bitmap scan + prefix sum, Sec. 4.1.5, Fig. 7),
  * then run built-in method `method_id` on every object in the snapshot.
  * Objects created by the method are not visited; the method may delete `this`
- * and objects of other types. */
+ * and objects of other types.  A type with subtypes (dsoa_register_subtype)
+ * covers their objects too: one enumeration launch snapshots the type and all
+ * its subtypes, then the method runs in one launch per type (Sec. 2.1). */
 int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args_host,
                      size_t args_bytes);
 

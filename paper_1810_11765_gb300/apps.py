@@ -67,13 +67,20 @@ class InstanceTable:
 
 # ----------------------------------------------------------------------------- microbench
 class Micro:
-    """One type {int32 id, float x, int64 tag}; rounds of new / scale / delete."""
+    """One type {int32 id, float x, int64 tag}; rounds of new / scale / delete.
+
+    With ``sub_fields`` a subtype extending it by those fields is registered too,
+    and every round creates its last ``sub_share`` of the objects (the highest
+    ids) as subtype objects; the do-alls run on the base type and so cover both."""
 
     FIELDS = [4, 4, 8]
 
-    def __init__(self, heap_bytes: int, seed: int, n_per_round: int, stream=None, heap=None):
+    def __init__(self, heap_bytes: int, seed: int, n_per_round: int, stream=None, heap=None,
+                 sub_fields=None, sub_share: float = 0.5):
         self.heap = heap if heap is not None else D.Heap(heap_bytes, stream)
         self.type = self.heap.register_type(self.FIELDS)
+        self.sub_type = None if sub_fields is None else self.heap.register_subtype(self.type, sub_fields)
+        self.sub_share = sub_share
         self.heap.freeze()
         self.seed, self.n = seed, n_per_round
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -87,7 +94,11 @@ class Micro:
 
     def new(self, rnd: int, n: int | None = None):
         n = self.n if n is None else n
-        self.heap.parallel_new(self.type, n, D.C_MICRO, self.args(id_base=rnd * self.n))
+        n_sub = 0 if self.sub_type is None else int(n * self.sub_share)
+        if n - n_sub:
+            self.heap.parallel_new(self.type, n - n_sub, D.C_MICRO, self.args(id_base=rnd * self.n))
+        if n_sub:
+            self.heap.parallel_new(self.sub_type, n_sub, D.C_MICRO, self.args(id_base=rnd * self.n + n - n_sub))
 
     def scale(self, method: int = D.M_MICRO_SCALE):
         self.heap.parallel_do(self.type, method, self.args())

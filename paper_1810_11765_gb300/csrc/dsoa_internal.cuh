@@ -19,6 +19,7 @@ struct dsoa_type_info {
     uint32_t col_off[DSOA_MAX_FIELDS];
     uint32_t data_bytes;  // 64-slot data segment of this type
     uint32_t capacity;    // slots per block (64, or N_T in the per-type capacity mode)
+    int base;             // the type this one extends (its fields first), or -1
 };
 
 struct dsoa_heap {

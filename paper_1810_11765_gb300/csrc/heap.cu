@@ -836,8 +836,29 @@ int dsoa_register_type(dsoa_heap* h, const uint32_t* field_bytes, int nfields, i
     }
     ti.data_bytes = off;
     ti.capacity = DSOA_SLOTS;
+    ti.base = -1;
     h->types[h->ntypes] = ti;
     *type_out = h->ntypes++;
+    return DSOA_OK;
+}
+
+int dsoa_register_subtype(dsoa_heap* h, int base, const uint32_t* extra_field_bytes, int n_extra, int* type_out) {
+    if (!h || !type_out || base < 0 || base >= h->ntypes || n_extra < 0 || (n_extra > 0 && !extra_field_bytes))
+        return DSOA_ERR_INVALID_ARG;
+    const dsoa_type_info& b = h->types[base];
+    if (b.nfields + n_extra > DSOA_MAX_FIELDS) return DSOA_ERR_INVALID_ARG;
+    uint32_t fb[DSOA_MAX_FIELDS];
+    for (int f = 0; f < b.nfields; ++f) fb[f] = b.field_bytes[f];       // inherited columns first
+    for (int f = 0; f < n_extra; ++f) fb[b.nfields + f] = extra_field_bytes[f];
+    const int rc = dsoa_register_type(h, fb, b.nfields + n_extra, type_out);
+    if (rc) return rc;
+    h->types[*type_out].base = base;
+    return DSOA_OK;
+}
+
+int dsoa_type_base(dsoa_heap* h, int type, int* base_out) {
+    if (!h || !base_out || type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+    *base_out = h->types[type].base;
     return DSOA_OK;
 }
 
@@ -947,16 +968,46 @@ int dsoa_parallel_new(dsoa_heap* h, int type, uint64_t n, int ctor_id, const voi
     return DSOA_ERR_UNKNOWN_METHOD;
 }
 
-int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args, size_t nb) {
-    int rc = dsoa_ensure_frozen(h);
-    if (rc) return rc;
-    if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+static int parallel_do_one(dsoa_heap* h, int type, int method_id, const void* args, size_t nb) {
     if (method_id >= 100 && method_id < 200) return dsoa_micro_do(h, type, method_id, args, nb);
     if (method_id >= 200 && method_id < 300) return dsoa_gol_do(h, type, method_id, args, nb);
     if (method_id >= 300 && method_id < 400) return dsoa_wator_do(h, type, method_id, args, nb);
     if (method_id >= 400 && method_id < 500) return dsoa_traffic_do(h, type, method_id, args, nb);
     if (method_id >= 500 && method_id < 600) return dsoa_nbody_do(h, type, method_id, args, nb);
     return DSOA_ERR_UNKNOWN_METHOD;
+}
+
+// type and every type that extends it, directly or not (subtypes are registered
+// after their base, so they follow it in id order)
+static int type_family(const dsoa_heap* h, int type, int* out) {
+    int n = 0;
+    for (int u = type; u < h->ntypes; ++u) {
+        int a = u;
+        while (a > type) a = h->types[a].base;
+        if (a == type) out[n++] = u;
+    }
+    return n;
+}
+
+int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args, size_t nb) {
+    int rc = dsoa_ensure_frozen(h);
+    if (rc) return rc;
+    if (type < 0 || type >= h->ntypes) return DSOA_ERR_INVALID_ARG;
+    int fam[DSOA_MAX_TYPES];
+    const int n = type_family(h, type, fam);
+    if (n == 1) return parallel_do_one(h, type, method_id, args, nb);
+    // The objects of the type and of its subtypes existing at entry: one
+    // enumeration launch snapshots every member, then one do-all launch per
+    // member type runs on its snapshot.
+    if (!h->skip_enumeration) {
+        rc = dsoa_enumerate_many(h, fam, n);
+        if (rc) return rc;
+    }
+    const bool skip = h->skip_enumeration;
+    h->skip_enumeration = true;
+    for (int q = 0; q < n && rc == DSOA_OK; ++q) rc = parallel_do_one(h, fam[q], method_id, args, nb);
+    h->skip_enumeration = skip;
+    return rc;
 }
 
 int dsoa_parallel_do_enumerated(dsoa_heap* h, int type, int method_id, const void* args, size_t nb) {
@@ -1117,13 +1168,14 @@ struct dsoa_image_header {
     uint32_t nfields[DSOA_MAX_TYPES];
     uint32_t field_bytes[DSOA_MAX_TYPES][DSOA_MAX_FIELDS];
     uint32_t capacity[DSOA_MAX_TYPES];
+    int32_t base[DSOA_MAX_TYPES];
 };
 static const uint64_t kImageMagic = 0x31304D4941534F44ull;   // "DOSAIM01"
 
 static void image_header(const dsoa_heap* h, dsoa_image_header* H) {
     std::memset(H, 0, sizeof(*H));
     H->magic = kImageMagic;
-    H->version = 1;
+    H->version = 2;
     H->bytes = h->bytes;
     H->M = h->ctx.M;
     H->meta = h->meta_bytes;
@@ -1135,6 +1187,7 @@ static void image_header(const dsoa_heap* h, dsoa_image_header* H) {
         H->nfields[t] = (uint32_t)h->types[t].nfields;
         for (int f = 0; f < h->types[t].nfields; ++f) H->field_bytes[t][f] = h->types[t].field_bytes[f];
         H->capacity[t] = h->types[t].capacity;
+        H->base[t] = h->types[t].base;
     }
 }
 

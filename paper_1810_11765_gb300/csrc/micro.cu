@@ -361,7 +361,8 @@ int dsoa_micro_new(dsoa_heap* h, int type, uint64_t n, int ctor, const void* a, 
     int rc = dsoa_copy_args(&args, a, nb);
     if (rc) return rc;
     if (ctor != DSOA_C_MICRO) return DSOA_ERR_UNKNOWN_METHOD;
-    if (h->types[type].nfields != 3 || h->types[type].field_bytes[0] != 4 || h->types[type].field_bytes[1] != 4 ||
+    // the microbench type, or a type extending it (its first three columns)
+    if (h->types[type].nfields < 3 || h->types[type].field_bytes[0] != 4 || h->types[type].field_bytes[1] != 4 ||
         h->types[type].field_bytes[2] != 8)
         return DSOA_ERR_INVALID_ARG;
     return dsoa_run_new<MicroCtor>(h, type, n, args);

@@ -444,8 +444,8 @@ __global__ void __launch_bounds__(256) k_pairs_tiled(dsoa_ctx c, uint32_t t, con
 // bodies of tile J in shared memory.  Within a group the pairs go round a
 // rotation: at step s lane l pairs its i with j = (l + s) mod 32, adds the i
 // term to its register sum and subtracts the j term from a running j sum that
-// moves one lane down after the step, so after the 32 steps every lane holds a
-// whole warp's sum for one j.  Warps take the groups in rotated order, their j
+// moves one lane down after the step, so after the 32 steps lane l holds a
+// whole warp's sum for j = l.  Warps take the groups in rotated order, their j
 // sums meet in shared memory (64-bit shared atomics) and leave with one global
 // atomic per body and item; the i sums leave when the CTA moves to the next
 // row.  In a diagonal tile (I = J) warp w pairs its group only with the groups
@@ -478,7 +478,7 @@ __device__ __forceinline__ float4 stage_body(const dsoa_ctx& c, uint32_t t, bool
 // items in the rows before row I of the triangle (I + 1 .. nt items per row)
 __device__ __forceinline__ uint64_t tri_start(uint64_t I, uint64_t nt) { return I * nt - I * (I - 1) / 2; }
 
-__global__ void __launch_bounds__(256) k_force_sym(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+__global__ void __launch_bounds__(256, 5) k_force_sym(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                                    const unsigned long long* __restrict__ occ,
                                                    const uint32_t* __restrict__ r_dev, dsoa_nbody_args a) {
     __shared__ float4 sj[2 * kTile];                 // group g at [64 g, 64 g + 64): its 32 bodies twice
@@ -539,15 +539,19 @@ __global__ void __launch_bounds__(256) k_force_sym(dsoa_ctx c, uint32_t t, const
             if (diag && g < warp) continue;
             const float4* col = sj + 64u * g + lane;
             if (diag && g == warp) {
-#pragma unroll
+#pragma unroll 4
                 for (uint32_t s = 1; s < 32u; ++s) {
                     const float4 q = col[s];
                     pair_term(px, py, gsm, q.x, q.y, q.z, eps2, fx, fy);
                 }
                 continue;
             }
-            unsigned long long gx = 0ull, gy = 0ull;
-#pragma unroll
+            // Terms below 2^25 in magnitude (nearly all) are summed in 32 bits over
+            // the group's 32 steps (at most 2^30, no overflow) and folded into the
+            // 64-bit sums once per group; a step with a larger term adds all four
+            // terms in 64 bits directly (the j terms by shared atomics).
+            int fx32 = 0, fy32 = 0, gx32 = 0, gy32 = 0;
+#pragma unroll 8
             for (uint32_t s = 0; s < 32u; ++s) {
                 const float4 q = col[s];
                 const float dx = __fsub_rn(q.x, px), dy = __fsub_rn(q.y, py);
@@ -556,18 +560,28 @@ __global__ void __launch_bounds__(256) k_force_sym(dsoa_ctx c, uint32_t t, const
                 const float inv3 = __fmul_rn(__fmul_rn(inv, inv), inv);
                 const float kij = __fmul_rn(__fmul_rn(gsm, q.z), inv3);
                 const float kji = __fmul_rn(__fmul_rn(q.w, m), inv3);
-                fx += fix(__fmul_rn(kij, dx));
-                fy += fix(__fmul_rn(kij, dy));
-                gx -= fix(__fmul_rn(kji, dx));
-                gy -= fix(__fmul_rn(kji, dy));
-                if (s < 31u) {
-                    gx = __shfl_sync(0xFFFFFFFFu, gx, src);
-                    gy = __shfl_sync(0xFFFFFFFFu, gy, src);
+                const float ax = __fmul_rn(kij, dx), ay = __fmul_rn(kij, dy);
+                const float bx = __fmul_rn(kji, dx), by = __fmul_rn(kji, dy);
+                if ((fabsf(ax) < 0x1p25f) & (fabsf(ay) < 0x1p25f) & (fabsf(bx) < 0x1p25f) & (fabsf(by) < 0x1p25f)) {
+                    fx32 += __float2int_rn(ax);
+                    fy32 += __float2int_rn(ay);
+                    gx32 -= __float2int_rn(bx);
+                    gy32 -= __float2int_rn(by);
+                } else {
+                    const uint32_t j = 32u * g + ((lane + s) & 31u);
+                    fx += fix(ax);
+                    fy += fix(ay);
+                    const unsigned long long ux = 0ull - fix(bx), uy = 0ull - fix(by);
+                    if (ux) atomicAdd(&sacc[0][j], ux);
+                    if (uy) atomicAdd(&sacc[1][j], uy);
                 }
+                gx32 = __shfl_sync(0xFFFFFFFFu, gx32, src);
+                gy32 = __shfl_sync(0xFFFFFFFFu, gy32, src);
             }
-            const uint32_t j = 32u * g + ((lane + 31u) & 31u);   // the sum lane l holds after step 31
-            if (gx) atomicAdd(&sacc[0][j], gx);
-            if (gy) atomicAdd(&sacc[1][j], gy);
+            fx += (unsigned long long)(long long)fx32;          // after 32 moves lane l holds j = l
+            fy += (unsigned long long)(long long)fy32;
+            if (gx32) atomicAdd(&sacc[0][32u * g + lane], (unsigned long long)(long long)gx32);
+            if (gy32) atomicAdd(&sacc[1][32u * g + lane], (unsigned long long)(long long)gy32);
         }
         __syncthreads();                             // every j sum of the item is in
         const unsigned long long jx = sacc[0][tid], jy = sacc[1][tid];

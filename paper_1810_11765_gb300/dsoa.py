@@ -96,7 +96,8 @@ class NBodyArgs(ctypes.Structure):
 
 # exported names of include/dsoa.h, in declaration order
 ABI_FUNCTIONS = [
-    "dsoa_heap_create", "dsoa_heap_create_from", "dsoa_register_type", "dsoa_heap_freeze",
+    "dsoa_heap_create", "dsoa_heap_create_from", "dsoa_register_type", "dsoa_register_subtype",
+    "dsoa_type_base", "dsoa_heap_freeze",
     "dsoa_heap_info", "dsoa_field_offset", "dsoa_parallel_new", "dsoa_parallel_do",
     "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_delete_handles", "dsoa_enumerate",
     "dsoa_enumerate_many", "dsoa_count", "dsoa_count_async", "dsoa_count_many_async",
@@ -132,6 +133,7 @@ def load(path: str | None = None):
     sig = {
         "dsoa_heap_create": [sz, vp, vp], "dsoa_heap_create_from": [vp, sz, vp, vp],
         "dsoa_register_type": [vp, vp, i32, vp], "dsoa_heap_freeze": [vp],
+        "dsoa_register_subtype": [vp, i32, vp, i32, vp], "dsoa_type_base": [vp, i32, vp],
         "dsoa_heap_info": [vp, vp, vp, vp, vp], "dsoa_field_offset": [vp, i32, i32, vp],
         "dsoa_parallel_new": [vp, i32, u64, i32, vp, sz], "dsoa_parallel_do": [vp, i32, i32, vp, sz],
         "dsoa_parallel_do_enumerated": [vp, i32, i32, vp, sz],
@@ -241,6 +243,19 @@ class Heap:
         t = ctypes.c_int()
         _ok(load().dsoa_register_type(self._h, fb, len(field_bytes), ctypes.byref(t)), "dsoa_register_type")
         return t.value
+
+    def register_subtype(self, base: int, extra_field_bytes=()) -> int:
+        """A type extending ``base``: base's fields, then ``extra_field_bytes``."""
+        n = len(extra_field_bytes)
+        fb = (ctypes.c_uint32 * max(n, 1))(*extra_field_bytes)
+        t = ctypes.c_int()
+        _ok(load().dsoa_register_subtype(self._h, base, fb, n, ctypes.byref(t)), "dsoa_register_subtype")
+        return t.value
+
+    def type_base(self, t: int) -> int:
+        b = ctypes.c_int()
+        _ok(load().dsoa_type_base(self._h, t, ctypes.byref(b)), "dsoa_type_base")
+        return b.value
 
     def freeze(self):
         _ok(load().dsoa_heap_freeze(self._h), "dsoa_heap_freeze")
