@@ -135,6 +135,42 @@ int dsoa_parallel_new(dsoa_heap* h, int type, uint64_t n, int ctor_id,
 int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args_host,
                      size_t args_bytes);
 
+/* ---- user methods (Sec. 2.1: parallel_do<T, &T::func> for any member
+ * function).  A user translation unit includes dsoa_device.cuh, writes a
+ * method struct (see dsoa_doall_kernel there) and names it with
+ * DSOA_METHOD(id, launcher, Method): that instantiates the do-all kernel for
+ * the method in the user's own library, and a static initializer registers the
+ * launcher under `id` when that library is loaded.  dsoa_parallel_do(h, type,
+ * id, args) then enumerates as for a built-in method and calls the launcher
+ * with the prepared launch; the launch runs on the heap's stream and counts as
+ * one of the heap's launches. */
+#define DSOA_USER_METHOD_MIN 1000
+#define DSOA_USER_METHOD_MAX 1999
+typedef struct {
+    const void* ctx;              /* host copy of this launch's struct dsoa_ctx          */
+    size_t ctx_bytes;             /* sizeof(struct dsoa_ctx) in the library              */
+    int32_t type;                 /* the type the do-all runs on                         */
+    uint32_t tpb;                 /* threads per CTA (multiple of 64)                    */
+    uint32_t max_ctas_per_sm;     /* resident CTAs per SM the grid may assume            */
+    uint32_t num_sms;
+    uint32_t waves;               /* grid = waves x resident grid                         */
+    uint32_t slots_per_thread;    /* 1 or 2                                              */
+    uint32_t pdl;                 /* 1: launch with programmatic stream serialization    */
+    uint32_t reserved;
+    const uint32_t* R;            /* device: block list of the snapshot                  */
+    const uint64_t* occ;          /* device: occupancy snapshot per listed block         */
+    const uint32_t* r_dev;        /* device: number of listed blocks                     */
+    void* stream;                 /* cudaStream_t of the heap                            */
+} dsoa_doall_launch;
+/* Launches the method's do-all kernel; DSOA_OK, or DSOA_ERR_INVALID_ARG (args
+ * of the wrong size, ctx of another library build), DSOA_ERR_CUDA. */
+typedef int (*dsoa_method_fn)(const dsoa_doall_launch* launch, const void* args_host, size_t args_bytes);
+/* Process-wide registration of `fn` under method id DSOA_USER_METHOD_MIN ..
+ * DSOA_USER_METHOD_MAX.  Registering the same fn again is a no-op; another fn
+ * under a taken id, a null fn or an id out of range give DSOA_ERR_INVALID_ARG.
+ * An unregistered id in dsoa_parallel_do gives DSOA_ERR_UNKNOWN_METHOD. */
+int dsoa_register_method(int method_id, dsoa_method_fn fn);
+
 /* The method kernel of dsoa_parallel_do alone, over the snapshot and block
  * list of the latest enumeration of `type` (dsoa_enumerate or a previous
  * dsoa_parallel_do of the same type).  Valid only while no object of `type`

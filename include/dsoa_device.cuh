@@ -29,6 +29,7 @@
 #define DSOA_DEVICE_CUH
 
 #include <stdint.h>
+#include <string.h>
 
 #include "dsoa.h"
 
@@ -623,6 +624,55 @@ __global__ void __maxnreg__(DSOA_DOALL_MAXNREG) dsoa_doall_kernel(dsoa_ctx c, ui
         }
     }
 }
+
+/* ------------------------------------------------------------------------
+ * User methods.  A user translation unit writes a method struct M like the
+ * built-in ones (typedef Args; static __device__ run(ctx, type, block, slot,
+ * args)) and names it once:
+ *     DSOA_METHOD(1000, my_launcher, M)
+ * which defines the extern "C" launcher (it instantiates dsoa_doall_kernel<M>
+ * in the user's library and launches it with the shape the library prepared)
+ * and registers it under the id when the library is loaded (the user library
+ * links against libdsoa).  The method may allocate (dsoa_new), delete `this`
+ * and objects of other types, and read / write any field (dsoa_field,
+ * dsoa_column), as the built-in methods do (Sec. 2.1).
+ * ------------------------------------------------------------------------ */
+template <class M>
+inline int dsoa_launch_user_doall(const dsoa_doall_launch* L, const void* args_host, size_t args_bytes) {
+    typedef typename M::Args A;
+    if (!L || !L->ctx || L->ctx_bytes != sizeof(dsoa_ctx) || !args_host || args_bytes != sizeof(A))
+        return DSOA_ERR_INVALID_ARG;
+    dsoa_ctx c;
+    memcpy(&c, L->ctx, sizeof(c));
+    A a;
+    memcpy(&a, args_host, sizeof(A));
+    void (*k)(dsoa_ctx, uint32_t, const uint32_t*, const unsigned long long*, const uint32_t*, A) =
+        L->slots_per_thread >= 2 ? &dsoa_doall_kernel<M, 2> : &dsoa_doall_kernel<M, 1>;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)L->tpb, 0) != cudaSuccess)
+        return DSOA_ERR_CUDA;
+    if (per_sm > (int)L->max_ctas_per_sm) per_sm = (int)L->max_ctas_per_sm;
+    if (per_sm < 1) per_sm = 1;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)per_sm * L->num_sms * (L->waves ? L->waves : 1u));
+    cfg.blockDim = dim3(L->tpb);
+    cfg.stream = (cudaStream_t)L->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = L->pdl ? 1u : 0u;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k, c, (uint32_t)L->type, L->R,
+                                             (const unsigned long long*)L->occ, L->r_dev, a);
+    return e == cudaSuccess ? DSOA_OK : DSOA_ERR_CUDA;
+}
+
+#define DSOA_METHOD(method_id, launcher, M)                                                        \
+    extern "C" int launcher(const dsoa_doall_launch* launch, const void* args, size_t args_bytes) { \
+        return dsoa_launch_user_doall<M>(launch, args, args_bytes);                                 \
+    }                                                                                               \
+    static const int launcher##_dsoa_registered = dsoa_register_method((method_id), &launcher);
 
 /* ------------------------------------------------------------------------
  * Streamed do-all: the enumeration of Sec. 3.7 done inside the method kernel.

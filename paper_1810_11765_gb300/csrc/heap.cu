@@ -968,7 +968,46 @@ int dsoa_parallel_new(dsoa_heap* h, int type, uint64_t n, int ctor_id, const voi
     return DSOA_ERR_UNKNOWN_METHOD;
 }
 
+// ---- user methods: launchers registered by user libraries (process-wide)
+static std::mutex g_user_mu;
+static dsoa_method_fn g_user[DSOA_USER_METHOD_MAX - DSOA_USER_METHOD_MIN + 1];
+
+static dsoa_method_fn user_method(int id) {
+    std::lock_guard<std::mutex> lock(g_user_mu);
+    return g_user[id - DSOA_USER_METHOD_MIN];
+}
+
+// Enumerate as for a built-in method, then hand the prepared launch to the
+// user's launcher (which instantiates dsoa_doall_kernel for its method).
+static int user_do(dsoa_heap* h, int type, int method_id, const void* args, size_t nb) {
+    const dsoa_method_fn fn = user_method(method_id);
+    if (!fn) return DSOA_ERR_UNKNOWN_METHOD;
+    int rc = dsoa_prepare_doall(h, type);
+    if (rc) return rc;
+    const dsoa_ctx c = dsoa_launch_ctx(h);
+    dsoa_doall_launch L;
+    std::memset(&L, 0, sizeof(L));
+    L.ctx = &c;
+    L.ctx_bytes = sizeof(c);
+    L.type = type;
+    L.tpb = (uint32_t)h->doall_tpb;
+    L.max_ctas_per_sm = (uint32_t)h->doall_ctas_per_sm;
+    L.num_sms = (uint32_t)h->num_sms;
+    L.waves = (uint32_t)h->doall_waves;
+    L.slots_per_thread = h->slots_per_thread >= 2 ? 2u : 1u;
+    L.pdl = (h->flags & DSOA_FLAG_PDL) ? 1u : 0u;
+    L.R = h->R[type];
+    L.occ = (const uint64_t*)h->Rocc[type];
+    L.r_dev = h->r_dev[type];
+    L.stream = (void*)h->stream;
+    rc = fn(&L, args, nb);
+    h->launches++;
+    return rc;
+}
+
 static int parallel_do_one(dsoa_heap* h, int type, int method_id, const void* args, size_t nb) {
+    if (method_id >= DSOA_USER_METHOD_MIN && method_id <= DSOA_USER_METHOD_MAX)
+        return user_do(h, type, method_id, args, nb);
     if (method_id >= 100 && method_id < 200) return dsoa_micro_do(h, type, method_id, args, nb);
     if (method_id >= 200 && method_id < 300) return dsoa_gol_do(h, type, method_id, args, nb);
     if (method_id >= 300 && method_id < 400) return dsoa_wator_do(h, type, method_id, args, nb);
@@ -987,6 +1026,15 @@ static int type_family(const dsoa_heap* h, int type, int* out) {
         if (a == type) out[n++] = u;
     }
     return n;
+}
+
+int dsoa_register_method(int method_id, dsoa_method_fn fn) {
+    if (!fn || method_id < DSOA_USER_METHOD_MIN || method_id > DSOA_USER_METHOD_MAX) return DSOA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_user_mu);
+    dsoa_method_fn& slot = g_user[method_id - DSOA_USER_METHOD_MIN];
+    if (slot && slot != fn) return DSOA_ERR_INVALID_ARG;
+    slot = fn;
+    return DSOA_OK;
 }
 
 int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args, size_t nb) {

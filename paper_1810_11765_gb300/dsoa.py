@@ -43,6 +43,7 @@ K_TRAFFIC_INIT, K_TRAFFIC_CLEAR, K_TRAFFIC_ONRAMP, K_TRAFFIC_ADVANCE = 450, 451,
 C_NBODY, M_NBODY_FORCE, M_NBODY_MOVE = 500, 501, 502
 M_COLL_FIND, M_COLL_CLAIM, M_COLL_MERGE, M_COLL_DELETE = 503, 504, 505, 506
 M_NBODY_READ, M_NBODY_FORCE_TILED, M_COLL_FIND_TILED = 507, 508, 509
+USER_METHOD_MIN, USER_METHOD_MAX = 1000, 1999
 NBODY_KEYED_FIND = 1
 NBODY_ALL_PAIRS = 2
 
@@ -97,7 +98,7 @@ class NBodyArgs(ctypes.Structure):
 # exported names of include/dsoa.h, in declaration order
 ABI_FUNCTIONS = [
     "dsoa_heap_create", "dsoa_heap_create_from", "dsoa_register_type", "dsoa_register_subtype",
-    "dsoa_type_base", "dsoa_heap_freeze",
+    "dsoa_type_base", "dsoa_register_method", "dsoa_heap_freeze",
     "dsoa_heap_info", "dsoa_field_offset", "dsoa_parallel_new", "dsoa_parallel_do",
     "dsoa_parallel_do_enumerated", "dsoa_run_kernel", "dsoa_delete_handles", "dsoa_enumerate",
     "dsoa_enumerate_many", "dsoa_count", "dsoa_count_async", "dsoa_count_many_async",
@@ -134,6 +135,7 @@ def load(path: str | None = None):
         "dsoa_heap_create": [sz, vp, vp], "dsoa_heap_create_from": [vp, sz, vp, vp],
         "dsoa_register_type": [vp, vp, i32, vp], "dsoa_heap_freeze": [vp],
         "dsoa_register_subtype": [vp, i32, vp, i32, vp], "dsoa_type_base": [vp, i32, vp],
+        "dsoa_register_method": [i32, vp],
         "dsoa_heap_info": [vp, vp, vp, vp, vp], "dsoa_field_offset": [vp, i32, i32, vp],
         "dsoa_parallel_new": [vp, i32, u64, i32, vp, sz], "dsoa_parallel_do": [vp, i32, i32, vp, sz],
         "dsoa_parallel_do_enumerated": [vp, i32, i32, vp, sz],

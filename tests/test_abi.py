@@ -104,3 +104,21 @@ def test_ctypes_layouts_match_c_headers(tmp_path):
             assert getattr(cls, parts[1]).offset == int(parts[2]), ln
         n += 1
     assert n >= 15
+
+
+def test_user_method_library_builds_against_the_public_headers(lib, tmp_path):
+    """A user library of do-all methods (tests/user_method.cu) compiles for
+    sm_103a from include/ alone, links against libdsoa and exports its launchers;
+    it needs dsoa_register_method, which libdsoa exports."""
+    from paper_1810_11765_gb300 import build
+    out = tmp_path / "libuser_methods.so"
+    r = subprocess.run([build._nvcc(), *build.ARCH, "-O3", "-std=c++17", "-I", INCLUDE, "-shared",
+                        "-Xcompiler", "-fPIC", "-cudart", "shared", "-o", str(out),
+                        os.path.join(ROOT, "tests", "user_method.cu"), "-L", build.OUT, "-ldsoa"],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    syms = subprocess.run(["nm", "-D", str(out)], capture_output=True, text=True).stdout
+    for name in ("user_scale", "user_spawn", "user_mark"):
+        assert re.search(rf" T {name}$", syms, flags=re.M), name
+    assert re.search(r" U dsoa_register_method$", syms, flags=re.M)
+    assert hasattr(lib, "dsoa_register_method")
