@@ -873,6 +873,18 @@ def dsoa_arm(args):
         # --- alloc + free
         out["l2_atomic_peak"] = l2_atomic_peak()
         out["l2_atomic_contended"] = l2_atomic_peak(words=32)
+        # each step phase's L2 atomic rate against the probe's (both as L2 atomic
+        # requests, counted by ncu per agent and per probe op)
+        probe_req = ncu_traffic("k_atomic_peak", 1.0, "l2_atomic_requests_per_unit")
+        for k, ph in out.get("step_phases", {}).items():
+            req = ncu_traffic(k, ph["agents"], "l2_atomic_requests_per_unit")
+            if req is None or probe_req is None:
+                ph["l2_atomic"] = None
+                continue
+            rate = req / (ph["ms"] / 1e3)
+            peak = out["l2_atomic_peak"]["atomics_per_s"] * probe_req
+            ph["l2_atomic"] = {"requests_per_agent": req / ph["agents"], "requests_per_s": rate,
+                               "peak_requests_per_s": peak, "frac": rate / peak}
         sweep = {}
         for lg in (18, 20, 22, 24):      # 2^18 threads' worth x {1, 4, 16, 64} objects
             st = alloc_free_storm(lg, flush)
