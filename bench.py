@@ -697,17 +697,16 @@ def nbody_leg(flush, steps=5, collide_steps=10):
 
 
 def serving_leg(n_req=24, multiples=(0.25, 0.5, 1.0, 2.0)):
-    """Continuous batching of game-of-life / wa-tor instances (sides 2^8..2^10 and
-    100..300 steps to bound the run time).  The service rate is measured first with
-    every request arriving at once (requests / wall time); Poisson arrival rates are
-    then swept as multiples of it."""
+    """Continuous batching of game-of-life / wa-tor instances as configured: sides
+    round(2^U(8,12)), 100..1000 steps, one heap capped at 64 GiB.  The service rate
+    is measured first with every request arriving at once (requests / wall time);
+    Poisson arrival rates are then swept as multiples of it."""
     from paper_1810_11765_gb300 import inputs
     from paper_1810_11765_gb300.serving import Server
 
     def run(rate):
-        reqs = inputs.serving_requests(n_req, rate_per_s=rate, side_log2_min=8, side_log2_max=10,
-                                       steps_min=100, steps_max=300)
-        srv = Server(8 << 30, capacity=32)
+        reqs = inputs.serving_requests(n_req, rate_per_s=rate)
+        srv = Server(64 << 30, capacity=32)
         _, summary = srv.run(reqs)
         srv.close()
         summary.pop("rejected", None)

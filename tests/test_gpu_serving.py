@@ -67,3 +67,21 @@ def test_admission_waits_for_blocks():
     assert len(fin) == 6
     for f in fin.values():
         assert np.array_equal(f.grid, oracle_grid(f))
+
+
+def test_configured_stream_sampled():
+    """The configured serving stream (24 requests, half game of life and half
+    Wa-Tor, sides 2^U(8,12), 100-1000 steps, 64 GiB heap), all arriving at once:
+    the three cheapest instances equal the oracle alone, and the largest equals a
+    GPU run of it alone."""
+    from paper_1810_11765_gb300 import inputs
+    reqs = inputs.serving_requests(24, rate_per_s=1e9)
+    mixed, summary = serve(reqs, heap_bytes=64 << 30, capacity=32)
+    assert summary["device_errors"] == 0 and len(mixed) == 24
+    assert max(q.side for q in reqs) > 2048
+    for q in sorted(reqs, key=lambda q: q.side * q.side * q.steps)[:3]:
+        f = mixed[q.rid]
+        assert np.array_equal(f.grid, oracle_grid(f)), (f.rid, f.kind, f.side, f.steps)
+    big = max(reqs, key=lambda q: q.side)
+    alone, _ = serve([big], heap_bytes=64 << 30, capacity=1)
+    assert np.array_equal(alone[big.rid].grid, mixed[big.rid].grid)
