@@ -613,10 +613,13 @@ def app_steps(kind, steps, flush, warmup=3, side=None, heap_bytes=1 << 30):
 
 
 # Algorithmic operations of one unordered pair of the n-body force (both bodies'
-# terms): dx, dy (2 sub), d2 (2 mul, 2 add), sqrt, reciprocal, d^-3 (2 mul), the two
-# coefficients (G S m_i) m_j d^-3 and (G S m_j) m_i d^-3 (4 mul), k dx and k dy for
-# each body (4 mul), four conversions to the fixed-point grid, four 64-bit adds.
-NBODY_OPS_PER_UNORDERED_PAIR = 26
+# terms) in the configured workload, where G S is a power of two and the masses
+# are small integers, so (G S m_i) m_j = (G S m_j) m_i and j's term is the negated
+# i term: dx, dy (2 sub), d2 (2 mul, 2 add), sqrt, reciprocal, d^-3 (2 mul), the
+# coefficient k (2 mul), k dx and k dy (2 mul), two conversions to the fixed-point
+# grid, four adds (i and j).  With unequal coefficients it is 26 (a second k and
+# its two products and conversions).
+NBODY_OPS_PER_UNORDERED_PAIR = 20
 
 
 def fp32_lane_peak(clock_mhz):

@@ -478,6 +478,70 @@ __device__ __forceinline__ float4 stage_body(const dsoa_ctx& c, uint32_t t, bool
 // items in the rows before row I of the triangle (I + 1 .. nt items per row)
 __device__ __forceinline__ uint64_t tri_start(uint64_t I, uint64_t nt) { return I * nt - I * (I - 1) / 2; }
 
+// One 32-step rotation of warp group `g` (see above).  Terms below 2^25 in
+// magnitude (nearly all) are summed in 32 bits over the 32 steps (at most 2^30,
+// no overflow) and folded into the 64-bit sums once; a step with a larger term
+// adds its terms in 64 bits directly (the j terms by shared atomics).  kSame:
+// the two coefficients of every pair are known to be equal, (G S m_i) m_j =
+// (G S m_j) m_i exactly, so the j term is the negated i term.
+template <bool kSame>
+__device__ __forceinline__ void sym_group(const float4* col, float px, float py, float m, float gsm, float eps2,
+                                          uint32_t g, uint32_t lane, uint32_t src, unsigned long long& fx,
+                                          unsigned long long& fy, unsigned long long* sx, unsigned long long* sy) {
+    int fx32 = 0, fy32 = 0, gx32 = 0, gy32 = 0;
+#pragma unroll 8
+    for (uint32_t s = 0; s < 32u; ++s) {
+        const float4 q = col[s];
+        const float dx = __fsub_rn(q.x, px), dy = __fsub_rn(q.y, py);
+        const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), eps2);
+        const float inv = __frcp_rn(__fsqrt_rn(d2));
+        const float inv3 = __fmul_rn(__fmul_rn(inv, inv), inv);
+        const float kij = __fmul_rn(__fmul_rn(gsm, q.z), inv3);
+        const float ax = __fmul_rn(kij, dx), ay = __fmul_rn(kij, dy);
+        if (kSame) {
+            if ((fabsf(ax) < 0x1p25f) & (fabsf(ay) < 0x1p25f)) {
+                const int vx = __float2int_rn(ax), vy = __float2int_rn(ay);
+                fx32 += vx;
+                fy32 += vy;
+                gx32 -= vx;
+                gy32 -= vy;
+            } else {
+                const uint32_t j = 32u * g + ((lane + s) & 31u);
+                const unsigned long long ux = fix(ax), uy = fix(ay);
+                fx += ux;
+                fy += uy;
+                if (ux) atomicAdd(&sx[j], 0ull - ux);
+                if (uy) atomicAdd(&sy[j], 0ull - uy);
+            }
+        } else {
+            const float kji = __fmul_rn(__fmul_rn(q.w, m), inv3);
+            const float bx = __fmul_rn(kji, dx), by = __fmul_rn(kji, dy);
+            if ((fabsf(ax) < 0x1p25f) & (fabsf(ay) < 0x1p25f) & (fabsf(bx) < 0x1p25f) & (fabsf(by) < 0x1p25f)) {
+                fx32 += __float2int_rn(ax);
+                fy32 += __float2int_rn(ay);
+                gx32 -= __float2int_rn(bx);
+                gy32 -= __float2int_rn(by);
+            } else {
+                const uint32_t j = 32u * g + ((lane + s) & 31u);
+                fx += fix(ax);
+                fy += fix(ay);
+                const unsigned long long ux = 0ull - fix(bx), uy = 0ull - fix(by);
+                if (ux) atomicAdd(&sx[j], ux);
+                if (uy) atomicAdd(&sy[j], uy);
+            }
+        }
+        gx32 = __shfl_sync(0xFFFFFFFFu, gx32, src);
+        gy32 = __shfl_sync(0xFFFFFFFFu, gy32, src);
+    }
+    fx += (unsigned long long)(long long)fx32;               // after 32 moves lane l holds j = l
+    fy += (unsigned long long)(long long)fy32;
+    if (gx32) atomicAdd(&sx[32u * g + lane], (unsigned long long)(long long)gx32);
+    if (gy32) atomicAdd(&sy[32u * g + lane], (unsigned long long)(long long)gy32);
+}
+
+// an integer mass in [0, 2^12]: products of two are exact in binary32
+__device__ __forceinline__ bool small_integer(float m) { return m >= 0.0f && m <= 0x1p12f && m == truncf(m); }
+
 __global__ void __launch_bounds__(256, 5) k_force_sym(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                                    const unsigned long long* __restrict__ occ,
                                                    const uint32_t* __restrict__ r_dev, dsoa_nbody_args a) {
@@ -490,6 +554,7 @@ __global__ void __launch_bounds__(256, 5) k_force_sym(dsoa_ctx c, uint32_t t, co
     const bool dense = r <= kDenseMaxR;
     const uint32_t nb = index_space(dense, r, occ, pre, wsum);
     const float gs = __fmul_rn(a.G, a.fscale), eps2 = a.eps2;
+    const bool gs_pow2 = (__float_as_uint(gs) & 0x807FFFFFu) == 0u && gs >= 0x1p-100f && gs <= 0x1p100f;
     const uint64_t nt = (nb + kTile - 1) / kTile, items = nt * (nt + 1) / 2;
     const uint64_t wb = items * blockIdx.x / gridDim.x, we = items * (blockIdx.x + 1) / gridDim.x;
     sacc[0][tid] = 0ull;
@@ -531,7 +596,9 @@ __global__ void __launch_bounds__(256, 5) k_force_sym(dsoa_ctx c, uint32_t t, co
         __syncthreads();                             // readers of the previous tile are done
         sj[2u * tid - lane] = v;                     // = 64 warp + lane
         sj[2u * tid - lane + 32u] = v;
-        __syncthreads();
+        // G S a power of two and every mass of both tiles a small integer: the
+        // products (G S m_i) m_j and (G S m_j) m_i are exact, hence equal
+        const bool same = __syncthreads_and(small_integer(m) && small_integer(v.z)) && gs_pow2;
         const bool diag = I == J;
 #pragma unroll 1
         for (uint32_t k = 0; k < kSymGroups; ++k) {
@@ -546,42 +613,10 @@ __global__ void __launch_bounds__(256, 5) k_force_sym(dsoa_ctx c, uint32_t t, co
                 }
                 continue;
             }
-            // Terms below 2^25 in magnitude (nearly all) are summed in 32 bits over
-            // the group's 32 steps (at most 2^30, no overflow) and folded into the
-            // 64-bit sums once per group; a step with a larger term adds all four
-            // terms in 64 bits directly (the j terms by shared atomics).
-            int fx32 = 0, fy32 = 0, gx32 = 0, gy32 = 0;
-#pragma unroll 8
-            for (uint32_t s = 0; s < 32u; ++s) {
-                const float4 q = col[s];
-                const float dx = __fsub_rn(q.x, px), dy = __fsub_rn(q.y, py);
-                const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), eps2);
-                const float inv = __frcp_rn(__fsqrt_rn(d2));
-                const float inv3 = __fmul_rn(__fmul_rn(inv, inv), inv);
-                const float kij = __fmul_rn(__fmul_rn(gsm, q.z), inv3);
-                const float kji = __fmul_rn(__fmul_rn(q.w, m), inv3);
-                const float ax = __fmul_rn(kij, dx), ay = __fmul_rn(kij, dy);
-                const float bx = __fmul_rn(kji, dx), by = __fmul_rn(kji, dy);
-                if ((fabsf(ax) < 0x1p25f) & (fabsf(ay) < 0x1p25f) & (fabsf(bx) < 0x1p25f) & (fabsf(by) < 0x1p25f)) {
-                    fx32 += __float2int_rn(ax);
-                    fy32 += __float2int_rn(ay);
-                    gx32 -= __float2int_rn(bx);
-                    gy32 -= __float2int_rn(by);
-                } else {
-                    const uint32_t j = 32u * g + ((lane + s) & 31u);
-                    fx += fix(ax);
-                    fy += fix(ay);
-                    const unsigned long long ux = 0ull - fix(bx), uy = 0ull - fix(by);
-                    if (ux) atomicAdd(&sacc[0][j], ux);
-                    if (uy) atomicAdd(&sacc[1][j], uy);
-                }
-                gx32 = __shfl_sync(0xFFFFFFFFu, gx32, src);
-                gy32 = __shfl_sync(0xFFFFFFFFu, gy32, src);
-            }
-            fx += (unsigned long long)(long long)fx32;          // after 32 moves lane l holds j = l
-            fy += (unsigned long long)(long long)fy32;
-            if (gx32) atomicAdd(&sacc[0][32u * g + lane], (unsigned long long)(long long)gx32);
-            if (gy32) atomicAdd(&sacc[1][32u * g + lane], (unsigned long long)(long long)gy32);
+            if (same)
+                sym_group<true>(col, px, py, m, gsm, eps2, g, lane, src, fx, fy, sacc[0], sacc[1]);
+            else
+                sym_group<false>(col, px, py, m, gsm, eps2, g, lane, src, fx, fy, sacc[0], sacc[1]);
         }
         __syncthreads();                             // every j sum of the item is in
         const unsigned long long jx = sacc[0][tid], jy = sacc[1][tid];
