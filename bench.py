@@ -453,23 +453,28 @@ def alloc_roofline(storm, peak):
             "peak_kind": "measured live: K_MICRO_ATOMIC_PEAK probe"}
 
 
-def heap_utilisation(heap_bytes=1 << 30):
-    """Fill a fixed heap with 16-byte objects until allocation fails (Sec. 6.5)."""
+def heap_utilisation(heap_bytes=1 << 30, object_bytes=16, threads=1 << 20):
+    """Fill a fixed heap with objects until allocation fails (Sec. 6.5), `threads`
+    new() per round.  16-byte objects are the microbench type; 64-byte objects a
+    subtype of it with six more 8-byte fields (the Linux-scalability shape of
+    Sec. 6.5: 16,384 threads per round, 64-byte objects, 1 GiB heap)."""
     import torch
     from paper_1810_11765_gb300.apps import Micro
-    m = Micro(heap_bytes, 0x5EED0001, 1 << 20)
+    extra = None if object_bytes == 16 else [8] * ((object_bytes - 16) // 8)
+    m = Micro(heap_bytes, 0x5EED0001, threads, sub_fields=extra, sub_share=1.0)
+    t = m.type if extra is None else m.sub_type
     cap = m.heap.info()["num_blocks"] * 64
     rnd = 0
     while True:
         m.new(rnd)
         rnd += 1
-        if m.heap.get_error() or rnd * (1 << 20) > cap + (1 << 20):
+        if m.heap.get_error() or rnd * threads > cap + threads:
             break
-    live = m.heap.count(m.type)
+    live = m.heap.count(t)
     m.heap.close()
     torch.cuda.empty_cache()
-    return {"heap_bytes": heap_bytes, "objects": live, "object_bytes": 16,
-            "utilisation": live * 16 / heap_bytes}
+    return {"heap_bytes": heap_bytes, "objects": live, "object_bytes": object_bytes,
+            "threads_per_round": threads, "utilisation": live * object_bytes / heap_bytes}
 
 
 def largest_instance(kind, heap_bytes=64 << 20, steps=40, mode=0, lo=64, hi=4096):
@@ -898,6 +903,7 @@ def dsoa_arm(args):
         out["alloc_free_sweep"] = sweep
         out["alloc_roofline"] = alloc_roofline(storm, out["l2_atomic_peak"])
         out["heap_utilisation"] = heap_utilisation()
+        out["heap_utilisation_64b"] = heap_utilisation(object_bytes=64, threads=16384)
         out["bitmapalloc"] = bitmap_legs(flush)
         out["largest_instance"] = largest_instance_leg()
         # --- other apps (plain vs graph) and serving
