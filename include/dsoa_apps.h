@@ -183,10 +183,13 @@ typedef struct {
                                          with DSOA_NBODY_KEYED_FIND, MOVE resets target,
                                          incoming, merged and sets fx to all ones; this
                                          method leaves min(bits(d2) << 32 | id) in fx; CLAIM
-                                         turns it into the target and clears fx             */
+                                         turns it into the target and clears fx.  By
+                                         default each unordered pair is evaluated once (the
+                                         smaller body gets the candidate); with
+                                         DSOA_NBODY_ALL_PAIRS every ordered pair           */
 #define DSOA_NBODY_NONE 0xFFFFFFFFu   /* no target / no incoming proposal                    */
 #define DSOA_NBODY_KEYED_FIND 1u      /* flags: the step uses FIND_TILED                     */
-#define DSOA_NBODY_ALL_PAIRS 2u       /* flags: FORCE_TILED over ordered pairs                */
+#define DSOA_NBODY_ALL_PAIRS 2u       /* flags: FORCE_TILED / FIND_TILED over ordered pairs   */
 typedef struct {
     uint64_t* handle_of;  /* [n_ids] id -> handle; needed by collisions (CLAIM, MERGE read
                              it, the ctor writes it, DELETE clears it); nullable for n-body */
@@ -205,7 +208,7 @@ typedef struct {
     float vscale;         /* initial velocities in [-vscale/2, vscale/2)                  */
     int32_t body_type;
     uint32_t flags;       /* DSOA_NBODY_KEYED_FIND (MOVE and CLAIM for FIND_TILED),
-                             DSOA_NBODY_ALL_PAIRS (FORCE_TILED)                           */
+                             DSOA_NBODY_ALL_PAIRS (FORCE_TILED, FIND_TILED)               */
 } dsoa_nbody_args;
 
 #ifdef __cplusplus

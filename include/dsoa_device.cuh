@@ -633,7 +633,9 @@ __global__ void __maxnreg__(DSOA_DOALL_MAXNREG) dsoa_doall_kernel(dsoa_ctx c, ui
  * which defines the extern "C" launcher (it instantiates dsoa_doall_kernel<M>
  * in the user's library and launches it with the shape the library prepared)
  * and registers it under the id when the library is loaded (the user library
- * links against libdsoa).  The method may allocate (dsoa_new), delete `this`
+ * links against libdsoa).  The registration's return code is kept in
+ * `launcher##_dsoa_registered` (file scope): an id already taken by another
+ * launcher stays with the first one.  The method may allocate (dsoa_new), delete `this`
  * and objects of other types, and read / write any field (dsoa_field,
  * dsoa_column), as the built-in methods do (Sec. 2.1).
  * ------------------------------------------------------------------------ */

@@ -1001,7 +1001,7 @@ static int user_do(dsoa_heap* h, int type, int method_id, const void* args, size
     L.r_dev = h->r_dev[type];
     L.stream = (void*)h->stream;
     rc = fn(&L, args, nb);
-    h->launches++;
+    if (rc == DSOA_OK) h->launches++;
     return rc;
 }
 

@@ -637,6 +637,121 @@ __global__ void __launch_bounds__(256, 5) k_force_sym(dsoa_ctx c, uint32_t t, co
     }
 }
 
+// ---------------------------------------------------------------------------
+// FIND over unordered pairs.  Of two distinct bodies exactly one is "bigger"
+// (heavier, or as heavy with the lower id), and both see the same d2 (the
+// differences of the pair are exact negations), so one evaluation per pair
+// decides whose candidate it is and with which key: the smaller body's, with
+// key bits(d2) << 32 | id of the bigger one.  Pairs farther apart than the merge
+// distance are the rule and cost a distance and a compare; a pair within reach
+// updates the i body's key in a register or the j body's key by a shared
+// atomicMin, folded into the fx field with one global atomicMin per body and
+// item (i keys when the CTA moves to the next row).  Tiles, items and staging
+// as in k_force_sym; no running sums move between lanes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 stage_find(const dsoa_ctx& c, uint32_t t, bool dense, const uint32_t* pre,
+                                             uint32_t r, const unsigned long long* __restrict__ occ,
+                                             const uint32_t* __restrict__ R, uint32_t nb, uint64_t d, bool& ok,
+                                             uint64_t& b, uint32_t& slot) {
+    float4 v = make_float4(0.f, 0.f, 0.f, __uint_as_float(kNone));
+    uint32_t q = 0;
+    slot = 0;
+    ok = d < nb && locate(dense, pre, r, occ, (uint32_t)d, q, slot);
+    if (ok) {
+        b = __ldg(&R[q]);
+        v.x = fld<float>(c, t, b, slot, kPx);
+        v.y = fld<float>(c, t, b, slot, kPy);
+        v.z = fld<float>(c, t, b, slot, kM);
+        v.w = __uint_as_float(fld<uint32_t>(c, t, b, slot, kId));
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_find_sym(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
+                                                  const unsigned long long* __restrict__ occ,
+                                                  const uint32_t* __restrict__ r_dev, dsoa_nbody_args a) {
+    __shared__ float4 sj[2 * kTile];                 // group g at [64 g, 64 g + 64): its 32 bodies twice
+    __shared__ unsigned long long smin[kTile];       // j keys of the item
+    __shared__ uint32_t pre[kDenseMaxR + 1];
+    __shared__ uint32_t wsum[8];
+    const uint32_t r = __ldg(r_dev);
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const bool dense = r <= kDenseMaxR;
+    const uint32_t nb = index_space(dense, r, occ, pre, wsum);
+    const float rc2 = a.rc2;
+    const uint64_t nt = (nb + kTile - 1) / kTile, items = nt * (nt + 1) / 2;
+    const uint64_t wb = items * blockIdx.x / gridDim.x, we = items * (blockIdx.x + 1) / gridDim.x;
+    smin[tid] = ~0ull;
+    uint64_t I = 0, J = 0;
+    if (wb < we) {
+        uint64_t lo = 0, hi = nt;
+        while (hi - lo > 1u) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (tri_start(mid, nt) <= wb) lo = mid; else hi = mid;
+        }
+        I = lo;
+        J = I + (wb - tri_start(I, nt));
+    }
+    uint64_t cur = ~0ull, bi = 0;
+    uint32_t si = 0, id = kNone;
+    bool imine = false;
+    float px = 0.f, py = 0.f, m = 0.f;
+    unsigned long long key = ~0ull;
+    for (uint64_t w = wb; w < we; ++w) {
+        if (I != cur) {
+            if (imine && key != ~0ull) atomicMin(&fld<unsigned long long>(c, t, bi, si, kFx), key);
+            cur = I;
+            const float4 v = stage_find(c, t, dense, pre, r, occ, R, nb, I * kTile + tid, imine, bi, si);
+            px = v.x;
+            py = v.y;
+            m = v.z;
+            id = __float_as_uint(v.w);
+            key = ~0ull;
+        }
+        bool jmine;
+        uint64_t bj = 0;
+        uint32_t sl;
+        const float4 v = stage_find(c, t, dense, pre, r, occ, R, nb, J * kTile + tid, jmine, bj, sl);
+        __syncthreads();                             // readers of the previous tile are done
+        sj[2u * tid - lane] = v;
+        sj[2u * tid - lane + 32u] = v;
+        __syncthreads();
+        const bool diag = I == J;
+#pragma unroll 1
+        for (uint32_t k = 0; k < kSymGroups; ++k) {
+            const uint32_t g = (warp + k) & (kSymGroups - 1u);
+            if (diag && g < warp) continue;
+            const float4* col = sj + 64u * g + lane;
+            const bool own = diag && g == warp;      // own group: the i side of each ordered pair
+#pragma unroll 8
+            for (uint32_t s = own ? 1u : 0u; s < 32u; ++s) {
+                const float4 q = col[s];
+                const float dx = __fsub_rn(q.x, px), dy = __fsub_rn(q.y, py);
+                const float d2 = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+                if (d2 < rc2) {                      // rare: a pair within reach
+                    const uint32_t qid = __float_as_uint(q.w);
+                    const unsigned long long hi = (unsigned long long)__float_as_uint(d2) << 32;
+                    if (q.z > m || (q.z == m && qid < id)) {
+                        const unsigned long long kk = hi | qid;
+                        if (kk < key) key = kk;
+                    } else if (!own) {
+                        atomicMin(&smin[32u * g + ((lane + s) & 31u)], hi | id);
+                    }
+                }
+            }
+        }
+        __syncthreads();                             // every j key of the item is in
+        const unsigned long long jk = smin[tid];
+        smin[tid] = ~0ull;
+        if (jmine && jk != ~0ull) atomicMin(&fld<unsigned long long>(c, t, bj, sl, kFx), jk);
+        if (++J == nt) {
+            ++I;
+            J = I;
+        }
+    }
+    if (imine && key != ~0ull) atomicMin(&fld<unsigned long long>(c, t, bi, si, kFx), key);
+}
+
 // Body's field sizes in bytes (id, px, py, vx, vy, m, fx, fy, target, incoming, merged)
 constexpr uint32_t kFieldBytes[11] = {4, 4, 4, 4, 4, 4, 8, 8, 4, 4, 4};
 
@@ -688,9 +803,9 @@ int dsoa_nbody_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
             if (method == DSOA_M_NBODY_FORCE_TILED && !(args.eps2 >= 0x1p-80f)) return DSOA_ERR_INVALID_ARG;
             rc = dsoa_prepare_doall(h, type);
             if (rc) return rc;
-            auto* k = method == DSOA_M_COLL_FIND_TILED ? &k_pairs_tiled<FindOp>
-                      : (args.flags & DSOA_NBODY_ALL_PAIRS) ? &k_pairs_tiled<ForceOp>
-                                                            : &k_force_sym;
+            const bool all_pairs = (args.flags & DSOA_NBODY_ALL_PAIRS) != 0u;
+            auto* k = method == DSOA_M_COLL_FIND_TILED ? (all_pairs ? &k_pairs_tiled<FindOp> : &k_find_sym)
+                                                       : (all_pairs ? &k_pairs_tiled<ForceOp> : &k_force_sym);
             const unsigned grid = (unsigned)(dsoa_resident_ctas(reinterpret_cast<const void*>(k), 256) * h->num_sms);
             k<<<grid ? grid : 1u, 256, 0, h->stream>>>(dsoa_launch_ctx(h), (uint32_t)type, h->R[type], h->Rocc[type],
                                                      h->r_dev[type], args);

@@ -29,11 +29,11 @@ def cfg(**kw):
     return inputs.NBodyConfig(**{k: v for k, v in d.items() if k in inputs.NBodyConfig.__dataclass_fields__})
 
 
-def world(c, collide, tiled, heap_bytes=64 << 20):
+def world(c, collide, tiled, heap_bytes=64 << 20, all_pairs=False):
     from paper_1810_11765_gb300 import dsoa as D
     from paper_1810_11765_gb300.apps import NBodyWorld
     heap = D.Heap(heap_bytes)
-    w = NBodyWorld(heap, c, collide=collide, tiled=tiled)
+    w = NBodyWorld(heap, c, collide=collide, tiled=tiled, all_pairs=all_pairs)
     heap.freeze()
     return heap, w
 
@@ -62,11 +62,12 @@ def test_nbody_bit_exact(n, tiled):
     heap.close()
 
 
-@pytest.mark.parametrize("tiled", [False, True])
-def test_collisions_bit_exact_per_step(tiled):
+@pytest.mark.parametrize("tiled,all_pairs", [(False, False), (True, False), (True, True)])
+def test_collisions_bit_exact_per_step(tiled, all_pairs):
+    """FIND by device_do, by the unordered-pair kernel and by the ordered-pair one."""
     c = cfg(seed=7, G=2.0 ** -24)
     n, steps = 2000, 20
-    heap, w = world(c, True, tiled)
+    heap, w = world(c, True, tiled, all_pairs=all_pairs)
     w.create(n)
     _, _, counts, _ = oracle_run(c, n, steps, True)
     for k in range(steps):
@@ -81,6 +82,55 @@ def test_collisions_bit_exact_per_step(tiled):
     assert all(v == 0 for v in heap.check().values())
     host = host_check(heap, 1)
     assert all(v == 0 for v in host["violations"].values()), host
+    heap.close()
+
+
+@pytest.mark.parametrize("all_pairs", [False, True])
+def test_collisions_with_many_bodies_in_reach(all_pairs):
+    """A merge distance of 1/8 gives every body dozens of candidates: the keys of
+    both bodies of a pair (register and shared-memory minima) must reproduce the
+    oracle's targets, merges and deletions step by step."""
+    c = cfg(seed=31, G=2.0 ** -24, rc2=2.0 ** -6)
+    n, steps = 1500, 6
+    heap, w = world(c, True, True, all_pairs=all_pairs)
+    w.create(n)
+    _, _, counts, _ = oracle_run(c, n, steps, True)
+    for k in range(steps):
+        w.step()
+        assert w.count() == counts[k + 1], k
+    st, alive = w.read()
+    ref, ref_alive, _, _ = oracle_run(c, n, steps, True)
+    assert counts[-1] < 0.8 * n
+    assert np.array_equal(alive, ref_alive)
+    assert np.array_equal(st.view(np.uint32), ref.view(np.uint32))
+    assert heap.get_error() == 0
+    heap.close()
+
+
+def test_collisions_over_four_slot_blocks_indexed_by_slot():
+    """17,000 bodies in blocks of four (4,250 listed blocks, beyond dense
+    indexing): FORCE and FIND stage empty slots as mass-0 placeholders at the
+    origin, which must never become a target; two collision steps equal the
+    oracle's."""
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import NBodyWorld
+    c = cfg(seed=5, G=2.0 ** -24, rc2=2.0 ** -12)
+    n, steps = 17000, 2
+    heap = D.Heap(64 << 20)
+    heap.register_type([4])
+    heap.set_capacity_mode(D.CAPACITY_PER_TYPE)
+    w = NBodyWorld(heap, c, collide=True, tiled=True)
+    heap.freeze()
+    assert heap.capacity(w.type) == 4
+    w.create(n)
+    for _ in range(steps):
+        w.step()
+    st, alive = w.read()
+    ref, ref_alive, counts, _ = oracle_run(c, n, steps, True)
+    assert counts[-1] < n
+    assert np.array_equal(alive, ref_alive)
+    assert np.array_equal(st.view(np.uint32), ref.view(np.uint32))
+    assert heap.get_error() == 0
     heap.close()
 
 
