@@ -14,6 +14,7 @@
 // integers of (i, j).
 #include "dsoa_internal.cuh"
 #include "rng.cuh"
+#include "rn_math.cuh"
 
 namespace {
 
@@ -483,7 +484,9 @@ __device__ __forceinline__ uint64_t tri_start(uint64_t I, uint64_t nt) { return 
 // no overflow) and folded into the 64-bit sums once; a step with a larger term
 // adds its terms in 64 bits directly (the j terms by shared atomics).  kSame:
 // the two coefficients of every pair are known to be equal, (G S m_i) m_j =
-// (G S m_j) m_i exactly, so the j term is the negated i term.
+// (G S m_j) m_i exactly, so the j term is the negated i term, and every
+// coordinate is below 2^62 in magnitude, so d2 is finite and in [eps2, FLT_MAX]
+// where dsoa_rcp_sqrt_rn gives the very bits of the two rounded intrinsics.
 template <bool kSame>
 __device__ __forceinline__ void sym_group(const float4* col, float px, float py, float m, float gsm, float eps2,
                                           uint32_t g, uint32_t lane, uint32_t src, unsigned long long& fx,
@@ -494,7 +497,7 @@ __device__ __forceinline__ void sym_group(const float4* col, float px, float py,
         const float4 q = col[s];
         const float dx = __fsub_rn(q.x, px), dy = __fsub_rn(q.y, py);
         const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), eps2);
-        const float inv = __frcp_rn(__fsqrt_rn(d2));
+        const float inv = kSame ? dsoa_rcp_sqrt_rn(d2) : __frcp_rn(__fsqrt_rn(d2));
         const float inv3 = __fmul_rn(__fmul_rn(inv, inv), inv);
         const float kij = __fmul_rn(__fmul_rn(gsm, q.z), inv3);
         const float ax = __fmul_rn(kij, dx), ay = __fmul_rn(kij, dy);
@@ -541,6 +544,8 @@ __device__ __forceinline__ void sym_group(const float4* col, float px, float py,
 
 // an integer mass in [0, 2^12]: products of two are exact in binary32
 __device__ __forceinline__ bool small_integer(float m) { return m >= 0.0f && m <= 0x1p12f && m == truncf(m); }
+// coordinates below 2^62 in magnitude: squared differences stay finite
+__device__ __forceinline__ bool bounded(float4 v) { return fabsf(v.x) < 0x1p62f && fabsf(v.y) < 0x1p62f; }
 
 __global__ void __launch_bounds__(256, 5) k_force_sym(dsoa_ctx c, uint32_t t, const uint32_t* __restrict__ R,
                                                    const unsigned long long* __restrict__ occ,
@@ -597,8 +602,10 @@ __global__ void __launch_bounds__(256, 5) k_force_sym(dsoa_ctx c, uint32_t t, co
         sj[2u * tid - lane] = v;                     // = 64 warp + lane
         sj[2u * tid - lane + 32u] = v;
         // G S a power of two and every mass of both tiles a small integer: the
-        // products (G S m_i) m_j and (G S m_j) m_i are exact, hence equal
-        const bool same = __syncthreads_and(small_integer(m) && small_integer(v.z)) && gs_pow2;
+        // products (G S m_i) m_j and (G S m_j) m_i are exact, hence equal; with
+        // all coordinates of both tiles bounded, d2 is finite
+        const bool same = __syncthreads_and(small_integer(m) && small_integer(v.z) &&
+                                            bounded(make_float4(px, py, 0.f, 0.f)) && bounded(v)) && gs_pow2;
         const bool diag = I == J;
 #pragma unroll 1
         for (uint32_t k = 0; k < kSymGroups; ++k) {

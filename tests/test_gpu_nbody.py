@@ -239,6 +239,26 @@ def test_force_over_four_slot_blocks(n):
         assert np.array_equal(_forces(c, init, True, all_pairs, four_slot_blocks=True), want), all_pairs
 
 
+def test_inverse_root_sequence_is_exact_on_its_whole_domain(tmp_path):
+    """The FORCE kernel's fused-multiply-add sequence for 1/sqrt(d2) gives the bits
+    of RN(1 / RN(sqrt d2)) (what the oracle computes) for every binary32 d2 in
+    [2^-80, FLT_MAX]: all 1.74 G inputs, compared on the GPU."""
+    import ctypes
+    import os
+    import subprocess
+    from conftest import ROOT
+    from paper_1810_11765_gb300 import build
+    lib = tmp_path / "libinvroot.so"
+    subprocess.run([build._nvcc(), *build.ARCH, "-O3", "-I", build.CSRC, "-shared", "-Xcompiler", "-fPIC",
+                    "-cudart", "shared", "-o", str(lib), os.path.join(ROOT, "tests", "inv_root_check.cu")],
+                   check=True)
+    f = ctypes.CDLL(str(lib)).inv_root_mismatches
+    f.argtypes, f.restype = [ctypes.c_uint32, ctypes.c_uint32], ctypes.c_longlong
+    lo = int(np.float32(2.0 ** -80).view(np.uint32))
+    hi = int(np.float32(np.inf).view(np.uint32))          # exclusive: up to FLT_MAX
+    assert f(lo, hi) == 0
+
+
 def test_collision_graph_replay_matches_plain():
     """A collision step (one enumeration, six do-alls) captured as a CUDA graph and
     replayed gives the plain steps' state, bit for bit."""
