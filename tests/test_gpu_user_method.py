@@ -139,3 +139,27 @@ def test_registration_and_dispatch_errors(user_lib):
     assert e.value.code == INVALID_ARG
     assert m.heap.get_error() == 0
     m.heap.close()
+
+
+def test_user_method_covers_subtypes(user_lib):
+    """A user do-all on a base type runs on the objects of its subtypes too (one
+    snapshot, one launch per type): the microbench split over a base and a
+    subtype, scaled by the user's method, equals the oracle."""
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import Micro
+    n, rounds = 4000, 4
+    ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
+    heap = D.Heap(64 << 20)
+    heap.set_capacity_mode(D.CAPACITY_PER_TYPE)
+    m = Micro(0, SEED, n, heap=heap, sub_fields=[8, 8], sub_share=0.6)
+    for r in range(rounds):
+        m.new(r)
+        heap.parallel_do(m.type, SCALE, UserArgs())
+        m.delete(r)
+    assert heap.count(m.sub_type) > 0
+    x, live = m.gather(n * rounds)
+    assert np.array_equal(live, live_ref)
+    sel = live_ref.astype(bool)
+    assert np.array_equal(x[sel].view(np.uint32), x_ref[sel].view(np.uint32))
+    assert heap.get_error() == 0
+    heap.close()
