@@ -215,11 +215,15 @@ int dsoa_enumerate_many(dsoa_heap* h, const int* types_host, int ntypes);
  * heap's stream.  Not allowed during stream capture. */
 int dsoa_count(dsoa_heap* h, int type, uint64_t* out_host);
 
-/* Same, written to device memory `out_dev` (uint64); graph-capturable. */
+/* Same, stored to `out_dev` (uint64) by the kernel; graph-capturable.  out_dev
+ * is any address the device may write: device memory, or pinned host memory
+ * mapped into the device's address space (the value then reaches the host
+ * without a copy); it needs no initialisation. */
 int dsoa_count_async(dsoa_heap* h, int type, uint64_t* out_dev);
 
 /* Live objects of `ntypes` distinct types (ids at types_host) in one launch:
- * out_dev[q] (uint64) = live objects of types_host[q].  Graph-capturable. */
+ * out_dev[q] (uint64) = live objects of types_host[q], stored as by
+ * dsoa_count_async.  Graph-capturable. */
 int dsoa_count_many_async(dsoa_heap* h, const int* types_host, int ntypes, uint64_t* out_dev);
 
 /* Number of free blocks (popcount of the free-block bitmap) to `out_dev`

@@ -59,6 +59,8 @@ struct dsoa_heap {
     int scan_tiles_per_cta = 0;      // 0 = single-pass look-back; 1, 2 = tile-count + compaction kernels
     bool stream_enum = false;        // enumerate inside methods that create no objects of their own type
     uint32_t* stream_ctl = nullptr;  // ticket, finished CTAs, R length of the streamed do-all
+    unsigned long long* count_acc = nullptr;  // [DSOA_MAX_TYPES] partial counts of k_count_many (zero between launches)
+    uint32_t* count_ticket = nullptr;         // finished CTAs of k_count_many (zero between launches)
     unsigned long long* lb_state = nullptr;  // [ntypes][tiles] look-back state words (epoch, status, value)
     uint32_t* lb_ctl = nullptr;              // [ntypes][4]: ticket, done counter, epoch of the look-back kernel
     int lb_fits = -1;                        // look-back CTAs resident per SM (-1: not queried yet)

@@ -516,54 +516,53 @@ __global__ void __launch_bounds__(64) k_enum_lookback_multi(dsoa_ctx c, uint64_t
 
 // Live objects of one type: warp per tile; for every non-empty level-0
 // container the warp reads the 64 slot words coalesced.
-__global__ void k_count(dsoa_ctx c, uint32_t b, uint64_t tiles, unsigned long long* out) {
-    const uint32_t lane = threadIdx.x & 31u, wpc = blockDim.x >> 5;
-    const unsigned long long* L0 = dsoa_level(c, b, 0);
-    const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, b, 1) : nullptr;
-    uint32_t cnt = 0;
-    for (uint64_t t = (uint64_t)blockIdx.x * wpc + (threadIdx.x >> 5); t < tiles;
-         t += (uint64_t)gridDim.x * wpc) {
-        unsigned long long sel = L1 ? L1[t] : 1ull;
-        for (; sel; sel &= sel - 1ull) {
-            const uint64_t wi = t * 64 + (uint64_t)(__ffsll((long long)sel) - 1);
-            if (wi >= c.lvl_words[0]) break;
-            const unsigned long long w = L0[wi];
-            const uint64_t bid = wi * 64 + lane;
-            if ((w >> lane) & 1ull) cnt += __popcll(~c.slot[bid]);
-            if ((w >> (lane + 32)) & 1ull) cnt += __popcll(~c.slot[bid + 32]);
-        }
-    }
-    cnt = warp_sum(cnt);
-    if (lane == 0 && cnt) atomicAdd(out, (unsigned long long)cnt);
-}
-
-// Live objects of several types in one launch: CTA-tiles over (type, level-1
-// tile) pairs, the same per-tile work as k_count, into out[q] (pre-zeroed).
+// Live objects of several types in one launch, stored to out[q]: one warp per
+// level-0 word of a type's allocated-block bitmap (a word that is zero costs one
+// load), its lanes popcount the slot words of the word's blocks (two each) in
+// parallel, so the two dependent loads of every word run concurrently across the
+// grid.  Counts meet in shared memory, then in acc (one atomic per CTA and
+// type); the CTA that finishes last stores the totals to out and leaves acc and
+// the ticket at zero for the next launch.  Plain stores to out, no pre-zeroing:
+// out may be device memory or mapped pinned host memory.
 struct CountBatch {
     uint32_t n;
     uint32_t b[DSOA_MAX_TYPES];
 };
-__global__ void k_count_many(dsoa_ctx c, uint64_t tiles, CountBatch cb, unsigned long long* out) {
+__global__ void k_count_many(dsoa_ctx c, CountBatch cb, unsigned long long* out, unsigned long long* acc,
+                             uint32_t* ticket) {
+    __shared__ unsigned long long s_cnt[DSOA_MAX_TYPES];
+    __shared__ bool s_last;
     const uint32_t lane = threadIdx.x & 31u, wpc = blockDim.x >> 5;
-    const uint64_t total = tiles * cb.n;
+    if (threadIdx.x < DSOA_MAX_TYPES) s_cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    const uint64_t words = c.lvl_words[0], total = words * cb.n;
+    uint32_t q_cur = 0, cnt = 0;
     for (uint64_t g = (uint64_t)blockIdx.x * wpc + (threadIdx.x >> 5); g < total; g += (uint64_t)gridDim.x * wpc) {
-        const uint32_t q = (uint32_t)(g / tiles);
-        const uint64_t t = g - (uint64_t)q * tiles;
-        const unsigned long long* L0 = dsoa_level(c, cb.b[q], 0);
-        const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, cb.b[q], 1) : nullptr;
-        uint32_t cnt = 0;
-        unsigned long long sel = L1 ? L1[t] : 1ull;
-        for (; sel; sel &= sel - 1ull) {
-            const uint64_t wi = t * 64 + (uint64_t)(__ffsll((long long)sel) - 1);
-            if (wi >= c.lvl_words[0]) break;
-            const unsigned long long w = L0[wi];
-            const uint64_t bid = wi * 64 + lane;
-            if ((w >> lane) & 1ull) cnt += __popcll(~c.slot[bid]);
-            if ((w >> (lane + 32)) & 1ull) cnt += __popcll(~c.slot[bid + 32]);
+        const uint32_t q = (uint32_t)(g / words);
+        const uint64_t wi = g - (uint64_t)q * words;
+        if (q != q_cur) {                          /* warp-uniform */
+            cnt = warp_sum(cnt);
+            if (lane == 0 && cnt) atomicAdd(&s_cnt[q_cur], (unsigned long long)cnt);
+            q_cur = q;
+            cnt = 0;
         }
-        cnt = warp_sum(cnt);
-        if (lane == 0 && cnt) atomicAdd(&out[q], (unsigned long long)cnt);
+        const unsigned long long w = dsoa_level(c, cb.b[q], 0)[wi];
+        const uint64_t bid = wi * 64 + lane;
+        if ((w >> lane) & 1ull) cnt += __popcll(~c.slot[bid]);
+        if ((w >> (lane + 32)) & 1ull) cnt += __popcll(~c.slot[bid + 32]);
     }
+    cnt = warp_sum(cnt);
+    if (lane == 0 && cnt) atomicAdd(&s_cnt[q_cur], (unsigned long long)cnt);
+    __syncthreads();
+    if (threadIdx.x < cb.n && s_cnt[threadIdx.x]) atomicAdd(&acc[threadIdx.x], s_cnt[threadIdx.x]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < cb.n) out[threadIdx.x] = atomicExch(&acc[threadIdx.x], 0ull);
+    if (threadIdx.x == 0) atomicExch(ticket, 0u);
 }
 
 __global__ void k_popc_level0(dsoa_ctx c, uint32_t b, unsigned long long* out) {
@@ -901,6 +900,8 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     h->done = (uint32_t*)(small + 1);
     h->scratch64 = (unsigned long long*)(small + 32);
     h->stream_ctl = (uint32_t*)(small + 44);  // [3] of the streamed do-all
+    h->count_acc = (unsigned long long*)(small + 46);  // [16] words 46..61
+    h->count_ticket = (uint32_t*)(small + 62);
     c.M = L.M;
     c.bm_stride = L.bm_stride;
     for (int l = 0; l < DSOA_MAX_LEVELS; ++l) { c.lvl_off[l] = L.lvl_off[l]; c.lvl_words[l] = L.lvl_words[l]; }
@@ -1114,13 +1115,7 @@ int dsoa_enumerate_many(dsoa_heap* h, const int* types_host, int ntypes) {
 }
 
 int dsoa_count_async(dsoa_heap* h, int type, uint64_t* out_dev) {
-    int rc = dsoa_ensure_frozen(h);
-    if (rc) return rc;
-    if (type < 0 || type >= h->ntypes || !out_dev) return DSOA_ERR_INVALID_ARG;
-    DSOA_CUDA_TRY(cudaMemsetAsync(out_dev, 0, 8, h->stream));
-    const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((h->tiles + 7) / 8, (uint64_t)h->num_sms * 8));
-    k_count<<<g, 256, 0, h->stream>>>(h->ctx, dsoa_bm_alloc((uint32_t)type), h->tiles, (unsigned long long*)out_dev);
-    return dsoa_check_launch(h);
+    return dsoa_count_many_async(h, &type, 1, out_dev);
 }
 
 int dsoa_count_many_async(dsoa_heap* h, const int* types_host, int ntypes, uint64_t* out_dev) {
@@ -1134,10 +1129,9 @@ int dsoa_count_many_async(dsoa_heap* h, const int* types_host, int ntypes, uint6
         if (types_host[q] < 0 || types_host[q] >= h->ntypes) return DSOA_ERR_INVALID_ARG;
         cb.b[q] = dsoa_bm_alloc((uint32_t)types_host[q]);
     }
-    DSOA_CUDA_TRY(cudaMemsetAsync(out_dev, 0, 8 * (size_t)ntypes, h->stream));
-    const uint64_t warps = h->tiles * (uint64_t)ntypes;
+    const uint64_t warps = h->ctx.lvl_words[0] * (uint64_t)ntypes;
     const unsigned g = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 7) / 8, (uint64_t)h->num_sms * 8));
-    k_count_many<<<g, 256, 0, h->stream>>>(h->ctx, h->tiles, cb, (unsigned long long*)out_dev);
+    k_count_many<<<g, 256, 0, h->stream>>>(h->ctx, cb, (unsigned long long*)out_dev, h->count_acc, h->count_ticket);
     return dsoa_check_launch(h);
 }
 

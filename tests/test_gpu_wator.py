@@ -252,3 +252,30 @@ def test_full_config_in_the_benchmarked_launch_configuration():
         assert all(v == 0 for v in heap.check().values())
         g.close()
         heap.close()
+
+
+def test_counts_stored_into_mapped_pinned_host_memory():
+    """dsoa_count_many_async stores its totals (no pre-zeroing, no copy) into any
+    device-writable address: a captured step writes each step's populations
+    straight into pinned host memory, repeatedly, and they equal the oracle's."""
+    import torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        heap, w = world(64 << 20)
+        w.add(128, 96, 23)
+        host = torch.full((2,), -1, dtype=torch.int64).pin_memory()
+        heap.graph_begin()
+        w.step()
+        heap.count_many_async([w.fish_type, w.shark_type], host)
+        g = heap.graph_end()
+        _, st = oracle.wator_run(128, 96, 15, seed=23)
+        for k in range(15):
+            g.launch()
+            s.synchronize()
+            assert host.tolist() == [st[k]["fish"], st[k]["sharks"]], k
+        dev = torch.full((3,), 7, dtype=torch.int64, device="cuda")
+        heap.count_many_async([w.shark_type, w.fish_type], dev[1:])   # stored, not added
+        assert dev.tolist() == [7, st[14]["sharks"], st[14]["fish"]]
+        assert heap.get_error() == 0
+        g.close()
+        heap.close()
