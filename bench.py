@@ -188,14 +188,14 @@ WATOR_KERNELS = [  # (type attr, method, reuses the previous snapshot, algorithm
     ("fish_type", "M_WATOR_FISH_CHOOSE", False, 24),
     ("fish_type", "M_WATOR_FISH_MOVE", True, 20),
     ("shark_type", "M_WATOR_SHARK_CHOOSE", False, 28),
-    ("shark_type", "M_WATOR_SHARK_MOVE", True, 32),
+    ("shark_type", "M_WATOR_SHARK_MOVE_ADVANCE", True, 32),
 ]
 WATOR_KERNELS_DEFERRED = [  # the same step with births created by the births kernel
     ("fish_type", "M_WATOR_FISH_CHOOSE", False, 24),
     ("fish_type", "M_WATOR_FISH_MOVE_DEFER", True, 20),
     ("fish_type", "K_WATOR_BIRTHS", None, 0),
     ("shark_type", "M_WATOR_SHARK_CHOOSE", False, 28),
-    ("shark_type", "M_WATOR_SHARK_MOVE", True, 32),
+    ("shark_type", "M_WATOR_SHARK_MOVE_ADVANCE", True, 32),
 ]
 
 
@@ -238,7 +238,6 @@ def wator_kernel_profile(seed, warmup, steps, flush, launch=None):
             r["ms"].append(e0.elapsed_time(e1))
             r["bytes"].append(alg)
             r["units"].append(n_agents)
-        heap.run_kernel(D.K_WATOR_ADVANCE, 1, a)
     torch.cuda.synchronize()
     heap.close()
     return acc

@@ -83,6 +83,8 @@ typedef struct {
 #define DSOA_M_GOL_DECIDE 203    /* Cell: dead with count 3 -> new Alive; count = 0       */
 #define DSOA_M_GOL_READ 204      /* Cell: occ[cell] = alive                               */
 #define DSOA_M_GOL_KILL 205      /* Cell or Alive of a KILL instance: delete this         */
+#define DSOA_M_GOL_DECIDE_ADVANCE 206 /* DECIDE, and t += 1 for RUN instances (the same as
+                                        K_GOL_ADVANCE after it, without its launch)        */
 #define DSOA_K_GOL_ADVANCE 250   /* n = n_inst: t += 1 for RUN instances                  */
 typedef struct {
     dsoa_inst* inst;     /* [n_inst] device table                                   */
@@ -101,6 +103,9 @@ typedef struct {
 #define DSOA_M_WATOR_KILL 305          /* agent of a KILL instance: delete this          */
 #define DSOA_M_WATOR_FISH_MOVE_DEFER 306 /* FISH_MOVE whose newborns are only marked (occ 3
                                           at the old cell); K_WATOR_BIRTHS creates them  */
+#define DSOA_M_WATOR_SHARK_MOVE_ADVANCE 307 /* SHARK_MOVE, and t += 1 for RUN instances (the
+                                               same as K_WATOR_ADVANCE after it, without
+                                               its launch)                                 */
 #define DSOA_K_WATOR_INIT 350          /* n = w*h of `target`: agents from `init` (nullable,
                                           0/1/2) or Philox(seed; 0xFFFFFFFF, c, 0, 0) vs
                                           0.30 / 0.35 thresholds                          */

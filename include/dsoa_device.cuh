@@ -588,6 +588,22 @@ __device__ __forceinline__ F& dsoa_field(const dsoa_ctx& c, dsoa_obj h, uint32_t
     return dsoa_column<F>(c, dsoa_h_type(h), dsoa_h_block(h), field)[dsoa_h_slot(h)];
 }
 
+/* A method may carry per-launch work that reads nothing the do-all writes:
+ *   static __device__ void prologue(const dsoa_ctx&, const Args&);
+ * CTA 0 of its do-all runs it (all threads of that CTA) before taking objects,
+ * which spares the step a launch of its own (e.g. advancing the instances' step
+ * counters in a kernel that does not read them). */
+template <class M, class = void>
+struct dsoa_has_prologue { static constexpr bool value = false; };
+template <class M>
+struct dsoa_has_prologue<M, decltype((void)&M::prologue, void())> { static constexpr bool value = true; };
+template <class M>
+__device__ __forceinline__ void dsoa_run_prologue(const dsoa_ctx& c, const typename M::Args& a) {
+    if constexpr (dsoa_has_prologue<M>::value) {
+        if (blockIdx.x == 0) M::prologue(c, a);
+    }
+}
+
 /* ------------------------------------------------------------------------
  * Parallel do-all kernel (Sec. 3.7, Fig. 6-7).  With G = 1 (the paper's
  * assignment) 64 consecutive threads serve one block of R: thread tid serves
@@ -605,6 +621,7 @@ __global__ void __maxnreg__(DSOA_DOALL_MAXNREG) dsoa_doall_kernel(dsoa_ctx c, ui
     constexpr uint32_t TPB = 64u / G;                          /* threads per block */
     dsoa_pdl_wait();
     dsoa_pdl_release();
+    dsoa_run_prologue<M>(c, args);
     const uint64_t n = (uint64_t)gridDim.x * blockDim.x;      /* multiple of 64 */
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint32_t s0 = (uint32_t)(tid % TPB);
@@ -701,6 +718,7 @@ struct dsoa_streamable<M, decltype((void)M::kNoNewOfOwnType, void())> {
     static constexpr bool value = M::kNoNewOfOwnType;
 };
 
+
 template <class M, int G = 1>
 __global__ void __maxnreg__(DSOA_DOALL_MAXNREG) dsoa_doall_stream_kernel(dsoa_ctx c, uint32_t t,
                                   uint32_t* __restrict__ R, unsigned long long* __restrict__ occ,
@@ -720,6 +738,7 @@ __global__ void __maxnreg__(DSOA_DOALL_MAXNREG) dsoa_doall_stream_kernel(dsoa_ct
     const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, b, 1) : nullptr;
     const uint32_t tid = threadIdx.x;
     const uint32_t grp = tid / TPB, ngrp = blockDim.x / TPB, s0 = tid % TPB;
+    dsoa_run_prologue<M>(c, args);
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(&ctl[0], 1u);
         __syncthreads();
@@ -858,6 +877,7 @@ __global__ void __launch_bounds__(512) dsoa_doall_fused_kernel(dsoa_ctx c, uint3
     const unsigned long long* L1 = c.nlevels >= 2 ? dsoa_level(c, b, 1) : nullptr;
     const uint64_t t_lo = tiles * blockIdx.x / nb, t_hi = tiles * (blockIdx.x + 1) / nb;
     uint32_t* agg = c.grid_scratch;
+    dsoa_run_prologue<M>(c, args);
     /* phase 1: count this CTA's tiles (warp per tile) */
     uint32_t mine = 0;
     for (uint64_t tt = t_lo + warp; tt < t_hi; tt += nwarps) {

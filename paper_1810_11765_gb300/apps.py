@@ -187,11 +187,11 @@ class GolWorld:
         else:
             self.heap.parallel_do(self.alive_type, D.M_GOL_SPREAD, a)
         self.heap.parallel_do_enumerated(self.alive_type, D.M_GOL_REAP, a)
+        # Decide also advances the instances' generation counters (CTA 0)
         if batch:
-            self.heap.parallel_do_enumerated(self.cell_type, D.M_GOL_DECIDE, a)
+            self.heap.parallel_do_enumerated(self.cell_type, D.M_GOL_DECIDE_ADVANCE, a)
         else:
-            self.heap.parallel_do(self.cell_type, D.M_GOL_DECIDE, a)
-        self.heap.run_kernel(D.K_GOL_ADVANCE, self.table.capacity, a)
+            self.heap.parallel_do(self.cell_type, D.M_GOL_DECIDE_ADVANCE, a)
 
     def read(self, slot: int) -> np.ndarray:
         self.heap.parallel_do(self.cell_type, D.M_GOL_READ, self.args())
@@ -273,8 +273,8 @@ class WatorWorld:
             self.heap.parallel_do_enumerated(self.shark_type, D.M_WATOR_SHARK_CHOOSE, a)
         else:
             self.heap.parallel_do(self.shark_type, D.M_WATOR_SHARK_CHOOSE, a)
-        self.heap.parallel_do_enumerated(self.shark_type, D.M_WATOR_SHARK_MOVE, a)
-        self.heap.run_kernel(D.K_WATOR_ADVANCE, self.table.capacity, a)
+        # Shark.move also advances the instances' step counters (CTA 0)
+        self.heap.parallel_do_enumerated(self.shark_type, D.M_WATOR_SHARK_MOVE_ADVANCE, a)
 
     def read(self, slot: int) -> np.ndarray:
         e = self.table.host[slot]

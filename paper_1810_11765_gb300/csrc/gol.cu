@@ -106,6 +106,16 @@ struct Decide {
     }
 };
 
+// Cell.decide that also advances the step counter of every running instance
+// (no method of a generation reads it): CTA 0 does it in its prologue, so the
+// generation needs no launch of its own for it.
+struct DecideAdvance : Decide {
+    static __device__ void prologue(const dsoa_ctx&, const Args& a) {
+        for (uint32_t i = threadIdx.x; i < a.n_inst; i += blockDim.x)
+            if (a.inst[i].state == DSOA_INST_RUN) a.inst[i].t += 1u;
+    }
+};
+
 struct Read {
     using Args = dsoa_gol_args;
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
@@ -152,6 +162,7 @@ int dsoa_gol_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) {
         case DSOA_M_GOL_SPREAD: return dsoa_run_doall<Spread>(h, type, args);
         case DSOA_M_GOL_REAP: return dsoa_run_doall<Reap>(h, type, args);
         case DSOA_M_GOL_DECIDE: return dsoa_run_doall<Decide>(h, type, args);
+        case DSOA_M_GOL_DECIDE_ADVANCE: return dsoa_run_doall<DecideAdvance>(h, type, args);
         case DSOA_M_GOL_READ: return dsoa_run_doall<Read>(h, type, args);
         case DSOA_M_GOL_KILL: return dsoa_run_doall<Kill>(h, type, args);
         default: return DSOA_ERR_UNKNOWN_METHOD;

@@ -218,6 +218,16 @@ struct SharkMove {
     }
 };
 
+// Shark.move that also advances the step counter of every running instance: the
+// step's last kernel reads no counter (only the choose methods draw), so CTA 0
+// advances them in its prologue and the step needs no launch of its own for it.
+struct SharkMoveAdvance : SharkMove {
+    static __device__ void prologue(const dsoa_ctx&, const Args& a) {
+        for (uint32_t i = threadIdx.x; i < a.n_inst; i += blockDim.x)
+            if (a.inst[i].state == DSOA_INST_RUN) a.inst[i].t += 1u;
+    }
+};
+
 struct Kill {
     using Args = dsoa_wator_args;
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
@@ -348,6 +358,8 @@ int dsoa_wator_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) 
             return fish ? dsoa_run_doall<FishMoveDeferred>(h, type, args) : DSOA_ERR_INVALID_ARG;
         case DSOA_M_WATOR_SHARK_CHOOSE: return shark ? dsoa_run_doall<SharkChoose>(h, type, args) : DSOA_ERR_INVALID_ARG;
         case DSOA_M_WATOR_SHARK_MOVE: return shark ? dsoa_run_doall<SharkMove>(h, type, args) : DSOA_ERR_INVALID_ARG;
+        case DSOA_M_WATOR_SHARK_MOVE_ADVANCE:
+            return shark ? dsoa_run_doall<SharkMoveAdvance>(h, type, args) : DSOA_ERR_INVALID_ARG;
         case DSOA_M_WATOR_KILL: return (fish || shark) ? dsoa_run_doall<Kill>(h, type, args) : DSOA_ERR_INVALID_ARG;
         default: return DSOA_ERR_UNKNOWN_METHOD;
     }

@@ -38,6 +38,7 @@ K_GOL_ADVANCE = 250
 M_WATOR_FISH_CHOOSE, M_WATOR_FISH_MOVE, M_WATOR_SHARK_CHOOSE, M_WATOR_SHARK_MOVE = 301, 302, 303, 304
 M_WATOR_KILL, K_WATOR_INIT, K_WATOR_ADVANCE = 305, 350, 351
 M_WATOR_FISH_MOVE_DEFER, K_WATOR_BIRTHS = 306, 352
+M_GOL_DECIDE_ADVANCE, M_WATOR_SHARK_MOVE_ADVANCE = 206, 307
 M_TRAFFIC_MOVE, M_TRAFFIC_READ = 401, 402
 K_TRAFFIC_INIT, K_TRAFFIC_CLEAR, K_TRAFFIC_ONRAMP, K_TRAFFIC_ADVANCE = 450, 451, 452, 453
 C_NBODY, M_NBODY_FORCE, M_NBODY_MOVE = 500, 501, 502

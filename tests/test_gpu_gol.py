@@ -121,3 +121,30 @@ def test_launch_modes_graph_captured(launch, flags):
     assert alive == alive_ref[-1]
     assert heap.get_error() == 0
     g.close()
+
+
+def test_separate_advance_launch_equals_folded():
+    """The generation counter advanced by its own kernel (K_GOL_ADVANCE) or by CTA 0
+    of Cell.decide (DECIDE_ADVANCE, the default): the same generations."""
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import GolWorld
+
+    class Separate(GolWorld):
+        def step(self):
+            a = self.args()
+            self.heap.parallel_do(self.alive_type, D.M_GOL_SPREAD, a)
+            self.heap.parallel_do_enumerated(self.alive_type, D.M_GOL_REAP, a)
+            self.heap.parallel_do(self.cell_type, D.M_GOL_DECIDE, a)
+            self.heap.run_kernel(D.K_GOL_ADVANCE, self.table.capacity, a)
+
+    W, H, gens, seed = 64, 48, 25, 19
+    heap = D.Heap(32 << 20)
+    g = Separate(heap)
+    heap.freeze()
+    s = g.add(W, H, seed)
+    for _ in range(gens):
+        g.step()
+    ref, alive, _ = oracle.gol_run(W, H, gens, seed=seed)
+    assert np.array_equal(g.read(s), ref)
+    assert heap.get_error() == 0
+    heap.close()

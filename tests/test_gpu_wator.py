@@ -279,3 +279,32 @@ def test_counts_stored_into_mapped_pinned_host_memory():
         assert heap.get_error() == 0
         g.close()
         heap.close()
+
+
+def test_separate_advance_launch_equals_folded():
+    """The step counter advanced by its own kernel after Shark.move (K_WATOR_ADVANCE)
+    or by CTA 0 of Shark.move itself (SHARK_MOVE_ADVANCE, the default): the same
+    simulation."""
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import WatorWorld
+
+    class Separate(WatorWorld):
+        def step(self):
+            a = self.args()
+            self.heap.parallel_do(self.fish_type, D.M_WATOR_FISH_CHOOSE, a)
+            self.heap.parallel_do_enumerated(self.fish_type, D.M_WATOR_FISH_MOVE, a)
+            self.heap.parallel_do(self.shark_type, D.M_WATOR_SHARK_CHOOSE, a)
+            self.heap.parallel_do_enumerated(self.shark_type, D.M_WATOR_SHARK_MOVE, a)
+            self.heap.run_kernel(D.K_WATOR_ADVANCE, self.table.capacity, a)
+
+    W, H, steps, seed = 96, 64, 30, 17
+    heap = D.Heap(32 << 20)
+    w = Separate(heap)
+    heap.freeze()
+    s = w.add(W, H, seed)
+    for _ in range(steps):
+        w.step()
+    ref, _ = oracle.wator_run(W, H, steps, seed=seed)
+    assert np.array_equal(w.read(s), ref)
+    assert heap.get_error() == 0
+    heap.close()
