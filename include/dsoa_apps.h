@@ -130,6 +130,7 @@ typedef struct {
 #define DSOA_K_TRAFFIC_CLEAR 451   /* n = total cells: next occupancy buffer = 0         */
 #define DSOA_K_TRAFFIC_ONRAMP 452  /* n = rings: new car at an empty cell 0              */
 #define DSOA_K_TRAFFIC_ADVANCE 453 /* n = 1: t += 1                                      */
+#define DSOA_K_TRAFFIC_ONRAMP_ADVANCE 454 /* ONRAMP, then ADVANCE, in one launch (n = rings) */
 typedef struct {
     uint8_t* occ0;               /* [total] occupancy, even steps read occ0           */
     uint8_t* occ1;               /* [total] occupancy, odd steps read occ1            */

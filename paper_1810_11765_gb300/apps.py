@@ -335,8 +335,7 @@ class TrafficWorld:
     def step(self):
         self.heap.run_kernel(D.K_TRAFFIC_CLEAR, self.total, self.a)
         self.heap.parallel_do(self.car_type, D.M_TRAFFIC_MOVE, self.a)
-        self.heap.run_kernel(D.K_TRAFFIC_ONRAMP, int(self.L.size), self.a)
-        self.heap.run_kernel(D.K_TRAFFIC_ADVANCE, 1, self.a)
+        self.heap.run_kernel(D.K_TRAFFIC_ONRAMP_ADVANCE, int(self.L.size), self.a)
         self.steps_done += 1
 
     def read(self):

@@ -2,7 +2,8 @@
 // (Table 1 "traffic"; Nagel & Schreckenberg 1992).  Car {0 ring, 1 pos, 2 v}
 // objects of all rings share one heap and one launch per step.  Occupancy is
 // double-buffered (step t reads buffer t&1, writes the other), so a step is
-// CLEAR(next) -> Car.move (do-all) -> ONRAMP -> ADVANCE(t).
+// CLEAR(next) -> Car.move (do-all) -> ONRAMP -> ADVANCE(t); ONRAMP_ADVANCE does the
+// last two in one launch.
 #include "dsoa_internal.cuh"
 #include "rng.cuh"
 
@@ -112,6 +113,27 @@ __global__ void k_onramp(dsoa_ctx c, dsoa_traffic_args a) {
 
 __global__ void k_advance(uint32_t* t_dev) { *t_dev += 1u; }
 
+// ONRAMP and ADVANCE in one launch: one CTA takes every ring (nothing else reads
+// t during the kernel), then advances t once all its threads have read it.
+__global__ void k_onramp_advance(dsoa_ctx c, dsoa_traffic_args a) {
+    const uint32_t step = *a.t_dev;
+    uint8_t* nxt = (step & 1u) ? a.occ0 : a.occ1;
+    for (uint32_t i = threadIdx.x; i < a.n_rings; i += blockDim.x) {
+        const uint64_t b = a.ring_base[i];
+        if (nxt[b] == 0 && dsoa_philox_w0(a.seed, step, 0u, i, 3u) < a.ramp_thr) {
+            const dsoa_obj o = dsoa_new(c, (uint32_t)a.car_type);
+            if (o) {
+                dsoa_field<uint32_t>(c, o, 0) = i;
+                dsoa_field<uint32_t>(c, o, 1) = 0u;
+                dsoa_field<uint32_t>(c, o, 2) = 0u;
+                nxt[b] = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *a.t_dev = step + 1u;
+}
+
 }  // namespace
 
 int dsoa_traffic_do(dsoa_heap* h, int type, int method, const void* a, size_t nb) {
@@ -152,6 +174,9 @@ int dsoa_traffic_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, siz
             return dsoa_check_launch(h);
         case DSOA_K_TRAFFIC_ADVANCE:
             k_advance<<<1, 1, 0, h->stream>>>(args.t_dev);
+            return dsoa_check_launch(h);
+        case DSOA_K_TRAFFIC_ONRAMP_ADVANCE:
+            k_onramp_advance<<<1, 256, 0, h->stream>>>(dsoa_launch_ctx(h), args);
             return dsoa_check_launch(h);
         default: return DSOA_ERR_UNKNOWN_METHOD;
     }

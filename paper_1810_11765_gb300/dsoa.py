@@ -41,6 +41,7 @@ M_WATOR_FISH_MOVE_DEFER, K_WATOR_BIRTHS = 306, 352
 M_GOL_DECIDE_ADVANCE, M_WATOR_SHARK_MOVE_ADVANCE = 206, 307
 M_TRAFFIC_MOVE, M_TRAFFIC_READ = 401, 402
 K_TRAFFIC_INIT, K_TRAFFIC_CLEAR, K_TRAFFIC_ONRAMP, K_TRAFFIC_ADVANCE = 450, 451, 452, 453
+K_TRAFFIC_ONRAMP_ADVANCE = 454
 C_NBODY, M_NBODY_FORCE, M_NBODY_MOVE = 500, 501, 502
 M_COLL_FIND, M_COLL_CLAIM, M_COLL_MERGE, M_COLL_DELETE = 503, 504, 505, 506
 M_NBODY_READ, M_NBODY_FORCE_TILED, M_COLL_FIND_TILED = 507, 508, 509

@@ -95,3 +95,37 @@ def test_programmatic_dependent_launch(flags):
     assert np.array_equal(go, o)
     assert np.array_equal(gv, v)
     assert heap.get_error() == 0
+
+
+def test_separate_onramp_and_advance_equal_folded():
+    """ONRAMP then ADVANCE as two launches, or ONRAMP_ADVANCE (the default) as one,
+    over 300 rings (several CTAs' worth for the separate on-ramp kernel): the same
+    cars as the oracle."""
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import TrafficWorld
+
+    class Separate(TrafficWorld):
+        def step(self):
+            self.heap.run_kernel(D.K_TRAFFIC_CLEAR, self.total, self.a)
+            self.heap.parallel_do(self.car_type, D.M_TRAFFIC_MOVE, self.a)
+            self.heap.run_kernel(D.K_TRAFFIC_ONRAMP, int(self.L.size), self.a)
+            self.heap.run_kernel(D.K_TRAFFIC_ADVANCE, 1, self.a)
+            self.steps_done += 1
+
+    rng = np.random.default_rng(3)
+    L = [int(x) for x in rng.integers(16, 400, 300)]
+    thr = [int(d * 2**32) for d in rng.uniform(0.1, 0.3, 300)]
+    seed, steps, ramp = 91, 25, int(0.3 * 2**32)
+    o, v, cars = oracle.traffic_run(L, thr, steps, seed=seed, ramp_thr=ramp)
+    for cls in (Separate, TrafficWorld):
+        heap = D.Heap(64 << 20)
+        w = cls(heap, L, thr, seed, ramp_thr=ramp)
+        heap.freeze()
+        w.init()
+        for _ in range(steps):
+            w.step()
+        go, gv = w.read()
+        assert np.array_equal(go, o) and np.array_equal(gv, v), cls.__name__
+        assert heap.count(w.car_type) == cars[-1].sum()
+        assert heap.get_error() == 0
+        heap.close()
