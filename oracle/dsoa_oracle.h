@@ -17,9 +17,14 @@
  *   orc_splitmix64      pinned: published first outputs of SplitMix64 from state 0
  *   orc_micro_run       pinned: closed forms (x recurrence, expected live counts),
  *                       brute-force recomputation per object, order independence
- *   orc_gol_run         pinned: blinker, glider, block still-life, numpy roll-sum
- *   orc_wator_run       pinned: hand-derived single/two-agent cases, conservation,
- *                       order independence
+ *   orc_gol_run         pinned: blinker, glider, block still-life, numpy roll-sum,
+ *                       initial cells from the Philox known answers
+ *   orc_wator_run       pinned: a cell-indexed brute force on 4x4..6x6 tori
+ *                       (random grids, shark breeding, high seed words, step
+ *                       offsets), hand-derived picks with 2, 3 and 4 candidates
+ *                       from the Philox known answers, hand-derived single- and
+ *                       two-agent cases, conservation, order independence; 21
+ *                       planted mistakes each fail at least three pins
  *   orc_traffic_run     pinned: deterministic (p=0) closed forms of Nagel &
  *                       Schreckenberg 1992, conservation, brute force on L=16
  *   orc_nbody_run       pinned: two-body closed forms (first step of a pair at
