@@ -39,6 +39,8 @@ extern "C" {
 #define DSOA_DEV_SPIN 2         /* a bounded retry loop gave up                     */
 #define DSOA_DEV_DOUBLE_FREE 4  /* a slot was freed twice                           */
 #define DSOA_DEV_BAD_HANDLE 8   /* a handle did not decode to a valid type/block    */
+#define DSOA_DEV_BAD_INDEX 16   /* a method read an instance / cell index out of range
+                                   from an object field and skipped the object        */
 
 #define DSOA_MAX_TYPES 16       /* registered types per heap                        */
 #define DSOA_MAX_FIELDS 12      /* fields per type                                  */
@@ -310,8 +312,14 @@ int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
  * last three are not in the paper); DSOA_FLAG_ENUM_TICKETS (32) makes the
  * single-pass enumeration hand tiles out by a ticket counter instead of
  * ordering them by CTA index (which relies on every CTA of the launch being
- * resident: true on an otherwise idle GPU).  Returns DSOA_ERR_INVALID_ARG for
- * an unknown bit.  Takes effect for launches issued after the call. */
+ * resident: true on an otherwise idle GPU).  Two experiment switches change
+ * the allocation policy (measured in the fragmentation analysis of Sec. 6.4):
+ * DSOA_FLAG_NO_FRESH_GROUP (128) keeps groups of 16 or more requests searching
+ * active blocks after a lost round instead of taking a fresh block, and
+ * DSOA_FLAG_PAPER_R (256) counts every active-block attempt of an allocation
+ * toward r, lost reservations included, and takes a fresh block after r of
+ * them (Alg. 1's reading of r).  Returns DSOA_ERR_INVALID_ARG for an unknown
+ * bit.  Takes effect for launches issued after the call. */
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags);
 
 /* r of Sec. 4.2 / Fig. 11: attempts to find an active block (try_find_set on
@@ -399,9 +407,13 @@ int dsoa_bitmap_heap_destroy(dsoa_bitmap_heap* h);
  *     larger heap returns DSOA_ERR_SCRATCH_LIMIT;
  *   - the heap must be frozen (DSOA_ERR_NOT_FROZEN otherwise; not frozen
  *     implicitly) and its device must be the current device;
- *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture;
+ *   - every call made outside stream capture looks up the array's device
+ *     address (cudaGetSymbolAddress) with the heap's device current; a call
+ *     made while the heap's stream is capturing uses the address of the
+ *     latest call outside capture on that device.  So make one call before
+ *     any stream capture, and again after a device reset (cudaDeviceReset
+ *     reloads the library's module, which may move the array); a call under
+ *     capture with no earlier call returns DSOA_ERR_CAPTURE;
  *   - every call shares the one array, which keeps the last call's contents;
  *     the ticket is cleared at the start of each call, counts and offsets are
  *     overwritten.  Calls that overlap on the GPU (two streams, two heaps at

@@ -42,6 +42,14 @@ extern "C" {
                                          stored to *(u64*)stats only when it equals seed.  It
                                          measures the L2 ceiling of single-lane bitmap atomics,
                                          the operation the allocator is built from (Sec. 4). */
+#define DSOA_K_MICRO_NEW_EACH 152     /* n threads; thread i creates `round` microbench objects
+                                         one after another (a loop of device new, the
+                                         per-thread allocation pattern of the Linux
+                                         scalability benchmark, Sec. 6.5); object j of
+                                         thread i gets id = id_base + i * round + j.  n_ids
+                                         holds the type to allocate (the microbench type or
+                                         a type extending it).  A full heap leaves the
+                                         remaining objects unallocated (DSOA_DEV_OOM). */
 typedef struct {
     uint64_t seed;       /* SplitMix64 key                                   */
     uint32_t id_base;    /* constructor: first id                            */

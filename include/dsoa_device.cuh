@@ -47,6 +47,14 @@
 #ifndef DSOA_ALLOC_ROUNDS
 #define DSOA_ALLOC_ROUNDS (1u << 12)
 #endif
+/* Without bitmap rotation (the NoShift ablation of Sec. 6.4) every leader
+ * searches from the same first bit and most rounds are lost to the same few
+ * blocks; lost rounds then back off exponentially (64 ns .. 4 us, jittered) and
+ * the bound is larger, so that legal workloads finish, as Alg. 1's unbounded
+ * retry loop does, only slower (about a second per allocation at most). */
+#ifndef DSOA_ALLOC_ROUNDS_NO_ROTATE
+#define DSOA_ALLOC_ROUNDS_NO_ROTATE (1u << 18)
+#endif
 #ifndef DSOA_TAKE_ATTEMPTS
 #define DSOA_TAKE_ATTEMPTS 256u
 #endif
@@ -119,7 +127,19 @@ struct dsoa_ctx {
                                              GPU); slower on large heaps                */
 #define DSOA_FLAG_PDL 16u                 /* programmatic dependent launch of the
                                              enumeration, do-all and step kernels  */
+#define DSOA_FLAG_NO_FRESH_GROUP 128u     /* experiment: large groups keep searching
+                                             active blocks after a lost round, like
+                                             small ones (no fresh-block shortcut)   */
+#define DSOA_FLAG_PAPER_R 256u            /* experiment: r counts every active-block
+                                             attempt of an allocation, lost
+                                             reservations included, and after r of
+                                             them the allocation takes a fresh block
+                                             (Alg. 1's reading of r, Sec. 4.2)      */
 #define DSOA_GRID_SCRATCH (DSOA_FUSED_MAX_CTAS + 64u)
+#define DSOA_CTX_NO_PROLOGUE (1u << 30)   /* set by the library in the context of the
+                                             do-all launches that follow the first one
+                                             of a family (a type with subtypes), so a
+                                             method's prologue runs once per do-all */
 
 /* Programmatic dependent launch (sm_90 and later).  A kernel launched with the
  * programmatic-serialization attribute may be scheduled while its predecessor
@@ -191,6 +211,18 @@ __device__ __forceinline__ uint32_t dsoa_smid() {
     uint32_t s;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(s));
     return s;
+}
+
+/* An index that a method read from an object field (an instance, a grid cell,
+ * a ring), checked before it addresses an application array: out of range
+ * raises DSOA_DEV_BAD_INDEX and the method skips the object.  In a consistent
+ * heap no index is ever out of range; the check keeps a method in bounds after
+ * a bounded wait gave up (DSOA_DEV_SPIN) and left a stale bitmap bit that lists
+ * a block under a type it no longer holds. */
+__device__ __forceinline__ bool dsoa_index_ok(const dsoa_ctx& c, uint64_t i, uint64_t n) {
+    if (i < n) return true;
+    dsoa_raise(c, DSOA_DEV_BAD_INDEX);
+    return false;
 }
 
 /* One wait step of a bounded spin; false once the bound is reached (error set). */
@@ -440,7 +472,15 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
         hp = c.hint + (gwarp & c.hint_mask) * c.ntypes + t;
     }
     uint32_t empty_free = 0;   /* rounds that found the free-block bitmap empty */
-    for (uint32_t round = 0; round < DSOA_ALLOC_ROUNDS; ++round) {
+    const uint32_t max_rounds = rot ? DSOA_ALLOC_ROUNDS : DSOA_ALLOC_ROUNDS_NO_ROTATE;
+    const bool paper_r = (c.flags & DSOA_FLAG_PAPER_R) != 0u;
+    const bool fresh_group = want >= DSOA_FRESH_GROUP && !(c.flags & DSOA_FLAG_NO_FRESH_GROUP);
+    uint32_t tries = 0;        /* paper_r: active-block attempts so far, lost ones included */
+    for (uint32_t round = 0; round < max_rounds; ++round) {
+        if (!rot && round) {           /* NoShift: thin out the races on the first bits */
+            const uint32_t span = 32u << (round < 7u ? round : 7u);
+            __nanosleep(span / 2u + (dsoa_hash(h ^ (round * 0x9E3779B9u)) & (span / 2u - 1u)));
+        }
         int64_t bid = -1;
         unsigned long long w = 0ull;   /* free slots of bid, if already known */
         if (round == 0 && hp) {
@@ -453,9 +493,15 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
          * (an allocation burst), they would otherwise keep converging on the same
          * few blocks.  Small groups keep searching, so steady-state
          * fragmentation is unchanged.  An empty free bitmap always searches. */
-        const bool search = round == 0 || empty_free || want < DSOA_FRESH_GROUP;
-        for (uint32_t a = 0; search && a < c.lookups && bid < 0; ++a)
-            bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
+        const bool search = paper_r ? (tries < c.lookups || empty_free != 0u)
+                                    : (round == 0 || empty_free || !fresh_group);
+        if (paper_r) {                 /* at most r finds per round, r attempts in all */
+            for (uint32_t a = 0; search && bid < 0 && a < c.lookups && (tries < c.lookups || empty_free); ++a, ++tries)
+                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u));
+        } else {
+            for (uint32_t a = 0; search && a < c.lookups && bid < 0; ++a)
+                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
+        }
         if (bid < 0) {
             const unsigned long long fmask = dsoa_lowest_k(c.cap[t], want);
             bid = dsoa_block_new_reserved(c, t, h ^ round, fmask);
@@ -592,7 +638,10 @@ __device__ __forceinline__ F& dsoa_field(const dsoa_ctx& c, dsoa_obj h, uint32_t
  *   static __device__ void prologue(const dsoa_ctx&, const Args&);
  * CTA 0 of its do-all runs it (all threads of that CTA) before taking objects,
  * which spares the step a launch of its own (e.g. advancing the instances' step
- * counters in a kernel that does not read them). */
+ * counters in a kernel that does not read them).  A do-all on a type with
+ * subtypes launches the method once per member type; the prologue runs in the
+ * first of those launches only (the library marks the others with
+ * DSOA_CTX_NO_PROLOGUE), so it runs once per dsoa_parallel_do. */
 template <class M, class = void>
 struct dsoa_has_prologue { static constexpr bool value = false; };
 template <class M>
@@ -600,7 +649,7 @@ struct dsoa_has_prologue<M, decltype((void)&M::prologue, void())> { static const
 template <class M>
 __device__ __forceinline__ void dsoa_run_prologue(const dsoa_ctx& c, const typename M::Args& a) {
     if constexpr (dsoa_has_prologue<M>::value) {
-        if (blockIdx.x == 0) M::prologue(c, a);
+        if (blockIdx.x == 0 && !(c.flags & DSOA_CTX_NO_PROLOGUE)) M::prologue(c, a);
     }
 }
 
@@ -833,7 +882,12 @@ __device__ inline void dsoa_device_do(const dsoa_ctx& c, uint32_t t, F&& f) {
  *            created by the method are never visited, Sec. 3.1)
  *   phase 3  the do-all loop of dsoa_doall_kernel over R
  * The grid must be co-resident (cooperative launch).  Barrier waits are
- * bounded; on the bound every CTA sets DSOA_DEV_SPIN and returns.
+ * bounded; on the bound every CTA sets DSOA_DEV_SPIN and returns, having
+ * stored r = 0 (an empty snapshot).  r is published only once the second
+ * barrier shows every CTA's part of R written, so a give-up never leaves a
+ * snapshot with unwritten entries for a later method to reuse.  The launcher
+ * zeroes the barrier words before each launch: a give-up leaves them
+ * mid-generation. 
  * ------------------------------------------------------------------------ */
 __device__ inline bool dsoa_grid_sync(const dsoa_ctx& c, uint32_t nblocks) {
     uint32_t* count = c.grid_scratch + DSOA_FUSED_MAX_CTAS;
@@ -896,7 +950,10 @@ __global__ void __launch_bounds__(512) dsoa_doall_fused_kernel(dsoa_ctx c, uint3
         for (uint32_t w = 0; w < nwarps; ++w) sum += red[w];
         dsoa_st32(&agg[blockIdx.x], sum);
     }
-    if (!dsoa_grid_sync(c, nb)) return;
+    if (!dsoa_grid_sync(c, nb)) {            /* gave up: publish an empty snapshot */
+        if (tid == 0) dsoa_st32(r_dev, 0u);
+        return;
+    }
     /* phase 2: prefix of the aggregates below this CTA and the total */
     uint32_t below = 0, total = 0;
     for (uint32_t i = tid; i < nb; i += blockDim.x) {
@@ -920,7 +977,6 @@ __global__ void __launch_bounds__(512) dsoa_doall_fused_kernel(dsoa_ctx c, uint3
     __syncthreads();
     uint32_t base = red[0];
     const uint32_t r = red[1];
-    if (blockIdx.x == 0 && tid == 0) *r_dev = r;
     /* compaction of this CTA's tiles, one tile at a time */
     for (uint64_t tt = t_lo; tt < t_hi; ++tt) {
         unsigned long long w = 0ull;
@@ -953,7 +1009,12 @@ __global__ void __launch_bounds__(512) dsoa_doall_fused_kernel(dsoa_ctx c, uint3
         base += tile_total;
         __syncthreads();
     }
-    if (!dsoa_grid_sync(c, nb)) return;
+    if (!dsoa_grid_sync(c, nb)) {
+        if (tid == 0) dsoa_st32(r_dev, 0u);
+        return;
+    }
+    /* every CTA wrote its part of R before the barrier: R is complete */
+    if (blockIdx.x == 0 && tid == 0) dsoa_st32(r_dev, r);
     /* phase 3: the do-all over the snapshot */
     constexpr uint32_t TPB = 64u / G;
     const uint64_t n = (uint64_t)gridDim.x * blockDim.x;

@@ -71,6 +71,7 @@ struct dsoa_heap {
     uint64_t launches = 0;
     bool enumerated[DSOA_MAX_TYPES] = {false};  // R[t] holds an enumeration of type t
     bool skip_enumeration = false;   // set by dsoa_parallel_do_enumerated
+    bool skip_prologue = false;      // launches after the first of a family's do-all
 };
 
 struct dsoa_graph {
@@ -174,6 +175,13 @@ int dsoa_run_doall_fused(dsoa_heap* h, int type, const typename M::Args& args) {
     auto* k = &dsoa_doall_fused_kernel<M, G>;
     unsigned grid = dsoa_persistent_grid(h, k, tpb);
     if (grid > DSOA_FUSED_MAX_CTAS) grid = DSOA_FUSED_MAX_CTAS;
+    /* barrier counter and generation start from zero (a launch whose barrier
+     * wait gave up leaves them mid-generation) */
+    if (cudaMemsetAsync(h->ctx.grid_scratch + DSOA_FUSED_MAX_CTAS, 0, 2 * sizeof(uint32_t), h->stream) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return DSOA_ERR_CUDA;
+    }
     const cudaError_t e = dsoa_launch_cooperative(k, grid, (unsigned)tpb, h->stream, dsoa_launch_ctx(h),
                                                   (uint32_t)type, h->R[type], h->Rocc[type], h->r_dev[type], args);
     h->launches++;

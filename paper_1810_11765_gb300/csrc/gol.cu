@@ -23,6 +23,10 @@ __device__ __forceinline__ void moore(uint32_t c, uint32_t w, uint32_t h, uint32
             if (dx != 1 || dy != 1) nb[k++] = rs[dy] + xs[dx];
 }
 
+// Cells of instance I: every cell index read from an object field is checked
+// against it before it addresses the instance's grids (dsoa_index_ok).
+__device__ __forceinline__ uint64_t cells_of(const dsoa_inst& I) { return (uint64_t)I.w * I.h; }
+
 struct CellCtor {
     using Args = dsoa_gol_args;
     static __device__ void ctor(const dsoa_ctx& c, dsoa_obj o, uint64_t i, const Args& a) {
@@ -51,9 +55,11 @@ struct Spread {
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, k, a.n_inst)) return;
         const dsoa_inst I = a.inst[k];
         if (I.state != DSOA_INST_RUN) return;
         const uint32_t cell = dsoa_column<uint32_t>(c, t, bid, 1)[s];
+        if (!dsoa_index_ok(c, cell, cells_of(I))) return;
         uint32_t nc[8];
         moore(cell, I.w, I.h, nc);
         dsoa_obj nb[8];
@@ -72,9 +78,11 @@ struct Reap {
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, k, a.n_inst)) return;
         const dsoa_inst& I = a.inst[k];
         if (I.state != DSOA_INST_RUN) return;
         const uint32_t cell = dsoa_column<uint32_t>(c, t, bid, 1)[s];
+        if (!dsoa_index_ok(c, cell, cells_of(I))) return;
         const dsoa_obj co = I.cellmap[cell];
         if (!co) return;
         const uint32_t n = dsoa_field<uint32_t>(c, co, 2);
@@ -91,6 +99,7 @@ struct Decide {
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, k, a.n_inst)) return;
         if (a.inst[k].state != DSOA_INST_RUN) return;
         uint32_t* cnt = dsoa_column<uint32_t>(c, t, bid, 2) + s;
         uint8_t* alive = dsoa_column<uint8_t>(c, t, bid, 3) + s;
@@ -121,8 +130,10 @@ struct Read {
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, k, a.n_inst)) return;
         uint8_t* occ = a.inst[k].occ;
-        if (occ) occ[dsoa_column<uint32_t>(c, t, bid, 1)[s]] = dsoa_column<uint8_t>(c, t, bid, 3)[s];
+        const uint32_t cell = dsoa_column<uint32_t>(c, t, bid, 1)[s];
+        if (occ && dsoa_index_ok(c, cell, cells_of(a.inst[k]))) occ[cell] = dsoa_column<uint8_t>(c, t, bid, 3)[s];
     }
 };
 
@@ -131,6 +142,7 @@ struct Kill {
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, k, a.n_inst)) return;
         if (a.inst[k].state == DSOA_INST_KILL) dsoa_delete(c, dsoa_make_handle(t, bid, s));
     }
 };

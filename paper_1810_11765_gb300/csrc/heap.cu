@@ -253,7 +253,11 @@ __global__ void __launch_bounds__(64 * TPC) k_compact(dsoa_ctx c, uint32_t b, ui
 // nothing is reset between launches (safe in graph replays); the last CTA to
 // finish advances the epoch and resets the ticket.  A published value is only
 // ever read as itself, so no fence precedes it.  Every wait is bounded
-// (DSOA_DEV_SPIN).
+// (DSOA_DEV_SPIN).  A tile whose look-back gives up still finishes (its
+// under-counted prefix keeps every write below the true end of R, so all
+// writes stay in bounds) and marks the epoch failed; the CTA that closes a
+// failed epoch publishes r = 0, so no method ever runs on, or later reuses,
+// a block list with misplaced entries.
 constexpr unsigned long long kLbA = 1ull, kLbP = 2ull;
 __device__ __forceinline__ unsigned long long lb_word(uint32_t ep, unsigned long long st, unsigned long long v) {
     return ((unsigned long long)(ep & 0xFFFFFFu) << 40) | (st << 38) | (v & ((1ull << 38) - 1ull));
@@ -269,7 +273,7 @@ struct EnumBatch {
     unsigned long long* Rocc[DSOA_MAX_TYPES];
     uint32_t* r_dev[DSOA_MAX_TYPES];
     unsigned long long* state[DSOA_MAX_TYPES];    // [tiles] look-back state words
-    uint32_t* ctl[DSOA_MAX_TYPES];                // ticket, done, epoch
+    uint32_t* ctl[DSOA_MAX_TYPES];                // ticket, done, epoch, failed
 };
 
 __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint64_t tiles, EnumBatch eb,
@@ -290,6 +294,7 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint64_t tiles
     uint32_t* ticket = ctl;
     uint32_t* done = ctl + 1;
     uint32_t* epoch = ctl + 2;
+    uint32_t* failed = ctl + 3;
     const uint32_t j = threadIdx.x, lane = j & 31u;
     dsoa_pdl_wait();
     dsoa_pdl_release();
@@ -362,7 +367,10 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint64_t tiles
             }
         }
         if (j == 0) {
-            if (!ok) dsoa_raise(c, DSOA_DEV_SPIN);
+            if (!ok) {
+                dsoa_raise(c, DSOA_DEV_SPIN);
+                atomicOr(failed, 1u);
+            }
             s_prefix = prefix;
             if (t > 0) dsoa_st(&state[t], lb_word(ep, kLbP, prefix + total));
             if (t == tiles - 1) *r_dev = (uint32_t)(prefix + total);
@@ -383,6 +391,11 @@ __global__ void __launch_bounds__(64) k_enum_lookback(dsoa_ctx c, uint64_t tiles
     if (j == 0) {
         __threadfence();
         if (atomicAdd(done, 1u) == (uint32_t)tiles - 1u) {
+            __threadfence();
+            if (dsoa_ld32(failed)) {         /* a tile gave up: empty snapshot */
+                dsoa_st32(r_dev, 0u);
+                dsoa_st32(failed, 0u);
+            }
             dsoa_st32(ticket, 0u);
             dsoa_st32(done, 0u);
             __threadfence();
@@ -416,6 +429,7 @@ __global__ void __launch_bounds__(64) k_enum_lookback_multi(dsoa_ctx c, uint64_t
     uint32_t* ticket = ctl;
     uint32_t* done = ctl + 1;
     uint32_t* epoch = ctl + 2;
+    uint32_t* failed = ctl + 3;
     const uint32_t j = threadIdx.x, lane = j & 31u, warp = j >> 5;
     dsoa_pdl_wait();
     dsoa_pdl_release();
@@ -477,7 +491,10 @@ __global__ void __launch_bounds__(64) k_enum_lookback_multi(dsoa_ctx c, uint64_t
             }
         }
         if (j == 0) {
-            if (!ok) dsoa_raise(c, DSOA_DEV_SPIN);
+            if (!ok) {
+                dsoa_raise(c, DSOA_DEV_SPIN);
+                atomicOr(failed, 1u);
+            }
             s_prefix = prefix;
             if (cta > 0) dsoa_st(&state[cta], lb_word(ep, kLbP, prefix + agg));
             if (cta == ctas - 1) *r_dev = (uint32_t)(prefix + agg);
@@ -506,6 +523,11 @@ __global__ void __launch_bounds__(64) k_enum_lookback_multi(dsoa_ctx c, uint64_t
     if (j == 0) {
         __threadfence();
         if (atomicAdd(done, 1u) == ctas - 1u) {
+            __threadfence();
+            if (dsoa_ld32(failed)) {         /* a CTA gave up: empty snapshot */
+                dsoa_st32(r_dev, 0u);
+                dsoa_st32(failed, 0u);
+            }
             dsoa_st32(ticket, 0u);
             dsoa_st32(done, 0u);
             __threadfence();
@@ -669,7 +691,7 @@ int dsoa_check_launch(dsoa_heap* h) {
 dsoa_ctx dsoa_launch_ctx(dsoa_heap* h) {
     dsoa_ctx c = h->ctx;
     c.seed = 0x9E3779B9u * (++h->launch_seq);
-    c.flags = h->flags;
+    c.flags = h->flags | (h->skip_prologue ? DSOA_CTX_NO_PROLOGUE : 0u);
     c.lookups = h->lookups;
     return c;
 }
@@ -895,7 +917,7 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     c.hint = (dsoa_hint*)(base + L.off_hint);
     c.hint_mask = (uint32_t)(L.hint_slots - 1);
     h->lb_state = (unsigned long long*)(base + L.off_lb);              // [ntypes][tiles]
-    h->lb_ctl = (uint32_t*)(h->lb_state + L.tiles * (uint64_t)h->ntypes);  // [ntypes][4]: ticket, done, epoch
+    h->lb_ctl = (uint32_t*)(h->lb_state + L.tiles * (uint64_t)h->ntypes);  // [ntypes][4]: ticket, done, epoch, failed
     c.grid_scratch = (uint32_t*)(base + L.off_grid);
     h->done = (uint32_t*)(small + 1);
     h->scratch64 = (unsigned long long*)(small + 32);
@@ -1054,7 +1076,11 @@ int dsoa_parallel_do(dsoa_heap* h, int type, int method_id, const void* args, si
     }
     const bool skip = h->skip_enumeration;
     h->skip_enumeration = true;
-    for (int q = 0; q < n && rc == DSOA_OK; ++q) rc = parallel_do_one(h, fam[q], method_id, args, nb);
+    for (int q = 0; q < n && rc == DSOA_OK; ++q) {
+        h->skip_prologue = q > 0;      // a method's prologue runs once per do-all
+        rc = parallel_do_one(h, fam[q], method_id, args, nb);
+    }
+    h->skip_prologue = false;
     h->skip_enumeration = skip;
     return rc;
 }
@@ -1337,7 +1363,8 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
 
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags) {
     if (!h || (flags & ~(DSOA_FLAG_NO_COALESCE | DSOA_FLAG_NO_ROTATE | DSOA_FLAG_NO_HINT | DSOA_FLAG_FUSED |
-                         DSOA_FLAG_PDL | DSOA_FLAG_ENUM_TICKETS)))
+                         DSOA_FLAG_PDL | DSOA_FLAG_ENUM_TICKETS | DSOA_FLAG_NO_FRESH_GROUP |
+                         DSOA_FLAG_PAPER_R)))
         return DSOA_ERR_INVALID_ARG;
     h->flags = flags;
     return DSOA_OK;

@@ -316,6 +316,18 @@ __global__ void k_micro_device_do(dsoa_ctx c, uint32_t t, uint64_t n, unsigned l
     out[2 * i + 1] = sid;
 }
 
+/* Each thread allocates k objects one after another; the lanes of a warp
+ * allocate together in every iteration, so each of the k rounds is one
+ * warp-coalesced request of up to 32 slots. */
+__global__ void k_micro_new_each(dsoa_ctx c, uint32_t t, uint64_t n, uint32_t k, dsoa_micro_args a) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        for (uint32_t j = 0; j < k; ++j) {
+            const dsoa_obj o = dsoa_new(c, t);
+            if (o) MicroCtor::ctor(c, o, i * k + j, a);
+        }
+}
+
 /* L2 ceiling of single-lane 64-bit bitmap atomics (the allocator's building
  * block, Sec. 4): consecutive lanes hit words 17 apart (136 bytes), so each
  * lane's op is a separate L2 request, as a warp leader's reservation is. */
@@ -345,6 +357,17 @@ int dsoa_micro_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_
         k_micro_atomic_peak<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
             (unsigned long long*)args.handles_out, nw - 1, n, args.round, (unsigned long long)args.seed,
             (unsigned long long*)args.stats);
+        return dsoa_check_launch(h);
+    }
+    if (kernel == DSOA_K_MICRO_NEW_EACH) {
+        const uint64_t type = args.n_ids;
+        if (n == 0 || args.round == 0 || type >= (uint64_t)h->ntypes || h->types[type].nfields < 3 ||
+            h->types[type].field_bytes[0] != 4 || h->types[type].field_bytes[1] != 4 ||
+            h->types[type].field_bytes[2] != 8 || n * (uint64_t)args.round + args.id_base > 0xFFFFFFFFull)
+            return DSOA_ERR_INVALID_ARG;
+        const int tpb = 256;
+        k_micro_new_each<<<dsoa_new_grid(h, n, tpb), tpb, 0, h->stream>>>(dsoa_launch_ctx(h), (uint32_t)type, n,
+                                                                         args.round, args);
         return dsoa_check_launch(h);
     }
     if (kernel != DSOA_K_MICRO_DEVICE_DO) return DSOA_ERR_UNKNOWN_METHOD;

@@ -113,13 +113,18 @@ __global__ void __launch_bounds__(64) k_compact_na(dsoa_ctx c, uint32_t b, uint6
     }
 }
 
-// Device address of s_enum_scratch on `dev` (current device), looked up once.
-uint32_t* scratch_address(int dev) {
+// Device address of s_enum_scratch on `dev` (the current device).  Outside
+// stream capture it is looked up on every call, so an address made stale by a
+// device reset (which reloads this library's module) is never used; a call
+// under capture takes the address of the latest call outside capture on that
+// device (nullptr if there was none).
+uint32_t* scratch_address(int dev, bool capturing) {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!capturing) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, s_enum_scratch) != cudaSuccess) {
             cudaGetLastError();
+            g_scratch_addr[dev] = nullptr;
             return nullptr;
         }
         g_scratch_addr[dev] = static_cast<uint32_t*>(p);
@@ -139,8 +144,14 @@ extern "C" int dsoa_enumerate_noalloc(dsoa_heap* h, int type, uint32_t* R_out_de
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device || dev < 0 || dev >= kMaxDevices)
         return DSOA_ERR_INVALID_ARG;
-    uint32_t* scratch = scratch_address(dev);
-    if (!scratch) return DSOA_ERR_CUDA;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return DSOA_ERR_CUDA;
+    }
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    uint32_t* scratch = scratch_address(dev, capturing);
+    if (!scratch) return capturing ? DSOA_ERR_CAPTURE : DSOA_ERR_CUDA;
     // the ticket must start at zero; counts and offsets are overwritten
     if (cudaMemsetAsync(scratch + 2 * kMaxTiles, 0, sizeof(uint32_t), h->stream) != cudaSuccess)
         return DSOA_ERR_CUDA;

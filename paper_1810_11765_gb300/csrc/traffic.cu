@@ -28,11 +28,13 @@ struct Move {
         const uint8_t* cur = (step & 1u) ? a.occ1 : a.occ0;
         uint8_t* nxt = (step & 1u) ? a.occ0 : a.occ1;
         const uint32_t i = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, i, a.n_rings)) return;
         uint32_t* posp = dsoa_column<uint32_t>(c, t, bid, 1) + s;
         uint32_t* vp = dsoa_column<uint32_t>(c, t, bid, 2) + s;
         const uint64_t b = a.ring_base[i];
         const uint32_t L = (uint32_t)(a.ring_base[i + 1] - b);
         const uint32_t pos = *posp;
+        if (!dsoa_index_ok(c, pos, L)) return;
         uint32_t v = min(*vp + 1u, kVmax);                 // accelerate
         uint32_t gap = 0;                                  // free cells ahead
         while (gap < v && !cur[b + (pos + gap + 1u) % L]) ++gap;
@@ -55,8 +57,10 @@ struct Read {
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t i = dsoa_column<uint32_t>(c, t, bid, 0)[s];
-        a.vel_out[a.ring_base[i] + dsoa_column<uint32_t>(c, t, bid, 1)[s]] =
-            (uint8_t)dsoa_column<uint32_t>(c, t, bid, 2)[s];
+        if (!dsoa_index_ok(c, i, a.n_rings)) return;
+        const uint32_t pos = dsoa_column<uint32_t>(c, t, bid, 1)[s];
+        if (!dsoa_index_ok(c, pos, a.ring_base[i + 1] - a.ring_base[i])) return;
+        a.vel_out[a.ring_base[i] + pos] = (uint8_t)dsoa_column<uint32_t>(c, t, bid, 2)[s];
     }
 };
 

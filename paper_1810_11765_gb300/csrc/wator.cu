@@ -35,6 +35,10 @@ __device__ __forceinline__ void neighbours(uint32_t c, uint32_t w, uint32_t h, u
     nb[3] = row + (x == 0u ? w - 1u : x - 1u);          // W
 }
 
+// Cells of instance I: every cell index read from an object field is checked
+// against it before it addresses the instance's grids (dsoa_index_ok).
+__device__ __forceinline__ uint64_t cells_of(const dsoa_inst& I) { return (uint64_t)I.w * I.h; }
+
 // Index of the chosen candidate among k >= 1: Philox word 0 modulo k.  With
 // one candidate the draw cannot matter, so it is not computed.
 __device__ __forceinline__ uint32_t pick(uint32_t k, uint64_t seed, uint32_t t, uint32_t cell, uint32_t stream) {
@@ -43,21 +47,38 @@ __device__ __forceinline__ uint32_t pick(uint32_t k, uint64_t seed, uint32_t t, 
     return k == 2u ? (u & 1u) : (k == 4u ? (u & 3u) : u % 3u);
 }
 
+// The p-th neighbour (in N, E, S, W order) among those whose bit is set in
+// `m`, by an unrolled scan: the candidate list stays in registers instead of
+// a dynamically indexed local array.
+__device__ __forceinline__ uint32_t nth_candidate(const uint32_t nb[4], uint32_t m, uint32_t p) {
+    uint32_t tg = kNone, seen = 0u;
+#pragma unroll
+    for (int d = 0; d < 4; ++d)
+        if ((m >> d) & 1u) {
+            if (seen == p) tg = nb[d];
+            ++seen;
+        }
+    return tg;
+}
+
 struct FishChoose {
     using Args = dsoa_wator_args;
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
-        const dsoa_inst I = a.inst[dsoa_column<uint32_t>(c, t, bid, 0)[s]];
+        const uint32_t ik = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, ik, a.n_inst)) return;
+        const dsoa_inst I = a.inst[ik];
         if (I.state != DSOA_INST_RUN) return;
         const uint32_t cell = dsoa_column<uint32_t>(c, t, bid, 1)[s];
-        uint32_t nb[4], cand[4], k = 0;
+        if (!dsoa_index_ok(c, cell, cells_of(I))) return;
+        uint32_t nb[4], empty = 0u;
         neighbours(cell, I.w, I.h, nb);
 #pragma unroll
         for (int d = 0; d < 4; ++d)
-            if (I.occ[nb[d]] == 0) cand[k++] = nb[d];
+            if (I.occ[nb[d]] == 0) empty |= 1u << d;
         uint32_t tg = kNone;
-        if (k) {
-            tg = cand[pick(k, I.seed, I.t, cell, 1u)];
+        if (empty) {
+            tg = nth_candidate(nb, empty, pick((uint32_t)__popc(empty), I.seed, I.t, cell, 1u));
             atomicMin(&I.claim[tg], cell);
         }
         dsoa_column<uint32_t>(c, t, bid, 3)[s] = tg;
@@ -69,6 +90,7 @@ struct FishMove {
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         dsoa_prefetch_hint(c, t);
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, k, a.n_inst)) return;
         const dsoa_inst I = a.inst[k];
         if (I.state != DSOA_INST_RUN) return;
         uint32_t* cellp = dsoa_column<uint32_t>(c, t, bid, 1) + s;
@@ -77,7 +99,9 @@ struct FishMove {
         const uint32_t age = *agep + 1u;
         *agep = age;
         const uint32_t old = *cellp;
-        if (tg == kNone || I.claim[tg] != old) return;
+        if (tg == kNone) return;
+        if (!dsoa_index_ok(c, tg, cells_of(I)) || !dsoa_index_ok(c, old, cells_of(I))) return;
+        if (I.claim[tg] != old) return;
         I.claim[tg] = kNone;
         I.occ[tg] = 1;
         I.cellmap[tg] = dsoa_make_handle(t, bid, s);
@@ -110,6 +134,7 @@ struct FishMoveDeferred {
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, k, a.n_inst)) return;
         const dsoa_inst I = a.inst[k];
         if (I.state != DSOA_INST_RUN) return;
         uint32_t* cellp = dsoa_column<uint32_t>(c, t, bid, 1) + s;
@@ -117,6 +142,7 @@ struct FishMoveDeferred {
         const uint32_t tg = dsoa_column<uint32_t>(c, t, bid, 3)[s];
         uint32_t age = *agep + 1u;
         const uint32_t old = *cellp;
+        if (tg != kNone && (!dsoa_index_ok(c, tg, cells_of(I)) || !dsoa_index_ok(c, old, cells_of(I)))) return;
         if (tg != kNone && I.claim[tg] == old) {
             I.claim[tg] = kNone;
             I.occ[tg] = 1;
@@ -135,26 +161,25 @@ struct SharkChoose {
     using Args = dsoa_wator_args;
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
-        const dsoa_inst I = a.inst[dsoa_column<uint32_t>(c, t, bid, 0)[s]];
+        const uint32_t ik = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, ik, a.n_inst)) return;
+        const dsoa_inst I = a.inst[ik];
         if (I.state != DSOA_INST_RUN) return;
         const uint32_t cell = dsoa_column<uint32_t>(c, t, bid, 1)[s];
-        uint32_t nb[4], cand[4], k = 0;
+        if (!dsoa_index_ok(c, cell, cells_of(I))) return;
+        uint32_t nb[4], fish = 0u, empty = 0u;
         neighbours(cell, I.w, I.h, nb);
-        uint8_t o[4];
 #pragma unroll
-        for (int d = 0; d < 4; ++d) o[d] = I.occ[nb[d]];
-#pragma unroll
-        for (int d = 0; d < 4; ++d)
-            if (o[d] == 1) cand[k++] = nb[d];
-        const uint32_t eat = k ? 1u : 0u;
-        if (!k) {
-#pragma unroll
-            for (int d = 0; d < 4; ++d)
-                if (o[d] == 0) cand[k++] = nb[d];
+        for (int d = 0; d < 4; ++d) {
+            const uint8_t o = I.occ[nb[d]];
+            fish |= (o == 1 ? 1u : 0u) << d;
+            empty |= (o == 0 ? 1u : 0u) << d;
         }
+        const uint32_t eat = fish ? 1u : 0u;
+        const uint32_t m = fish ? fish : empty;          /* fish first, else empty cells */
         uint32_t tg = kNone;
-        if (k) {
-            tg = cand[pick(k, I.seed, I.t, cell, 2u)];
+        if (m) {
+            tg = nth_candidate(nb, m, pick((uint32_t)__popc(m), I.seed, I.t, cell, 2u));
             atomicMin(&I.claim[tg], cell);
         }
         dsoa_column<uint32_t>(c, t, bid, 4)[s] = tg;
@@ -167,12 +192,15 @@ struct SharkMove {
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         dsoa_prefetch_hint(c, t);
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, k, a.n_inst)) return;
         const dsoa_inst I = a.inst[k];
         if (I.state != DSOA_INST_RUN) return;
         uint32_t* cellp = dsoa_column<uint32_t>(c, t, bid, 1) + s;
         uint32_t* agep = dsoa_column<uint32_t>(c, t, bid, 2) + s;
         uint32_t* enp = dsoa_column<uint32_t>(c, t, bid, 3) + s;
         const uint32_t tg = dsoa_column<uint32_t>(c, t, bid, 4)[s];
+        if (!dsoa_index_ok(c, *cellp, cells_of(I))) return;
+        if (tg != kNone && !dsoa_index_ok(c, tg, cells_of(I))) return;
         const dsoa_obj me = dsoa_make_handle(t, bid, s);
         const uint32_t age = *agep + 1u;
         *agep = age;
@@ -233,6 +261,7 @@ struct Kill {
     static constexpr bool kNoNewOfOwnType = true;   /* streamable */
     static __device__ void run(const dsoa_ctx& c, uint32_t t, uint64_t bid, uint32_t s, const Args& a) {
         const uint32_t k = dsoa_column<uint32_t>(c, t, bid, 0)[s];
+        if (!dsoa_index_ok(c, k, a.n_inst)) return;
         if (a.inst[k].state == DSOA_INST_KILL) dsoa_delete(c, dsoa_make_handle(t, bid, s));
     }
 };

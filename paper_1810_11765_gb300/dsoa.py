@@ -20,9 +20,10 @@ ERRORS = {-1: "invalid argument", -2: "heap layout already frozen", -3: "too man
           -7: "unknown built-in method", -8: "synchronous call during stream capture",
           -9: "heap larger than the fixed no-allocation scratch allows"}
 
-DEV_OOM, DEV_SPIN, DEV_DOUBLE_FREE, DEV_BAD_HANDLE = 1, 2, 4, 8
+DEV_OOM, DEV_SPIN, DEV_DOUBLE_FREE, DEV_BAD_HANDLE, DEV_BAD_INDEX = 1, 2, 4, 8, 16
 FLAG_NO_COALESCE, FLAG_NO_ROTATE, FLAG_NO_HINT, FLAG_FUSED, FLAG_PDL = 1, 2, 4, 8, 16
 FLAG_ENUM_TICKETS = 32
+FLAG_NO_FRESH_GROUP, FLAG_PAPER_R = 128, 256
 CHECK_NAMES = ["hier", "free_xor", "multi_type", "active_subset", "type", "free_word",
                "empty_alloc", "active_exact", "tail_bits", "cap_bits"]
 CAPACITY_UNIFORM, CAPACITY_PER_TYPE = 0, 1
@@ -33,6 +34,7 @@ M_MICRO_GATHER, M_MICRO_STATS, M_MICRO_SCALE_TMA, M_MICRO_DELETE_ALL = 104, 105,
 M_MICRO_HANDLES = 108
 K_MICRO_DEVICE_DO = 150
 K_MICRO_ATOMIC_PEAK = 151
+K_MICRO_NEW_EACH = 152
 C_GOL_CELL, M_GOL_SPREAD, M_GOL_REAP, M_GOL_DECIDE, M_GOL_READ, M_GOL_KILL = 200, 201, 202, 203, 204, 205
 K_GOL_ADVANCE = 250
 M_WATOR_FISH_CHOOSE, M_WATOR_FISH_MOVE, M_WATOR_SHARK_CHOOSE, M_WATOR_SHARK_MOVE = 301, 302, 303, 304

@@ -56,14 +56,39 @@ def frag_over_time(steps=500, every=25):
     return {"experiment": "fragmentation over time (Fig. 10d)", "rows": rows, "device_errors": err}
 
 
-def frag_vs_lookups(rs=(1, 2, 3, 5, 8), steps=300):
+FRAG_VARIANTS = {
+    # this runtime: r bounds the failed try_find_set calls of one round; a group of
+    # 16+ requests takes a fresh block after a lost round; per-warp block hint
+    "dsoa": 0,
+    "no_hint": D.FLAG_NO_HINT,
+    "no_fresh_group": D.FLAG_NO_FRESH_GROUP,
+    # Alg. 1's reading of r: every active-block attempt counts, lost reservations
+    # included, and after r of them the allocation takes a fresh block
+    "paper_r": D.FLAG_PAPER_R,
+    "paper_r_no_hint": D.FLAG_PAPER_R | D.FLAG_NO_HINT,
+}
+
+
+def frag_vs_lookups(rs=(1, 2, 3, 5, 8), steps=300, variants=None):
+    """Fragmentation F after `steps` plain steps against r, for the allocation
+    policies of FRAG_VARIANTS, with the mean step time of the last 50 steps."""
     rows = []
-    for r in rs:
-        heap, w = _world(lookups=r)
-        for _ in range(steps):
-            w.step()
-        rows.append(dict(r=r, **_frag(heap, w), device_errors=heap.get_error()))
-        heap.close()
+    for name in (variants or FRAG_VARIANTS):
+        fl = FRAG_VARIANTS[name]
+        for r in rs:
+            heap, w = _world(lookups=r, flags=fl)
+            for _ in range(steps - 50):
+                w.step()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(50):
+                w.step()
+            b.record()
+            b.synchronize()
+            rows.append(dict(variant=name, r=r, **_frag(heap, w), ms_per_step=a.elapsed_time(b) / 50,
+                             device_errors=heap.get_error()))
+            heap.close()
     return {"experiment": f"fragmentation after {steps} steps vs active-block lookups r (Fig. 11)", "rows": rows}
 
 
@@ -85,13 +110,20 @@ def ablation(steps=200):
     variants = {"dsoa": 0, "no_coalesce": D.FLAG_NO_COALESCE, "no_rotate": D.FLAG_NO_ROTATE,
                 "no_coalesce_no_rotate": D.FLAG_NO_COALESCE | D.FLAG_NO_ROTATE,
                 "no_hint": D.FLAG_NO_HINT, "fused": D.FLAG_FUSED}
-    rows = []
+    rows, ref = [], None
     for name, fl in variants.items():
         heap, w = _world(heap_bytes=2 << 30, flags=fl)
         t = _timed_steps(heap, w, steps, flush)
+        pops, grid = w.counts(), w.read(0)
+        if ref is None:
+            ref = (pops, grid)
         rows.append(dict(variant=name, steps_per_s=steps / (sum(t) / 1e3), median_ms=statistics.median(t),
-                         **_frag(heap, w), device_errors=heap.get_error()))
+                         **_frag(heap, w), device_errors=heap.get_error(), fish_sharks=list(pops),
+                         same_as_dsoa=bool(pops == ref[0] and (grid == ref[1]).all())))
         heap.close()
+    base = rows[0]["steps_per_s"]
+    for r in rows:
+        r["slowdown_vs_dsoa"] = base / r["steps_per_s"]
     return {"experiment": f"ablations, {steps} plain steps (Fig. 10c)", "rows": rows}
 
 

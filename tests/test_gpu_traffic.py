@@ -58,31 +58,41 @@ def test_deterministic_limit():
 
 
 def test_full_config_sampled_rings():
+    from concurrent.futures import ThreadPoolExecutor
     from paper_1810_11765_gb300 import inputs
     L, thr = inputs.traffic_instances()
     seed = inputs.SEED_TRAFFIC
-    heap, w = world(L, thr, seed, heap_bytes=512 << 20)
     base = np.concatenate([[0], np.cumsum(L.astype(np.int64))])
     order = np.argsort(L)
-    sample = [int(order[0]), int(order[1]), int(order[len(L) // 2])]
+    # the two shortest, the median and the two longest rings (about 2^20 cells:
+    # the longest gaps and the most cars of the batch), against the oracle run
+    # of each ring alone; the oracle (C through ctypes, which releases the GIL)
+    # runs in threads while the GPU steps
+    sample = [int(order[0]), int(order[1]), int(order[len(L) // 2]), int(order[-2]), int(order[-1])]
     checkpoints = [100, 1000]
+    pool = ThreadPoolExecutor(max_workers=len(sample) * len(checkpoints))
+    ref = {(k, i): pool.submit(oracle.traffic_run, [L[i]], [thr[i]], k, seed=seed, first_ring=i)
+           for k in checkpoints for i in sample}
+    heap, w = world(L, thr, seed, heap_bytes=512 << 20)
     for k in checkpoints:
         while w.steps_done < k:
             w.step()
         go, gv = w.read()
         for i in sample:
-            o, v, _ = oracle.traffic_run([L[i]], [thr[i]], k, seed=seed, first_ring=i)
+            o, v, _ = ref[(k, i)].result()
             assert np.array_equal(go[base[i]:base[i + 1]], o), (k, i)
             assert np.array_equal(gv[base[i]:base[i + 1]], v), (k, i)
+    pool.shutdown()
     # at any size: cars occupy distinct cells, speeds within [0, 5], count matches
     assert heap.count(w.car_type) == int(go.sum())
     assert gv.max() <= 5 and np.all(gv[~go.astype(bool)] == 0)
     assert heap.get_error() == 0
 
 
-@pytest.mark.parametrize("flags", [16])
-def test_programmatic_dependent_launch(flags):
-    """The batch stepped with programmatic dependent launch equals the oracle."""
+@pytest.mark.parametrize("flags", [16, 256, 128 | 16])
+def test_launch_flags_keep_semantics(flags):
+    """The batch stepped with programmatic dependent launch (16) and / or the
+    allocation-policy experiment flags (128, 256) equals the oracle."""
     L = [16, 23, 300, 4096, 5000]
     thr = [int(d * 2**32) for d in (0.3, 0.6, 0.2, 0.1, 0.3)]
     seed = 78

@@ -163,3 +163,29 @@ def test_user_method_covers_subtypes(user_lib):
     assert np.array_equal(x[sel].view(np.uint32), x_ref[sel].view(np.uint32))
     assert heap.get_error() == 0
     heap.close()
+
+
+def test_prologue_runs_once_per_do_all_of_a_family(user_lib):
+    """A do-all on a type with subtypes launches the method once per member type;
+    a method's prologue (per-launch work such as advancing step counters) must
+    still run once per dsoa_parallel_do, in plain and in enumerated do-alls."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import Micro
+    TALLY = 1003
+    heap = D.Heap(64 << 20)
+    m = Micro(0, SEED, 4000, heap=heap, sub_fields=[8], sub_share=0.5)
+    m.new(0)
+    assert heap.count(m.type) > 0 and heap.count(m.sub_type) > 0
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    args = UserArgs(out=cnt.data_ptr())
+    for k in range(1, 4):
+        heap.parallel_do(m.type, TALLY, args)
+        torch.cuda.synchronize()
+        assert int(cnt.item()) == k
+    heap.parallel_do_enumerated(m.type, TALLY, args)
+    heap.parallel_do(m.sub_type, TALLY, args)           # the subtype alone: one launch
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == 5
+    assert heap.get_error() == 0
+    heap.close()

@@ -94,7 +94,8 @@ def test_batched_instances_match_alone():
                                           (dict(), 8), (dict(tpb=512, ctas_per_sm=1), 12),
                                           (dict(waves=1), 0), (dict(tpb=128, slots_per_thread=2, waves=16), 0),
                                           (dict(), 16), (dict(tpb=128, scan_tiles=2, waves=8), 16),
-                                          (dict(tpb=512, ctas_per_sm=1, waves=1), 20)])
+                                          (dict(tpb=512, ctas_per_sm=1, waves=1), 20),
+                                          (dict(), 128), (dict(tpb=128, waves=8), 256 | 16), (dict(waves=1), 384 | 4)])
 def test_graph_captured_steps_match_oracle(launch, flags):
     """One step captured as a CUDA graph and replayed: the step index lives in
     device memory, so replays advance the simulation exactly like plain steps."""
@@ -120,6 +121,27 @@ def test_graph_captured_steps_match_oracle(launch, flags):
     assert counts == (st[-1]["fish"], st[-1]["sharks"])
     assert heap.get_error() == 0
     g.close()
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_ablations_finish_with_the_oracle_result(flags):
+    """NoCoal, NoShift and both (Sec. 6.4, Fig. 10c) on a 256 x 256 world: slower
+    placement, same simulation, no device error."""
+    W, H, steps, seed = 256, 256, 40, 0x5EED0003
+    heap, w = world(64 << 20)
+    heap.set_flags(flags)
+    slot = w.add(W, H, seed)
+    _, st = oracle.wator_run(W, H, steps, seed=seed)
+    for k in range(steps):
+        w.step()
+        if k % 10 == 9:
+            assert w.counts() == (st[k]["fish"], st[k]["sharks"]), k
+    ref, _ = oracle.wator_run(W, H, steps, seed=seed)
+    assert np.array_equal(w.read(slot), ref)
+    assert heap.get_error() == 0
+    host = host_check(heap, 2)
+    assert all(v == 0 for v in host["violations"].values()), host
+    heap.close()
 
 
 @pytest.mark.parametrize("scan", [1, 2, 3, 4])

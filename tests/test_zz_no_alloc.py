@@ -103,3 +103,57 @@ def test_rejects_what_it_cannot_hold():
     assert big.info()["num_blocks"] > 4096 * 4096
     assert no_alloc_enumeration(big, t) == -9
     big.close()
+
+
+def test_allocates_nothing_and_can_be_captured_in_global_mode():
+    """The property the entry point exists for, shown two ways after one warm-up
+    call: device free memory and torch's reserved memory are unchanged across
+    calls, and a call captured in global capture mode (where a cudaMalloc or
+    cudaFree from any thread would invalidate the capture) replays to the same
+    result as dsoa_enumerate."""
+    import torch
+    from paper_1810_11765_gb300 import dsoa as D
+    from paper_1810_11765_gb300.apps import Micro
+    s = torch.cuda.Stream()
+    m = Micro(64 << 20, SEED, 1 << 18, stream=s)
+    m.round(0)
+    M = m.heap.info()["num_blocks"]
+    R = torch.full((M,), -1, dtype=torch.int32, device="cuda")
+    occ = torch.zeros(M, dtype=torch.int64, device="cuda")
+    r = torch.zeros(1, dtype=torch.int32, device="cuda")
+    L = D.load()
+
+    def call():
+        return L.dsoa_enumerate_noalloc(m.heap.handle, m.type, R.data_ptr(), occ.data_ptr(), r.data_ptr(), M)
+
+    torch.cuda.synchronize()
+    assert call() == 0                               # warm-up: the array's address
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    for _ in range(3):
+        assert call() == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
+
+    R.fill_(-1)
+    occ.zero_()
+    r.zero_()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="global"):
+        rc = call()
+    assert rc == 0
+    assert int(r.cpu().item()) == 0                  # captured, not run
+    g.replay()
+    torch.cuda.synchronize()
+    Rr, occr, rr = m.heap.enumerate(m.type)
+    torch.cuda.synchronize()
+    n = int(torch.as_tensor(_DeviceArray(rr, 1, "<i4"), device="cuda").cpu().item())
+    ref_R = torch.as_tensor(_DeviceArray(Rr, n, "<i4"), device="cuda").cpu().numpy().view(np.uint32)
+    ref_occ = torch.as_tensor(_DeviceArray(occr, n, "<i8"), device="cuda").cpu().numpy().view(np.uint64)
+    assert n > 4096 and int(r.cpu().item()) == n
+    assert np.array_equal(R[:n].cpu().numpy().view(np.uint32), ref_R)
+    assert np.array_equal(occ[:n].cpu().numpy().view(np.uint64), ref_occ)
+    del g
+    m.heap.close()

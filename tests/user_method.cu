@@ -6,6 +6,8 @@
 //   1000 scale   x = x * 1.5 + id (every operation rounded to nearest)
 //   1001 spawn   allocate one object of args.other_type holding this id
 //   1002 mark    out[id] = 1 for a live object of a type whose field 0 is an id
+//   1003 tally   a prologue that adds 1 to *(uint32_t*)out once per launch that
+//                runs it (CTA 0, thread 0); the per-object method does nothing
 #include "dsoa_device.cuh"
 
 struct UserArgs {
@@ -39,6 +41,15 @@ struct UserMark {
     }
 };
 
+struct UserTally {
+    typedef UserArgs Args;
+    static __device__ void prologue(const dsoa_ctx&, const Args& a) {
+        if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned int*>(a.out), 1u);
+    }
+    static __device__ void run(const dsoa_ctx&, uint32_t, uint64_t, uint32_t, const Args&) {}
+};
+
 DSOA_METHOD(1000, user_scale, UserScale)
 DSOA_METHOD(1001, user_spawn, UserSpawn)
 DSOA_METHOD(1002, user_mark, UserMark)
+DSOA_METHOD(1003, user_tally, UserTally)
