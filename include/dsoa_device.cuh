@@ -67,12 +67,24 @@
 
 /* Entry of the per-warp block hint table: a block of the type that still had
  * free slots when this warp slot last reserved in it, and the free-slot word
- * that reservation left.  Advisory only (any value is safe). */
+ * that reservation left; and the level-0 word of the free-block bitmap this
+ * warp slot last took a block from, with the free bits that take left.
+ * Advisory only (any value is safe). */
 struct __align__(16) dsoa_hint {
     unsigned long long free;             /* free slots as last seen (1 = free)     */
     uint64_t block;                      /* block id, DSOA_NO_HINT_BLOCK if none   */
+    unsigned long long fword;            /* free blocks of level-0 word fidx as
+                                            last seen (1 = free)                   */
+    uint64_t fidx;                       /* level-0 word index of the free-block
+                                            bitmap, >= its word count if none      */
 };
 #define DSOA_NO_HINT_BLOCK (~0ull)
+#ifdef __CUDACC__
+/* the block half {free, block} of a hint entry, one 16-byte store */
+__device__ __forceinline__ void dsoa_hint_put(dsoa_hint* hp, unsigned long long free, uint64_t block) {
+    *reinterpret_cast<ulonglong2*>(hp) = make_ulonglong2(free, (unsigned long long)block);
+}
+#endif
 
 /* Device view of a heap.  Plain data, passed to kernels by value. */
 struct dsoa_ctx {
@@ -130,6 +142,8 @@ struct dsoa_ctx {
 #define DSOA_FLAG_NO_FRESH_GROUP 128u     /* experiment: large groups keep searching
                                              active blocks after a lost round, like
                                              small ones (no fresh-block shortcut)   */
+#define DSOA_FLAG_LOW_FIRST 512u          /* active-block search biased toward low block
+                                             indices (dsoa_bm_find_low)             */
 #define DSOA_FLAG_PAPER_R 256u            /* experiment: r counts every active-block
                                              attempt of an allocation, lost
                                              reservations included, and after r of
@@ -213,6 +227,12 @@ __device__ __forceinline__ uint32_t dsoa_smid() {
     return s;
 }
 
+/* Release fence before the store that publishes a block initialisation (the
+ * slot word): with the acquire RMW that reserves slots it orders the block's
+ * type store before any reservation that sees the slot word (a release
+ * pattern: fence.acq_rel, then a strong store). */
+__device__ __forceinline__ void dsoa_fence_release() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 /* An index that a method read from an object field (an instance, a grid cell,
  * a ring), checked before it addresses an application array: out of range
  * raises DSOA_DEV_BAD_INDEX and the method skips the object.  In a consistent
@@ -273,7 +293,8 @@ __device__ __forceinline__ unsigned long long* dsoa_level(const dsoa_ctx& c, uin
  * Returns whether this thread changed the level-l bit.
  * ------------------------------------------------------------------------ */
 __device__ inline bool dsoa_bm_clear(const dsoa_ctx& c, uint32_t b, uint64_t pos,
-                                     bool blocking, uint32_t l = 0) {
+                                     bool blocking, uint32_t l = 0,
+                                     unsigned long long* first_prev = nullptr) {
     bool first = true, changed = false;
     for (; l < c.nlevels; ++l) {
         unsigned long long* w = dsoa_level(c, b, l) + (pos >> 6);
@@ -282,6 +303,7 @@ __device__ inline bool dsoa_bm_clear(const dsoa_ctx& c, uint32_t b, uint64_t pos
         uint32_t spins = 0;
         for (;;) {
             prev = atomicAnd(w, ~m);
+            if (first && first_prev) *first_prev = prev;
             if (prev & m) break;
             if (!blocking) return false;
             if (!dsoa_backoff(c, spins)) return changed;
@@ -330,14 +352,45 @@ __device__ inline int64_t dsoa_bm_find(const dsoa_ctx& c, uint32_t b, uint32_t h
     return (int64_t)idx;
 }
 
+/* try_find_set biased toward low block indices, for the active-block search
+ * (not in the paper).  Above level 0 it takes one of the DSOA_LOW_SPREAD lowest
+ * set bits of each container (a hash chooses which), at level 0 a rotated bit
+ * of the word, so allocations concentrate on the lowest few hundred blocks
+ * with free slots while the choice still spreads warps over several of them.
+ * Rotation over the whole bitmap fills every partly used block at the same
+ * rate, so none drains as a population shrinks; filling the low blocks first
+ * lets the high ones empty and return to the free bitmap, as a first-fit
+ * allocator's do (Sec. 6.4 fragmentation). */
+#define DSOA_LOW_SPREAD 4u
+__device__ inline int64_t dsoa_bm_find_low(const dsoa_ctx& c, uint32_t b, uint32_t h) {
+    uint64_t idx = 0;
+    for (int l = (int)c.nlevels - 1; l >= 0; --l) {
+        const unsigned long long w = dsoa_ld(dsoa_level(c, b, (uint32_t)l) + idx);
+        if (!w) return -1;
+        uint32_t bit;
+        if (l > 0) {
+            const uint32_t n = (uint32_t)__popcll(w);
+            const uint32_t k = ((h >> ((uint32_t)l * 5u)) ^ (h >> 27)) % (n < DSOA_LOW_SPREAD ? n : DSOA_LOW_SPREAD);
+            bit = dsoa_nth_set(w, k);
+        } else {
+            const uint32_t r = (h ^ (h >> 17)) & 63u;
+            bit = ((uint32_t)__ffsll((long long)dsoa_rotr(w, r)) - 1u + r) & 63u;
+        }
+        idx = idx * 64u + bit;
+    }
+    return (int64_t)idx;
+}
+
 /* clear() = find-and-clear an arbitrary set bit (Sec. 4.1.2).  -1 when the
  * bitmap is empty at the top (OOM for the free-block bitmap), -2 when
- * DSOA_TAKE_ATTEMPTS attempts lost every race (the caller retries). */
-static __device__ __noinline__ int64_t dsoa_bm_take(const dsoa_ctx& c, uint32_t b, uint32_t h) {
+ * DSOA_TAKE_ATTEMPTS attempts lost every race (the caller retries).
+ * prev0, if given, receives the level-0 word as the successful clear found it. */
+static __device__ __noinline__ int64_t dsoa_bm_take(const dsoa_ctx& c, uint32_t b, uint32_t h,
+                                                    unsigned long long* prev0 = nullptr) {
     for (uint32_t a = 0; a < DSOA_TAKE_ATTEMPTS; ++a) {
         const int64_t pos = dsoa_bm_find(c, b, dsoa_hash(h + a * 0x9E3779B9u));
         if (pos >= 0) {
-            if (dsoa_bm_clear(c, b, (uint64_t)pos, false)) return pos;
+            if (dsoa_bm_clear(c, b, (uint64_t)pos, false, 0, prev0)) return pos;
         } else if (dsoa_ld(dsoa_level(c, b, c.nlevels - 1)) == 0ull) {
             return -1;
         }
@@ -353,7 +406,7 @@ static __device__ __noinline__ int64_t dsoa_bm_take(const dsoa_ctx& c, uint32_t 
 /* initialize_block<T> (Alg. 9): type first, fence, then all 64 slots free. */
 __device__ inline void dsoa_block_init(const dsoa_ctx& c, uint64_t bid, uint32_t t) {
     dsoa_st32(&c.btype[bid], t);
-    __threadfence();
+    dsoa_fence_release();
     dsoa_st(&c.slot[bid], DSOA_ALL);
 }
 
@@ -416,13 +469,40 @@ __device__ __forceinline__ void dsoa_block_release(const dsoa_ctx& c, uint32_t t
  * unless the reservation filled it.  Slots are only ever taken from the word,
  * so nobody can take these, and a block with reserved slots cannot be emptied,
  * invalidated or retyped: no reservation atomic and no type re-check are needed.
+ * The free block comes, when it can, from the level-0 free-bitmap word this
+ * warp slot took its previous block from (the hint's fword / fidx): one
+ * atomicAnd on a bit the hint still shows free, instead of the top-down find
+ * (one dependent load per level) and its clear; a hint that is stale costs that
+ * one atomic, then the find runs.  Emptying the word propagates as in clear().
  * -1 = no free block, -2 = every attempt lost its race. */
 static __device__ __noinline__ int64_t dsoa_block_new_reserved(const dsoa_ctx& c, uint32_t t, uint32_t h,
-                                                               unsigned long long mask) {
-    const int64_t bid = dsoa_bm_take(c, dsoa_bm_free(), h);
-    if (bid < 0) return bid;
+                                                               unsigned long long mask, dsoa_hint* hp) {
+    int64_t bid = -1;
+    unsigned long long* L0f = dsoa_level(c, dsoa_bm_free(), 0);
+    if (hp) {
+        const ulonglong2 fh = *reinterpret_cast<const ulonglong2*>(&hp->fword);
+        if (fh.y < c.lvl_words[0] && fh.x) {
+            const uint32_t r = h & 63u;
+            const uint32_t bit = ((uint32_t)__ffsll((long long)dsoa_rotr(fh.x, r)) - 1u + r) & 63u;
+            const unsigned long long m = 1ull << bit;
+            const unsigned long long prev = atomicAnd(L0f + fh.y, ~m);
+            *reinterpret_cast<ulonglong2*>(&hp->fword) = make_ulonglong2(prev & ~m, fh.y);
+            if (prev & m) {
+                bid = (int64_t)(fh.y * 64u + bit);
+                if (prev == m && c.nlevels > 1) dsoa_bm_clear(c, dsoa_bm_free(), fh.y, true, 1);
+            }
+        }
+    }
+    if (bid < 0) {
+        unsigned long long prev = 0ull;
+        bid = dsoa_bm_take(c, dsoa_bm_free(), h, &prev);
+        if (bid < 0) return bid;
+        if (hp)
+            *reinterpret_cast<ulonglong2*>(&hp->fword) =
+                make_ulonglong2(prev & ~(1ull << ((uint64_t)bid & 63u)), (unsigned long long)bid >> 6);
+    }
     dsoa_st32(&c.btype[bid], t);
-    __threadfence();
+    dsoa_fence_release();
     dsoa_st(&c.slot[bid], DSOA_ALL & ~mask);
     /* allocated[t] and active[t]: both level-0 RMWs in flight together; each
      * falls back to dsoa_bm_set's retry loop if its bit was already set, and
@@ -474,6 +554,7 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
     uint32_t empty_free = 0;   /* rounds that found the free-block bitmap empty */
     const uint32_t max_rounds = rot ? DSOA_ALLOC_ROUNDS : DSOA_ALLOC_ROUNDS_NO_ROTATE;
     const bool paper_r = (c.flags & DSOA_FLAG_PAPER_R) != 0u;
+    const bool low = rot && (c.flags & DSOA_FLAG_LOW_FIRST) != 0u;
     const bool fresh_group = want >= DSOA_FRESH_GROUP && !(c.flags & DSOA_FLAG_NO_FRESH_GROUP);
     uint32_t tries = 0;        /* paper_r: active-block attempts so far, lost ones included */
     for (uint32_t round = 0; round < max_rounds; ++round) {
@@ -484,8 +565,8 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
         int64_t bid = -1;
         unsigned long long w = 0ull;   /* free slots of bid, if already known */
         if (round == 0 && hp) {
-            const dsoa_hint hv = *hp;
-            if (hv.block < c.M && hv.free) { bid = (int64_t)hv.block; w = hv.free; }
+            const ulonglong2 hv = *reinterpret_cast<const ulonglong2*>(hp);   /* {free, block} */
+            if (hv.y < c.M && hv.x) { bid = (int64_t)hv.y; w = hv.x; }
         }
         /* After a lost race (round >= 1) a group of DSOA_FRESH_GROUP or more
          * requests takes a fresh block instead of searching active[t] again: when
@@ -497,14 +578,16 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
                                     : (round == 0 || empty_free || !fresh_group);
         if (paper_r) {                 /* at most r finds per round, r attempts in all */
             for (uint32_t a = 0; search && bid < 0 && a < c.lookups && (tries < c.lookups || empty_free); ++a, ++tries)
-                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u));
+                bid = low ? dsoa_bm_find_low(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u))
+                          : dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u));
         } else {
             for (uint32_t a = 0; search && a < c.lookups && bid < 0; ++a)
-                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
+                bid = low ? dsoa_bm_find_low(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u))
+                          : dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
         }
         if (bid < 0) {
             const unsigned long long fmask = dsoa_lowest_k(c.cap[t], want);
-            bid = dsoa_block_new_reserved(c, t, h ^ round, fmask);
+            bid = dsoa_block_new_reserved(c, t, h ^ round, fmask, hp);
             if (bid == -2) continue;
             if (bid < 0) {
                 /* No free block.  Blocks that other warps initialised in the
@@ -516,7 +599,7 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
                 continue;
             }
             const unsigned long long left = c.cap[t] & ~fmask;    /* fresh block: reserved on init */
-            if (hp) *hp = dsoa_hint{left, left ? (uint64_t)bid : DSOA_NO_HINT_BLOCK};
+            if (hp) dsoa_hint_put(hp, left, left ? (uint64_t)bid : DSOA_NO_HINT_BLOCK);
             *bid_out = (uint64_t)bid;
             return fmask;
         }
@@ -532,7 +615,7 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
         const unsigned long long got = before & mask;
         if (!got) {
             const unsigned long long left = before & c.cap[t];
-            if (hp) *hp = dsoa_hint{left, left ? (uint64_t)bid : DSOA_NO_HINT_BLOCK};
+            if (hp) dsoa_hint_put(hp, left, left ? (uint64_t)bid : DSOA_NO_HINT_BLOCK);
             continue;
         }
         const uint32_t bt = dsoa_ld32(&c.btype[bid]);
@@ -544,11 +627,11 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
         const bool full = left == 0ull && (before & capb) != 0ull;
         if (full) dsoa_block_deactivate(c, bt, (uint64_t)bid);
         if (bt != t) {                 /* block replaced by another type: roll back */
-            if (hp) *hp = dsoa_hint{0ull, DSOA_NO_HINT_BLOCK};
+            if (hp) dsoa_hint_put(hp, 0ull, DSOA_NO_HINT_BLOCK);
             dsoa_rollback(c, bt, (uint64_t)bid, got);
             continue;
         }
-        if (hp) *hp = dsoa_hint{left, full ? DSOA_NO_HINT_BLOCK : (uint64_t)bid};
+        if (hp) dsoa_hint_put(hp, left, full ? DSOA_NO_HINT_BLOCK : (uint64_t)bid);
         *bid_out = (uint64_t)bid;
         return got;
     }

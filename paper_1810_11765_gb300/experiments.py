@@ -44,16 +44,25 @@ def _frag(heap, w):
             "F": 1.0 - objs / slots if slots else 0.0}
 
 
-def frag_over_time(steps=500, every=25):
-    heap, w = _world()
-    rows = [dict(step=0, **_frag(heap, w))]
-    for k in range(1, steps + 1):
-        w.step()
-        if k % every == 0:
-            rows.append(dict(step=k, **_frag(heap, w)))
-    err = heap.get_error()
-    heap.close()
-    return {"experiment": "fragmentation over time (Fig. 10d)", "rows": rows, "device_errors": err}
+def frag_over_time(steps=500, every=25, variants=("dsoa", "low_first")):
+    """F every `every` steps (Fig. 10d) for allocation policies of FRAG_VARIANTS,
+    with the time of each stretch of `every` plain steps."""
+    out = {"experiment": "fragmentation over time (Fig. 10d)", "variants": {}}
+    for name in variants:
+        heap, w = _world(flags=FRAG_VARIANTS[name])
+        rows = [dict(step=0, **_frag(heap, w))]
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k in range(1, steps + 1):
+            w.step()
+            if k % every == 0:
+                b.record()
+                b.synchronize()
+                rows.append(dict(step=k, ms_per_step=a.elapsed_time(b) / every, **_frag(heap, w)))
+                a.record()
+        out["variants"][name] = {"rows": rows, "device_errors": heap.get_error()}
+        heap.close()
+    return out
 
 
 FRAG_VARIANTS = {
@@ -66,6 +75,9 @@ FRAG_VARIANTS = {
     # included, and after r of them the allocation takes a fresh block
     "paper_r": D.FLAG_PAPER_R,
     "paper_r_no_hint": D.FLAG_PAPER_R | D.FLAG_NO_HINT,
+    # active-block search biased toward low block indices (first-fit-like)
+    "low_first": D.FLAG_LOW_FIRST,
+    "low_first_no_fresh_group": D.FLAG_LOW_FIRST | D.FLAG_NO_FRESH_GROUP,
 }
 
 

@@ -131,4 +131,3 @@ def test_register_subtype_rejects_bad_requests():
     with pytest.raises(D.DsoaError):
         heap.register_subtype(t, [4])                        # after the freeze
     heap.close()
-
