@@ -142,8 +142,6 @@ struct dsoa_ctx {
 #define DSOA_FLAG_NO_FRESH_GROUP 128u     /* experiment: large groups keep searching
                                              active blocks after a lost round, like
                                              small ones (no fresh-block shortcut)   */
-#define DSOA_FLAG_LOW_FIRST 512u          /* active-block search biased toward low block
-                                             indices (dsoa_bm_find_low)             */
 #define DSOA_FLAG_PAPER_R 256u            /* experiment: r counts every active-block
                                              attempt of an allocation, lost
                                              reservations included, and after r of
@@ -352,35 +350,6 @@ __device__ inline int64_t dsoa_bm_find(const dsoa_ctx& c, uint32_t b, uint32_t h
     return (int64_t)idx;
 }
 
-/* try_find_set biased toward low block indices, for the active-block search
- * (not in the paper).  Above level 0 it takes one of the DSOA_LOW_SPREAD lowest
- * set bits of each container (a hash chooses which), at level 0 a rotated bit
- * of the word, so allocations concentrate on the lowest few hundred blocks
- * with free slots while the choice still spreads warps over several of them.
- * Rotation over the whole bitmap fills every partly used block at the same
- * rate, so none drains as a population shrinks; filling the low blocks first
- * lets the high ones empty and return to the free bitmap, as a first-fit
- * allocator's do (Sec. 6.4 fragmentation). */
-#define DSOA_LOW_SPREAD 4u
-__device__ inline int64_t dsoa_bm_find_low(const dsoa_ctx& c, uint32_t b, uint32_t h) {
-    uint64_t idx = 0;
-    for (int l = (int)c.nlevels - 1; l >= 0; --l) {
-        const unsigned long long w = dsoa_ld(dsoa_level(c, b, (uint32_t)l) + idx);
-        if (!w) return -1;
-        uint32_t bit;
-        if (l > 0) {
-            const uint32_t n = (uint32_t)__popcll(w);
-            const uint32_t k = ((h >> ((uint32_t)l * 5u)) ^ (h >> 27)) % (n < DSOA_LOW_SPREAD ? n : DSOA_LOW_SPREAD);
-            bit = dsoa_nth_set(w, k);
-        } else {
-            const uint32_t r = (h ^ (h >> 17)) & 63u;
-            bit = ((uint32_t)__ffsll((long long)dsoa_rotr(w, r)) - 1u + r) & 63u;
-        }
-        idx = idx * 64u + bit;
-    }
-    return (int64_t)idx;
-}
-
 /* clear() = find-and-clear an arbitrary set bit (Sec. 4.1.2).  -1 when the
  * bitmap is empty at the top (OOM for the free-block bitmap), -2 when
  * DSOA_TAKE_ATTEMPTS attempts lost every race (the caller retries).
@@ -554,7 +523,6 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
     uint32_t empty_free = 0;   /* rounds that found the free-block bitmap empty */
     const uint32_t max_rounds = rot ? DSOA_ALLOC_ROUNDS : DSOA_ALLOC_ROUNDS_NO_ROTATE;
     const bool paper_r = (c.flags & DSOA_FLAG_PAPER_R) != 0u;
-    const bool low = rot && (c.flags & DSOA_FLAG_LOW_FIRST) != 0u;
     const bool fresh_group = want >= DSOA_FRESH_GROUP && !(c.flags & DSOA_FLAG_NO_FRESH_GROUP);
     uint32_t tries = 0;        /* paper_r: active-block attempts so far, lost ones included */
     for (uint32_t round = 0; round < max_rounds; ++round) {
@@ -578,12 +546,10 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
                                     : (round == 0 || empty_free || !fresh_group);
         if (paper_r) {                 /* at most r finds per round, r attempts in all */
             for (uint32_t a = 0; search && bid < 0 && a < c.lookups && (tries < c.lookups || empty_free); ++a, ++tries)
-                bid = low ? dsoa_bm_find_low(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u))
-                          : dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u));
+                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u));
         } else {
             for (uint32_t a = 0; search && a < c.lookups && bid < 0; ++a)
-                bid = low ? dsoa_bm_find_low(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u))
-                          : dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
+                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
         }
         if (bid < 0) {
             const unsigned long long fmask = dsoa_lowest_k(c.cap[t], want);

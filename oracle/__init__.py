@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dsoa_oracle.c")
+_SRC_FRAG = os.path.join(_HERE, "frag_model.c")
 _HDR = os.path.join(_HERE, "dsoa_oracle.h")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liborc.so")
@@ -30,12 +31,12 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liborc.so`` (plain C11, no fp contraction)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_FRAG), os.path.getmtime(_HDR))
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
+           "-shared", "-Wall", "-Wextra", "-o", tmp, _SRC, _SRC_FRAG, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -81,6 +82,8 @@ def _load():
             lib.orc_gol_run.restype = i32
             lib.orc_wator_run.argtypes = [u32, u32, P, u64, u32, u32, u64, P, P]
             lib.orc_wator_run.restype = i32
+            lib.orc_wator_frag.argtypes = [u32, u32, u64, u32, i32, u32, P, P, P, P]
+            lib.orc_wator_frag.restype = i32
             lib.orc_traffic_run.argtypes = [u32, u32, P, P, u64, u32, u32, u32, P, P, u64,
                                             P, P, P]
             lib.orc_traffic_run.restype = i32
@@ -156,6 +159,23 @@ def wator_run(w: int, h: int, steps: int, seed: int = 0, init=None, t0: int = 0,
         raise RuntimeError("oracle wa-tor failed")
     rows = [{f: getattr(s, f) for f, _ in WatorStep._fields_} for s in stats[:steps]]
     return grid.reshape(h, w), rows
+
+
+FRAG_POLICIES = {"first_fit": 0, "best_fit": 1, "random_fit": 2}
+
+
+def wator_frag(w: int, h: int, steps: int, seed: int, policy: str = "first_fit", every: int = 25):
+    """Fragmentation of an idealised sequential allocator (frag_model.c) on the
+    Wa-Tor run: dict of arrays F, fish, sharks, blocks, one entry per `every` steps."""
+    k = steps // every
+    F = np.zeros(max(k, 1), dtype=np.float64)
+    fish, sharks, blocks = (np.zeros(max(k, 1), dtype=np.uint32) for _ in range(3))
+    rc = _load().orc_wator_frag(w, h, seed, steps, FRAG_POLICIES[policy], every, _ptr(F), _ptr(fish),
+                                _ptr(sharks), _ptr(blocks))
+    if rc != 0:
+        raise RuntimeError("oracle fragmentation model failed")
+    return {"step": np.arange(1, k + 1) * every, "F": F[:k], "fish": fish[:k], "sharks": sharks[:k],
+            "blocks": blocks[:k]}
 
 
 SLOW_THR = 858993459     # floor(0.20 * 2^32)

@@ -25,6 +25,8 @@
  *                       from the Philox known answers, hand-derived single- and
  *                       two-agent cases, conservation, order independence; 21
  *                       planted mistakes each fail at least three pins
+ *   orc_wator_frag      (frag_model.c, analysis) pinned: populations equal
+ *                       orc_wator_run's at every record; block accounting
  *   orc_traffic_run     pinned: deterministic (p=0) closed forms of Nagel &
  *                       Schreckenberg 1992, conservation, brute force on L=16
  *   orc_nbody_run       pinned: two-body closed forms (first step of a pair at
@@ -90,6 +92,15 @@ typedef struct {
 int orc_wator_run(uint32_t w, uint32_t h, const uint8_t* init, uint64_t seed,
                   uint32_t steps, uint32_t t0, uint64_t order_seed,
                   uint8_t* out_occ, orc_wator_step* stats);
+
+/* Fragmentation of an idealised sequential allocator on the Wa-Tor run drawn
+ * from `seed` (frag_model.c; analysis of Sec. 6.4, not a model of the GPU
+ * allocator): policy 0 first fit, 1 best fit, 2 random fit over 64-slot blocks.
+ * Every `every` steps one record: F = 1 - objects / (64 x blocks in use), fish,
+ * sharks and blocks (arrays of steps / every entries; any may be NULL).
+ * Returns 0 or -1. */
+int orc_wator_frag(uint32_t w, uint32_t h, uint64_t seed, uint32_t steps, int policy, uint32_t every,
+                   double* F_out, uint32_t* fish_out, uint32_t* sharks_out, uint32_t* blocks_out);
 
 /* ---- batched Nagel-Schreckenberg rings ---- */
 /* L[i], thr[i]: ring lengths and initial-density thresholds (u32 compare).

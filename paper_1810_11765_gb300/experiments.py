@@ -44,7 +44,7 @@ def _frag(heap, w):
             "F": 1.0 - objs / slots if slots else 0.0}
 
 
-def frag_over_time(steps=500, every=25, variants=("dsoa", "low_first")):
+def frag_over_time(steps=500, every=25, variants=("dsoa",)):
     """F every `every` steps (Fig. 10d) for allocation policies of FRAG_VARIANTS,
     with the time of each stretch of `every` plain steps."""
     out = {"experiment": "fragmentation over time (Fig. 10d)", "variants": {}}
@@ -75,9 +75,6 @@ FRAG_VARIANTS = {
     # included, and after r of them the allocation takes a fresh block
     "paper_r": D.FLAG_PAPER_R,
     "paper_r_no_hint": D.FLAG_PAPER_R | D.FLAG_NO_HINT,
-    # active-block search biased toward low block indices (first-fit-like)
-    "low_first": D.FLAG_LOW_FIRST,
-    "low_first_no_fresh_group": D.FLAG_LOW_FIRST | D.FLAG_NO_FRESH_GROUP,
 }
 
 

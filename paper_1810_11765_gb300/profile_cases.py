@@ -1,7 +1,7 @@
 """Small, bounded workloads for kernel profiling (ncu) and quick timing.
 
   python -m paper_1810_11765_gb300.profile_cases doall --log2n 24 [--holes] [--iters 3]
-  python -m paper_1810_11765_gb300.profile_cases wator --side 1024 --steps 3
+  python -m paper_1810_11765_gb300.profile_cases wator --side 1024 --steps 3 [--defer]
   python -m paper_1810_11765_gb300.profile_cases alloc --log2n 22
   python -m paper_1810_11765_gb300.profile_cases atomic --iters 64
   python -m paper_1810_11765_gb300.profile_cases nbody --n 16384 [--walk] [--iters 3]
@@ -52,9 +52,10 @@ def case_doall(log2n: int, holes: bool, iters: int, method: str = "vec"):
     m.heap.close()
 
 
-def case_wator(side: int, steps: int):
+def case_wator(side: int, steps: int, defer: bool = False):
     heap = D.Heap(512 << 20)
     w = WatorWorld(heap)
+    w.defer_births = defer
     heap.freeze()
     w.add(side, side, 0x5EED0003)
     for _ in range(steps):
@@ -140,12 +141,13 @@ def main():
     p.add_argument("--method", default="vec", choices=sorted(METHODS))
     p.add_argument("--side", type=int, default=1024)
     p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--defer", action="store_true", help="wator: births allocated by the births kernel")
     a = p.parse_args()
     build.build()
     if a.case == "doall":
         case_doall(a.log2n, a.holes, a.iters, a.method)
     elif a.case == "wator":
-        case_wator(a.side, a.steps)
+        case_wator(a.side, a.steps, a.defer)
     elif a.case == "atomic":
         case_atomic(a.iters)
     elif a.case == "nbody":
