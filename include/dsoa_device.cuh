@@ -142,11 +142,15 @@ struct dsoa_ctx {
 #define DSOA_FLAG_NO_FRESH_GROUP 128u     /* experiment: large groups keep searching
                                              active blocks after a lost round, like
                                              small ones (no fresh-block shortcut)   */
-#define DSOA_FLAG_PAPER_R 256u            /* experiment: r counts every active-block
-                                             attempt of an allocation, lost
-                                             reservations included, and after r of
-                                             them the allocation takes a fresh block
-                                             (Alg. 1's reading of r, Sec. 4.2)      */
+#define DSOA_FLAG_PAPER_R 256u            /* experiment: Alg. 1's reading of r alone:
+                                             every group, large ones too, searches
+                                             until r attempts (lost reservations
+                                             included) failed, then takes a fresh
+                                             block (no fresh-group shortcut)        */
+#define DSOA_FLAG_R_PER_ROUND 512u        /* experiment: the earlier policy: r bounds
+                                             the failed finds of one round, and a
+                                             group below DSOA_FRESH_GROUP searches
+                                             again in every round                   */
 #define DSOA_GRID_SCRATCH (DSOA_FUSED_MAX_CTAS + 64u)
 #define DSOA_CTX_NO_PROLOGUE (1u << 30)   /* set by the library in the context of the
                                              do-all launches that follow the first one
@@ -522,9 +526,10 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
     }
     uint32_t empty_free = 0;   /* rounds that found the free-block bitmap empty */
     const uint32_t max_rounds = rot ? DSOA_ALLOC_ROUNDS : DSOA_ALLOC_ROUNDS_NO_ROTATE;
-    const bool paper_r = (c.flags & DSOA_FLAG_PAPER_R) != 0u;
-    const bool fresh_group = want >= DSOA_FRESH_GROUP && !(c.flags & DSOA_FLAG_NO_FRESH_GROUP);
-    uint32_t tries = 0;        /* paper_r: active-block attempts so far, lost ones included */
+    const bool per_round = (c.flags & DSOA_FLAG_R_PER_ROUND) != 0u;
+    const bool fresh_group = want >= DSOA_FRESH_GROUP &&
+                             !(c.flags & (DSOA_FLAG_NO_FRESH_GROUP | DSOA_FLAG_PAPER_R));
+    uint32_t tries = 0;        /* active-block attempts so far, lost reservations included */
     for (uint32_t round = 0; round < max_rounds; ++round) {
         if (!rot && round) {           /* NoShift: thin out the races on the first bits */
             const uint32_t span = 32u << (round < 7u ? round : 7u);
@@ -536,20 +541,22 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
             const ulonglong2 hv = *reinterpret_cast<const ulonglong2*>(hp);   /* {free, block} */
             if (hv.y < c.M && hv.x) { bid = (int64_t)hv.y; w = hv.x; }
         }
-        /* After a lost race (round >= 1) a group of DSOA_FRESH_GROUP or more
-         * requests takes a fresh block instead of searching active[t] again: when
-         * far more warps allocate at once than there are active blocks with room
-         * (an allocation burst), they would otherwise keep converging on the same
-         * few blocks.  Small groups keep searching, so steady-state
-         * fragmentation is unchanged.  An empty free bitmap always searches. */
-        const bool search = paper_r ? (tries < c.lookups || empty_free != 0u)
-                                    : (round == 0 || empty_free || !fresh_group);
-        if (paper_r) {                 /* at most r finds per round, r attempts in all */
-            for (uint32_t a = 0; search && bid < 0 && a < c.lookups && (tries < c.lookups || empty_free); ++a, ++tries)
-                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u));
-        } else {
+        /* r of Alg. 1 (Sec. 4.2): an allocation makes at most r attempts on
+         * active blocks, a reservation that lost its race counting as one, and
+         * then takes a fresh block.  After a lost race a group of
+         * DSOA_FRESH_GROUP or more requests takes a fresh block at once: when far
+         * more warps allocate together than there are active blocks with room
+         * (an allocation burst) they would otherwise converge on the same few
+         * blocks.  An empty free bitmap always searches (at most r finds per
+         * round). */
+        const bool search = per_round ? (round == 0 || empty_free || !fresh_group)
+                                      : (empty_free != 0u || (tries < c.lookups && (round == 0 || !fresh_group)));
+        if (per_round) {
             for (uint32_t a = 0; search && a < c.lookups && bid < 0; ++a)
                 bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
+        } else {
+            for (uint32_t a = 0; search && bid < 0 && a < c.lookups && (tries < c.lookups || empty_free); ++a, ++tries)
+                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u));
         }
         if (bid < 0) {
             const unsigned long long fmask = dsoa_lowest_k(c.cap[t], want);

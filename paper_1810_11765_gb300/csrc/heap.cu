@@ -1364,7 +1364,7 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags) {
     if (!h || (flags & ~(DSOA_FLAG_NO_COALESCE | DSOA_FLAG_NO_ROTATE | DSOA_FLAG_NO_HINT | DSOA_FLAG_FUSED |
                          DSOA_FLAG_PDL | DSOA_FLAG_ENUM_TICKETS | DSOA_FLAG_NO_FRESH_GROUP |
-                         DSOA_FLAG_PAPER_R)))
+                         DSOA_FLAG_PAPER_R | DSOA_FLAG_R_PER_ROUND)))
         return DSOA_ERR_INVALID_ARG;
     h->flags = flags;
     return DSOA_OK;

@@ -66,13 +66,17 @@ def frag_over_time(steps=500, every=25, variants=("dsoa",)):
 
 
 FRAG_VARIANTS = {
-    # this runtime: r bounds the failed try_find_set calls of one round; a group of
-    # 16+ requests takes a fresh block after a lost round; per-warp block hint
+    # this runtime: r counts an allocation's active-block attempts (lost
+    # reservations included); a group of 16+ requests takes a fresh block after a
+    # lost round; per-warp block hint
     "dsoa": 0,
+    # the earlier policy: r bounds the failed try_find_set calls of one round and
+    # small groups search again in every round
+    "r_per_round": D.FLAG_R_PER_ROUND,
     "no_hint": D.FLAG_NO_HINT,
     "no_fresh_group": D.FLAG_NO_FRESH_GROUP,
-    # Alg. 1's reading of r: every active-block attempt counts, lost reservations
-    # included, and after r of them the allocation takes a fresh block
+    # Alg. 1's reading of r alone: every group (large ones too) searches until r
+    # attempts failed, then takes a fresh block
     "paper_r": D.FLAG_PAPER_R,
     "paper_r_no_hint": D.FLAG_PAPER_R | D.FLAG_NO_HINT,
 }
