@@ -276,6 +276,7 @@ __device__ __forceinline__ uint32_t dsoa_nth_set(unsigned long long w, uint32_t 
 }
 /* mask of the lowest k set bits of w */
 __device__ __forceinline__ unsigned long long dsoa_lowest_k(unsigned long long w, uint32_t k) {
+    if (k == 1u) return w & (0ull - w);               /* the lowest set bit (0 if none) */
     if ((uint32_t)__popcll(w) <= k) return w;
     if (k == 0) return 0ull;
     const uint32_t p = dsoa_nth_set(w, k - 1u);
@@ -474,17 +475,20 @@ static __device__ __noinline__ int64_t dsoa_block_new_reserved(const dsoa_ctx& c
             *reinterpret_cast<ulonglong2*>(&hp->fword) =
                 make_ulonglong2(prev & ~(1ull << ((uint64_t)bid & 63u)), (unsigned long long)bid >> 6);
     }
-    dsoa_st32(&c.btype[bid], t);
-    dsoa_fence_release();
-    dsoa_st(&c.slot[bid], DSOA_ALL & ~mask);
-    /* allocated[t] and active[t]: both level-0 RMWs in flight together; each
-     * falls back to dsoa_bm_set's retry loop if its bit was already set, and
-     * propagates upwards if its container was empty */
+    /* allocated[t] is read by enumerations of later launches only, so its
+     * level-0 RMW goes out with the type store and its latency overlaps the
+     * release fence; active[t] and the slot word, which publish the block to
+     * allocations in flight, follow the fence.  Each RMW falls back to
+     * dsoa_bm_set's retry loop if its bit was already set, and propagates
+     * upwards if its container was empty. */
     const unsigned long long m = 1ull << ((uint64_t)bid & 63u);
     const bool act = (c.cap[t] & ~mask) != 0ull;
     unsigned long long* wa = dsoa_level(c, dsoa_bm_alloc(t), 0) + ((uint64_t)bid >> 6);
     unsigned long long* wv = dsoa_level(c, dsoa_bm_active(t), 0) + ((uint64_t)bid >> 6);
+    dsoa_st32(&c.btype[bid], t);
     const unsigned long long pa = atomicOr(wa, m);
+    dsoa_fence_release();
+    dsoa_st(&c.slot[bid], DSOA_ALL & ~mask);
     const unsigned long long pv = act ? atomicOr(wv, m) : m;
     if (pa & m) dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid);
     else if (pa == 0ull && c.nlevels > 1) dsoa_bm_set(c, dsoa_bm_alloc(t), (uint64_t)bid >> 6, 1);
@@ -540,15 +544,17 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
         if (round == 0 && hp) {
             const ulonglong2 hv = *reinterpret_cast<const ulonglong2*>(hp);   /* {free, block} */
             if (hv.y < c.M && hv.x) { bid = (int64_t)hv.y; w = hv.x; }
+            else if (fresh_group && !per_round) tries = c.lookups;   /* no hinted block: fresh at once */
         }
         /* r of Alg. 1 (Sec. 4.2): an allocation makes at most r attempts on
          * active blocks, a reservation that lost its race counting as one, and
-         * then takes a fresh block.  After a lost race a group of
-         * DSOA_FRESH_GROUP or more requests takes a fresh block at once: when far
-         * more warps allocate together than there are active blocks with room
-         * (an allocation burst) they would otherwise converge on the same few
-         * blocks.  An empty free bitmap always searches (at most r finds per
-         * round). */
+         * then takes a fresh block.  A group of DSOA_FRESH_GROUP or more requests
+         * takes a fresh block after a lost race, and at once when its warp slot
+         * has no hinted block: when far more warps allocate together than there
+         * are active blocks with room (an allocation burst) they would otherwise
+         * converge on the same few blocks, whose other slots the owners' hints
+         * are about to take.  An empty free bitmap always searches (at most r
+         * finds per round). */
         const bool search = per_round ? (round == 0 || empty_free || !fresh_group)
                                       : (empty_free != 0u || (tries < c.lookups && (round == 0 || !fresh_group)));
         if (per_round) {

@@ -14,7 +14,9 @@ l2_atomic_requests_per_unit); `atom_inst` records
 smsp__sass_inst_executed_op_global_atom.sum per unit (key
 atomic_instructions_per_unit: warp-level atomic instructions, which for the
 allocator's single-lane bitmap atomics equal the atomic operations; --scale 32
-turns a full warp's instruction into its 32 operations).  The mean over
+turns a full warp's instruction into its 32 operations); `inst` records
+smsp__inst_executed.sum per unit (key warp_instructions_per_unit), the issue-slot
+work of an issue-bound kernel.  The mean over
 launches is stored under KEY together with the library's build fingerprint;
 bench.py ignores the record once the fingerprint no longer matches the sources.
 """
@@ -37,9 +39,10 @@ COUNTERS = {
     "dram": ("dram_bytes_per_unit", ("dram__bytes_read.sum", "dram__bytes_write.sum")),
     "l2_atomic": ("l2_atomic_requests_per_unit", ("lts__t_requests_op_atom.sum", "lts__t_requests_op_red.sum")),
     "atom_inst": ("atomic_instructions_per_unit", ("smsp__sass_inst_executed_op_global_atom.sum",)),
+    "inst": ("warp_instructions_per_unit", ("smsp__inst_executed.sum",)),
 }
 SCALE = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "request": 1.0, "": 1.0,
-         "Krequest": 1e3, "Mrequest": 1e6}
+         "Krequest": 1e3, "Mrequest": 1e6, "inst": 1.0, "Kinst": 1e3, "Minst": 1e6, "Ginst": 1e9}
 
 
 def read_rows(report: str):
