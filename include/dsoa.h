@@ -322,9 +322,12 @@ int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
  * bit.  Takes effect for launches issued after the call. */
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags);
 
-/* r of Sec. 4.2 / Fig. 11: attempts to find an active block (try_find_set on
- * the active bitmap) before an allocation initialises a new block; 1..64,
- * default 5.  Takes effect for launches issued after the call. */
+/* r of Sec. 4.2 / Fig. 11: an allocation's attempts on active blocks
+ * (try_find_set on the active bitmap; a reservation that lost its race counts
+ * as one) before it initialises a new block; 1..64, default 32 (the paper's
+ * default is 5; with lost reservations counted, 5 takes fresh blocks so often
+ * that a 64 MiB heap holds a Wa-Tor torus of 1344^2 instead of 1600^2 at r = 32,
+ * at the same speed).  Takes effect for launches issued after the call. */
 int dsoa_set_lookups(dsoa_heap* h, int r);
 
 /* Blocks of `type` (popcount of its allocated-block bitmap) and its live
