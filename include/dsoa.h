@@ -291,7 +291,10 @@ int dsoa_graph_destroy(dsoa_graph* g);
  * ones), the enumeration (1 or 2 = tile-count kernel + compaction kernel with
  * that many level-1 tiles per CTA, 3 = single-pass decoupled look-back kernel,
  * the default, 4 = as 3, but methods that create no objects of their own type
- * enumerate inside their own kernel, tile by tile), and the waves of the
+ * enumerate inside their own kernel, tile by tile, 5 = a thread-block cluster
+ * of 8 CTAs per type scans the bitmap in shared memory and exchanges its CTAs'
+ * totals through distributed shared memory, for heaps of at most 65,536
+ * level-0 words (4,194,304 blocks; larger heaps use 3)), and the waves of the
  * method do-all grid (1..DSOA_MAX_WAVES, default
  * 4): its grid is `waves` times the resident grid, so that SMs that finish their
  * share early take over the rest (streaming do-alls keep one resident wave).

@@ -2,7 +2,7 @@
 
 Searches do-all threads per CTA, slots per thread (one block per 64 threads, or one
 block per warp), the enumeration (two kernels or the single-pass look-back kernel)
-and the waves of the method do-all grid; the streamed enumeration and the fused
+(or a thread-block cluster per type) and the waves of the method do-all grid; the streamed enumeration and the fused
 cooperative do-all are tried in a few shapes.
 Each candidate runs a fresh world from the same seed, captures one step as a CUDA
 graph and times replays with CUDA events (L2 flushed between replays, as in the
@@ -24,7 +24,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_DIR = os.path.join(HERE, "_tune")
 
 CANDIDATES = [dict(tpb=tpb, ctas_per_sm=8, slots_per_thread=spt, scan_tiles=scan, waves=waves, fused=0)
-              for tpb, spt, scan, waves in itertools.product((128, 256, 512), (1, 2), (1, 3), (1, 2, 4, 8))]
+              for tpb, spt, scan, waves in itertools.product((128, 256, 512), (1, 2), (1, 3, 5), (1, 2, 4, 8))]
 CANDIDATES += [dict(tpb=tpb, ctas_per_sm=8, slots_per_thread=1, scan_tiles=4, waves=4, fused=0) for tpb in (128, 256)]
 CANDIDATES.append(dict(tpb=256, ctas_per_sm=8, slots_per_thread=1, scan_tiles=3, waves=1, fused=1))
 
@@ -70,7 +70,7 @@ def time_wator_step(seed: int, launch: dict, side: int = 1024, warmup: int = 5, 
 
 
 def best_wator_launch(seed: int, use_cache: bool = True, verbose: bool = False) -> dict:
-    path = _cache_path("wator1024-v5")
+    path = _cache_path("wator1024-v6")
     if use_cache and os.path.exists(path):
         with open(path) as f:
             return json.load(f)["best"]

@@ -58,6 +58,7 @@ struct dsoa_heap {
     int vec_slots_per_thread = 4;    // vectorised kernels: slots per thread (1, 2 or 4)
     int scan_tiles_per_cta = 0;      // 0 = single-pass look-back; 1, 2 = tile-count + compaction kernels
     bool stream_enum = false;        // enumerate inside methods that create no objects of their own type
+    bool cluster_enum = false;       // enumerate with a thread-block cluster per type (heaps up to 4 M blocks)
     uint32_t* stream_ctl = nullptr;  // ticket, finished CTAs, R length of the streamed do-all
     unsigned long long* count_acc = nullptr;  // [DSOA_MAX_TYPES] partial counts of k_count_many (zero between launches)
     uint32_t* count_ticket = nullptr;         // finished CTAs of k_count_many (zero between launches)

@@ -11,7 +11,11 @@
 #include <new>
 #include <utility>
 
+#include <cooperative_groups.h>
+
 #include "dsoa_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -536,6 +540,114 @@ __global__ void __launch_bounds__(64) k_enum_lookback_multi(dsoa_ctx c, uint64_t
     }
 }
 
+// Enumeration by a thread-block cluster per type (scan_tiles = 5; not in the
+// paper): kEnumCl CTAs of 1024 threads split the level-0 words of the type's
+// allocated-block bitmap into contiguous ranges, in order.  Each CTA scans the
+// popcounts of its range in shared memory; after a cluster barrier every CTA
+// reads the totals of the CTAs before it from their shared memory
+// (distributed shared memory), which gives its first position in R; a second
+// barrier keeps every CTA's shared memory alive until all have read it.  The
+// CTA then stages its block ids in shared memory and writes them with the
+// snapshot words, four per thread in flight.  The cluster is co-scheduled by
+// the hardware, so no CTA waits on one that has not started, and nothing
+// spins.  For heaps of at most kEnumCl * 1024 * kEnumClK level-0 words.
+constexpr uint32_t kEnumCl = 8, kEnumClThreads = 1024, kEnumClK = 8;
+constexpr uint64_t kEnumClWords = (uint64_t)kEnumCl * kEnumClThreads * kEnumClK;   // 65,536 words
+constexpr uint32_t kEnumClChunk = 4096;
+
+__global__ void __launch_bounds__(1024, 1) k_enum_cluster(dsoa_ctx c, EnumBatch eb) {
+    __shared__ uint32_t list[kEnumClChunk];
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t s_tot;
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t rank = cl.block_rank();
+    const uint32_t q = blockIdx.x / kEnumCl;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t b = eb.b[q];
+    uint32_t* __restrict__ R = eb.R[q];
+    unsigned long long* __restrict__ Rocc = eb.Rocc[q];
+    dsoa_pdl_wait();
+    dsoa_pdl_release();
+    const unsigned long long* L0 = dsoa_level(c, b, 0);
+    const uint64_t w0 = c.lvl_words[0];
+    const uint64_t per_cta = (w0 + kEnumCl - 1) / kEnumCl;
+    const uint64_t lo = (uint64_t)rank * per_cta;
+    const uint64_t hi = lo + per_cta < w0 ? lo + per_cta : w0;
+    const uint64_t per_thr = (per_cta + kEnumClThreads - 1) / kEnumClThreads;   /* <= kEnumClK */
+    const uint64_t first = lo + (uint64_t)tid * per_thr;
+    unsigned long long w[kEnumClK];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kEnumClK; ++k) {
+        const uint64_t i = first + k;
+        w[k] = (k < per_thr && i < hi) ? L0[i] : 0ull;
+        cnt += (uint32_t)__popcll(w[k]);
+    }
+    uint32_t incl = cnt;                                    /* CTA-wide exclusive scan */
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += v;
+    }
+    if (lane == 31u) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t x = wsum[lane];
+        uint32_t y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= (uint32_t)o) y += v;
+        }
+        wsum[lane] = y - x;
+        if (lane == 31u) s_tot = y;                         /* this CTA's blocks */
+    }
+    cl.sync();                                              /* every CTA's total is in place */
+    __shared__ uint32_t s_base;
+    if (tid == 0) {
+        uint32_t base = 0;
+        for (uint32_t r = 0; r < rank; ++r) base += *cl.map_shared_rank(&s_tot, r);
+        s_base = base;
+        if (rank == kEnumCl - 1u) *eb.r_dev[q] = base + s_tot;
+    }
+    cl.sync();                                              /* remote reads done before any CTA leaves */
+    const uint32_t cta_base = s_base, cta_n = s_tot;
+    const uint32_t mine = wsum[warp] + incl - cnt;          /* position within this CTA's part */
+    for (uint32_t chunk0 = 0; chunk0 < cta_n; chunk0 += kEnumClChunk) {
+        if (cnt && mine < chunk0 + kEnumClChunk && mine + cnt > chunk0) {
+            uint32_t pos = mine;
+#pragma unroll
+            for (uint32_t k = 0; k < kEnumClK; ++k) {
+                const uint64_t bid0 = (first + k) * 64u;
+                for (unsigned long long x = w[k]; x; x &= x - 1ull, ++pos)
+                    if (pos >= chunk0 && pos < chunk0 + kEnumClChunk)
+                        list[pos - chunk0] = (uint32_t)(bid0 + (uint32_t)(__ffsll((long long)x) - 1));
+            }
+        }
+        __syncthreads();
+        const uint32_t n = cta_n - chunk0 < kEnumClChunk ? cta_n - chunk0 : kEnumClChunk;
+        for (uint32_t i0 = 0; i0 < n; i0 += 4u * kEnumClThreads) {
+            uint32_t id[4];
+            unsigned long long o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {                   /* four snapshot loads in flight */
+                const uint32_t i = i0 + (uint32_t)u * kEnumClThreads + tid;
+                id[u] = i < n ? list[i] : 0u;
+                o[u] = i < n ? ~c.slot[id[u]] : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t i = i0 + (uint32_t)u * kEnumClThreads + tid;
+                if (i < n) {
+                    R[cta_base + chunk0 + i] = id[u];
+                    Rocc[cta_base + chunk0 + i] = o[u];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Live objects of one type: warp per tile; for every non-empty level-0
 // container the warp reads the 64 slot words coalesced.
 // Live objects of several types in one launch, stored to out[q]: one warp per
@@ -754,6 +866,30 @@ static int enumerate_lookback(dsoa_heap* h, const int* types, int n) {
     }
     int rc;
     const bool tickets = (h->flags & DSOA_FLAG_ENUM_TICKETS) != 0u;
+    if (h->cluster_enum && h->ctx.lvl_words[0] <= kEnumClWords) {
+        // a cluster of kEnumCl CTAs per type (scan_tiles = 5)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)n * kEnumCl);
+        cfg.blockDim = dim3(kEnumClThreads);
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = kEnumCl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = (h->flags & DSOA_FLAG_PDL) ? 2u : 1u;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_enum_cluster, h->ctx, eb);
+        h->launches++;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return DSOA_ERR_CUDA;
+        }
+        for (int q = 0; q < n; ++q) h->enumerated[types[q]] = true;
+        return DSOA_OK;
+    }
     if (!fits && !tickets) {
         // several tiles per CTA, so that the whole launch is resident (else tickets)
         static int multi_per_sm = -1;
@@ -1350,9 +1486,10 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
         h->vec_slots_per_thread = slots_per_thread;
     }
     if (scan_tiles) {
-        if (scan_tiles < 1 || scan_tiles > 4) return DSOA_ERR_INVALID_ARG;
-        h->scan_tiles_per_cta = scan_tiles >= 3 ? 0 : scan_tiles;   // 3, 4 = single-pass look-back
+        if (scan_tiles < 1 || scan_tiles > 5) return DSOA_ERR_INVALID_ARG;
+        h->scan_tiles_per_cta = scan_tiles >= 3 ? 0 : scan_tiles;   // 3, 4, 5 = single pass
         h->stream_enum = scan_tiles == 4;                           // 4 = + streamed do-alls
+        h->cluster_enum = scan_tiles == 5;                          // 5 = a cluster per type
     }
     if (waves) {
         if (waves < 1 || waves > DSOA_MAX_WAVES) return DSOA_ERR_INVALID_ARG;

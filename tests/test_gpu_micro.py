@@ -119,7 +119,8 @@ def test_ablations_keep_semantics(flags):
 
 
 @pytest.mark.parametrize("tpb,ctas,scan,waves", [(64, 1, 1, 1), (128, 4, 2, 2), (512, 2, 1, 4), (512, 8, 2, 16),
-                                                 (256, 8, 3, 4), (64, 2, 3, 8), (128, 8, 4, 1), (512, 1, 4, 2)])
+                                                 (256, 8, 3, 4), (64, 2, 3, 8), (128, 8, 4, 1), (512, 1, 4, 2),
+                                                 (128, 8, 5, 4), (256, 4, 5, 1)])
 def test_launch_shapes_keep_semantics(tpb, ctas, scan, waves):
     n, rounds = 30000, 3
     ref, x_ref, live_ref = oracle.micro_run(SEED, n, rounds, per_object=True)
@@ -164,7 +165,7 @@ def test_launch_shape_bounds():
     from paper_1810_11765_gb300 import dsoa as D
     m = make(heap_bytes=4 << 20, n=10)
     for bad in (dict(tpb=1024), dict(tpb=96), dict(ctas_per_sm=64), dict(slots_per_thread=3), dict(waves=17),
-                dict(waves=-1), dict(scan_tiles=5)):
+                dict(waves=-1), dict(scan_tiles=6)):
         with pytest.raises(D.DsoaError):
             m.heap.set_launch(**bad)
 
@@ -314,7 +315,7 @@ def test_atomic_peak_probe_final_words():
     assert m.heap.get_error() == 0
 
 
-@pytest.mark.parametrize("scan,flags", [(3, 0), (3, 32), (1, 0)])
+@pytest.mark.parametrize("scan,flags", [(3, 0), (3, 32), (1, 0), (5, 0)])
 def test_heap_beyond_one_wave_of_enumeration_ctas(scan, flags):
     """A 5 GiB heap has more level-1 tiles (~1200) than single-tile look-back CTAs
     fit on the GPU at once (~900): the enumeration runs the multi-tile kernel (CTA

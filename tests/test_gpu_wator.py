@@ -144,7 +144,7 @@ def test_ablations_finish_with_the_oracle_result(flags):
     heap.close()
 
 
-@pytest.mark.parametrize("scan", [1, 2, 3, 4])
+@pytest.mark.parametrize("scan", [1, 2, 3, 4, 5])
 def test_enumeration_modes_agree(scan):
     """Tile-count + compaction kernels (1 or 2 tiles per CTA), the single-pass
     look-back kernel and the streamed enumeration inside the choose methods give
@@ -177,7 +177,7 @@ def _enumeration(heap, t, ptrs):
     return lst, snap
 
 
-@pytest.mark.parametrize("scan_tiles", [1, 3])
+@pytest.mark.parametrize("scan_tiles", [1, 3, 5])
 def test_enumerate_many_equals_separate_enumerations(scan_tiles):
     """One launch enumerating Fish and Shark gives, per type, the block list and
     occupancy snapshot of a separate dsoa_enumerate (same per-type buffers)."""
