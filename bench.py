@@ -891,8 +891,16 @@ def dsoa_arm(args):
         alg = statistics.mean(d["bytes"])
         ach = alg / (avg_ms / 1e3) / 1e9
         units = statistics.mean(d["units"])
+        # traffic inside a step (ncu without cache control on a run that flushes L2
+        # between steps, as here); the cold-cache figure (caches flushed before the
+        # kernel alone) beside it
+        t_step = ncu_traffic(dom, units, "dram_bytes_in_step_per_unit")
+        t_cold = ncu_traffic(dom, units)
         out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                           "unit": "GB/s", "frac": ach / hbm_peak, "traffic": ncu_traffic(dom, units),
+                           "unit": "GB/s", "frac": ach / hbm_peak,
+                           "traffic": t_step if t_step is not None else t_cold,
+                           "traffic_kind": "in step" if t_step is not None else "cold caches",
+                           "traffic_cold": t_cold,
                            "peak_kind": peak_kind, "avg_launch_ms": avg_ms, "alg_bytes_per_launch": alg,
                            "units_per_launch": units}
         out["step_kernels_ms"] = {k: statistics.mean(v["ms"]) for k, v in prof.items()}
@@ -932,6 +940,9 @@ def dsoa_arm(args):
             peak = out["l2_atomic_peak"]["atomics_per_s"] * probe_req
             ph["l2_atomic"] = {"requests_per_agent": req / ph["agents"], "requests_per_s": rate,
                                "peak_requests_per_s": peak, "frac": rate / peak}
+        for k, ph in out.get("step_phases", {}).items():
+            ph["dram_bytes_per_agent"] = {"in_step": ncu_traffic(k, 1.0, "dram_bytes_in_step_per_unit"),
+                                          "cold": ncu_traffic(k, 1.0)}
         sweep = {}
         for lg in (18, 20, 22, 24):      # 2^18 threads' worth x {1, 4, 16, 64} objects
             st = alloc_free_storm(lg, flush)

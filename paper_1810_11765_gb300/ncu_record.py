@@ -3,12 +3,16 @@ profiles/ncu_traffic.json, which bench.py reads for the `traffic` field of its
 rooflines.
 
   python -m paper_1810_11765_gb300.ncu_record REPORT.ncu-rep --match REGEX \\
-      --name KEY --units U1,U2,... [--counter dram|l2_atomic|atom_inst] [--scale S]
+      --name KEY --units U1,U2,... [--counter dram|dram_step|l2_atomic|atom_inst|inst] [--scale S]
 
 REPORT is read with `ncu -i REPORT --page raw --csv`; the launches whose kernel
 name matches REGEX are taken in order and launch i is divided by Ui (objects
 that launch processed).  `dram` records dram__bytes_read.sum +
-dram__bytes_write.sum per unit (key dram_bytes_per_unit); `l2_atomic` records
+dram__bytes_write.sum per unit (key dram_bytes_per_unit), from a capture that
+flushes the caches before each launch; `dram_step` records the same counters
+from a capture without cache control of a run that flushes L2 only between steps
+(key dram_bytes_in_step_per_unit: the traffic a kernel causes inside a timed
+step, where earlier kernels of the step have already brought shared lines in); `l2_atomic` records
 lts__t_requests_op_atom.sum + lts__t_requests_op_red.sum per unit (key
 l2_atomic_requests_per_unit); `atom_inst` records
 smsp__sass_inst_executed_op_global_atom.sum per unit (key
@@ -37,6 +41,7 @@ OUT = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 
 COUNTERS = {
     "dram": ("dram_bytes_per_unit", ("dram__bytes_read.sum", "dram__bytes_write.sum")),
+    "dram_step": ("dram_bytes_in_step_per_unit", ("dram__bytes_read.sum", "dram__bytes_write.sum")),
     "l2_atomic": ("l2_atomic_requests_per_unit", ("lts__t_requests_op_atom.sum", "lts__t_requests_op_red.sum")),
     "atom_inst": ("atomic_instructions_per_unit", ("smsp__sass_inst_executed_op_global_atom.sum",)),
     "inst": ("warp_instructions_per_unit", ("smsp__inst_executed.sum",)),

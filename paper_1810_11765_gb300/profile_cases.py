@@ -1,7 +1,7 @@
 """Small, bounded workloads for kernel profiling (ncu) and quick timing.
 
   python -m paper_1810_11765_gb300.profile_cases doall --log2n 24 [--holes] [--iters 3]
-  python -m paper_1810_11765_gb300.profile_cases wator --side 1024 --steps 3 [--defer]
+  python -m paper_1810_11765_gb300.profile_cases wator --side 1024 --steps 3 [--defer] [--flush]
   python -m paper_1810_11765_gb300.profile_cases alloc --log2n 22
   python -m paper_1810_11765_gb300.profile_cases atomic --iters 64
   python -m paper_1810_11765_gb300.profile_cases nbody --n 16384 [--walk] [--iters 3]
@@ -52,19 +52,27 @@ def case_doall(log2n: int, holes: bool, iters: int, method: str = "vec"):
     m.heap.close()
 
 
-def case_wator(side: int, steps: int, defer: bool = False):
+def case_wator(side: int, steps: int, defer: bool = False, flush: bool = False):
+    """`flush`: a 256 MiB write before every step, as between the benchmark's timed
+    steps, so that a capture without cache control sees each kernel's DRAM traffic
+    as it is inside a benchmarked step (the first kernel to touch a line reads it)."""
     heap = D.Heap(512 << 20)
     w = WatorWorld(heap)
     w.defer_births = defer
     heap.freeze()
     w.add(side, side, 0x5EED0003)
+    buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush else None
     for _ in range(steps):
+        if buf is not None:
+            buf.zero_()
         a, b = _ev(), _ev()
         a.record()
         w.step()
         b.record()
         b.synchronize()
-        print(f"wator {side}^2 step: {a.elapsed_time(b):.4f} ms  populations {w.counts()}")
+        fs, ss = heap.type_stats(w.fish_type), heap.type_stats(w.shark_type)
+        print(f"wator {side}^2 step: {a.elapsed_time(b):.4f} ms  populations {w.counts()}  "
+              f"blocks {fs['blocks']} / {ss['blocks']}")
     print("err", heap.get_error())
     heap.close()
 
@@ -142,12 +150,13 @@ def main():
     p.add_argument("--side", type=int, default=1024)
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--defer", action="store_true", help="wator: births allocated by the births kernel")
+    p.add_argument("--flush", action="store_true", help="wator: write 256 MiB before every step (L2 flush)")
     a = p.parse_args()
     build.build()
     if a.case == "doall":
         case_doall(a.log2n, a.holes, a.iters, a.method)
     elif a.case == "wator":
-        case_wator(a.side, a.steps, a.defer)
+        case_wator(a.side, a.steps, a.defer, a.flush)
     elif a.case == "atomic":
         case_atomic(a.iters)
     elif a.case == "nbody":
