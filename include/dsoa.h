@@ -321,8 +321,14 @@ int dsoa_set_launch(dsoa_heap* h, int doall_tpb, int doall_ctas_per_sm,
  * active blocks after a lost round instead of taking a fresh block, and
  * DSOA_FLAG_PAPER_R (256) counts every active-block attempt of an allocation
  * toward r, lost reservations included, and takes a fresh block after r of
- * them (Alg. 1's reading of r).  Returns DSOA_ERR_INVALID_ARG for an unknown
- * bit.  Takes effect for launches issued after the call. */
+ * them (Alg. 1's reading of r), and DSOA_FLAG_R_PER_ROUND (512) restores an
+ * earlier policy in which r bounds the failed finds of one round and small
+ * groups search again in every round.  DSOA_FLAG_DRAIN (1024) lets blocks that
+ * fell to an eighth of their capacity drain: a search passes over them (at most
+ * 4 times per allocation) and a warp drops its hint to one, so that they empty
+ * instead of being refilled (not in the paper; it lowers fragmentation).
+ * Returns DSOA_ERR_INVALID_ARG for an unknown bit.  Takes effect for launches
+ * issued after the call. */
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags);
 
 /* r of Sec. 4.2 / Fig. 11: an allocation's attempts on active blocks

@@ -99,6 +99,8 @@ struct dsoa_ctx {
     int* err;                            /* sticky DSOA_DEV_* bits                 */
     dsoa_hint* hint;                     /* [hint_mask + 1][ntypes] last block with
                                             free slots per warp slot (advisory)       */
+    uint8_t* drain;                      /* [M] 1 = the block fell to few objects and
+                                            is left to drain (advisory)               */
     uint32_t* grid_scratch;              /* [DSOA_GRID_SCRATCH] per-CTA aggregates and
                                             grid-barrier words of the fused do-all    */
     uint64_t M;                          /* number of blocks                       */
@@ -155,6 +157,18 @@ struct dsoa_ctx {
                                              the failed finds of one round, and a
                                              group below DSOA_FRESH_GROUP searches
                                              again in every round                   */
+#define DSOA_FLAG_DRAIN 1024u             /* let blocks that fell to few objects
+                                             drain: searches pass over them and a
+                                             warp drops its hint to one
+                                             (dsoa_drain_mark)                      */
+#ifndef DSOA_DRAIN_SKIPS
+#define DSOA_DRAIN_SKIPS 4u               /* draining blocks one allocation passes
+                                             over at most                           */
+#endif
+#ifndef DSOA_DRAIN_SHIFT
+#define DSOA_DRAIN_SHIFT 3u               /* a block drains at or below
+                                             capacity >> DSOA_DRAIN_SHIFT objects   */
+#endif
 #define DSOA_GRID_SCRATCH (DSOA_FUSED_MAX_CTAS + 64u)
 #define DSOA_CTX_NO_PROLOGUE (1u << 30)   /* set by the library in the context of the
                                              do-all launches that follow the first one
@@ -205,6 +219,14 @@ __device__ __forceinline__ void dsoa_st(unsigned long long* p, unsigned long lon
 }
 __device__ __forceinline__ void dsoa_st32(uint32_t* p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t dsoa_ld8(const uint8_t* p) {
+    unsigned short v;
+    asm volatile("ld.relaxed.gpu.global.u8 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void dsoa_st8(uint8_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u8 [%0], %1;" ::"l"(p), "h"((unsigned short)v) : "memory");
 }
 /* atomicAnd with acquire semantics at device scope: loads after it observe
  * what was written before the release (fence + store) whose value it read. */
@@ -345,13 +367,16 @@ __device__ inline bool dsoa_bm_set(const dsoa_ctx& c, uint32_t b, uint64_t pos, 
 /* try_find_set (Alg. 4) with bitmap rotation (Sec. 4.2): top-down; at every
  * level the container is rotated by a hash-derived amount before ffs, so
  * different warps start at different bits.  -1 = FAIL (possibly spurious
- * while levels are transiently inconsistent). */
-__device__ inline int64_t dsoa_bm_find(const dsoa_ctx& c, uint32_t b, uint32_t h) {
+ * while levels are transiently inconsistent).  w0, if given, receives the
+ * level-0 word the search ended in. */
+__device__ inline int64_t dsoa_bm_find(const dsoa_ctx& c, uint32_t b, uint32_t h,
+                                       unsigned long long* w0 = nullptr) {
     uint64_t idx = 0;
     const bool rot = !(c.flags & DSOA_FLAG_NO_ROTATE);
     for (int l = (int)c.nlevels - 1; l >= 0; --l) {
         const unsigned long long w = dsoa_ld(dsoa_level(c, b, (uint32_t)l) + idx);
         if (!w) return -1;
+        if (l == 0 && w0) *w0 = w;
         const uint32_t r = rot ? ((h >> ((uint32_t)l * 5u)) ^ (h >> 27)) & 63u : 0u;
         const uint32_t bit = ((uint32_t)__ffsll((long long)dsoa_rotr(w, r)) - 1u + r) & 63u;
         idx = idx * 64u + bit;
@@ -425,6 +450,25 @@ static __device__ __noinline__ void dsoa_block_deactivate(const dsoa_ctx& c, uin
     dsoa_bm_clear(c, dsoa_bm_active(t), bid, true);         /* now full: inactive */
 }
 
+/* Draining (DSOA_FLAG_DRAIN; a policy of this runtime, not of the paper).
+ * Objects never move, so a block stays in use while it holds one object, and
+ * when allocations land on blocks at random, as the rotated search makes them,
+ * a population that shrinks leaves many blocks holding a few objects each.  A
+ * free that leaves a block's live objects at or below an eighth of its
+ * capacity (DSOA_DRAIN_SHIFT; having been above) marks the block draining: a search that finds
+ * it passes over it, at most DSOA_DRAIN_SKIPS times per allocation, and a warp
+ * that reserved in it drops its hint to it, so that it empties and returns to
+ * the free bitmap instead of being refilled.  The mark is cleared when the
+ * block is taken fresh or filled.  Advisory: the bitmaps and their invariants
+ * are the same with the flag and without it. */
+__device__ __forceinline__ void dsoa_drain_mark(const dsoa_ctx& c, uint32_t t, uint64_t bid,
+                                                unsigned long long before, unsigned long long bits) {
+    const uint32_t d = (uint32_t)__popcll(c.cap[t]) >> DSOA_DRAIN_SHIFT;
+    const uint32_t live_before = (uint32_t)__popcll(~before & c.cap[t]);
+    const uint32_t live_after = (uint32_t)__popcll(~(before | bits) & c.cap[t]);
+    if (live_after <= d && live_before > d && live_after != 0u) dsoa_st8(&c.drain[bid], 1u);
+}
+
 /* Block::deallocate for a set of slots (Alg. 8, multi-slot form used by
  * request coalescing and by rollback).  `t` is the block's type. */
 __device__ __forceinline__ void dsoa_block_release(const dsoa_ctx& c, uint32_t t, uint64_t bid,
@@ -435,6 +479,7 @@ __device__ __forceinline__ void dsoa_block_release(const dsoa_ctx& c, uint32_t t
         bits &= ~before;
         if (!bits) return;
     }
+    if (c.flags & DSOA_FLAG_DRAIN) dsoa_drain_mark(c, t, bid, before, bits);
     /* FIRST: real slots (below the capacity) freed in a block that had none free;
      * a rollback that only returns slots beyond the capacity changes nothing */
     if ((before & c.cap[t]) == 0ull && (bits & c.cap[t]) != 0ull) dsoa_block_first_free(c, t, bid);
@@ -490,6 +535,7 @@ static __device__ __noinline__ int64_t dsoa_block_new_reserved(const dsoa_ctx& c
     unsigned long long* wa = dsoa_level(c, dsoa_bm_alloc(t), 0) + ((uint64_t)bid >> 6);
     unsigned long long* wv = dsoa_level(c, dsoa_bm_active(t), 0) + ((uint64_t)bid >> 6);
     dsoa_st32(&c.btype[bid], t);
+    if (c.flags & DSOA_FLAG_DRAIN) dsoa_st8(&c.drain[bid], 0u);
     const unsigned long long pa = atomicOr(wa, m);
     dsoa_fence_release();
     dsoa_st(&c.slot[bid], DSOA_ALL & ~mask);
@@ -538,6 +584,8 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
     const bool fresh_group = want >= DSOA_FRESH_GROUP &&
                              !(c.flags & (DSOA_FLAG_NO_FRESH_GROUP | DSOA_FLAG_PAPER_R));
     uint32_t tries = 0;        /* active-block attempts so far, lost reservations included */
+    const bool drain = (c.flags & DSOA_FLAG_DRAIN) != 0u;
+    uint32_t skips = 0;        /* draining blocks passed over so far */
     for (uint32_t round = 0; round < max_rounds; ++round) {
         if (!rot && round) {           /* NoShift: thin out the races on the first bits */
             const uint32_t span = 32u << (round < 7u ? round : 7u);
@@ -545,6 +593,7 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
         }
         int64_t bid = -1;
         unsigned long long w = 0ull;   /* free slots of bid, if already known */
+        unsigned long long w0 = 0ull;  /* active blocks of the level-0 word the search ended in */
         if (round == 0 && hp) {
             const ulonglong2 hv = *reinterpret_cast<const ulonglong2*>(hp);   /* {free, block} */
             if (hv.y < c.M && hv.x) { bid = (int64_t)hv.y; w = hv.x; }
@@ -563,10 +612,10 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
                                       : (empty_free != 0u || (tries < c.lookups && (round == 0 || !fresh_group)));
         if (per_round) {
             for (uint32_t a = 0; search && a < c.lookups && bid < 0; ++a)
-                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u));
+                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + a) * 0x9E3779B9u), &w0);
         } else {
             for (uint32_t a = 0; search && bid < 0 && a < c.lookups && (tries < c.lookups || empty_free); ++a, ++tries)
-                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u));
+                bid = dsoa_bm_find(c, act, dsoa_hash(h ^ (round * DSOA_LOOKUP_ATTEMPTS + tries) * 0x9E3779B9u), &w0);
         }
         if (bid < 0) {
             const unsigned long long fmask = dsoa_lowest_k(c.cap[t], want);
@@ -586,8 +635,25 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
             *bid_out = (uint64_t)bid;
             return fmask;
         }
-        if (!w) {
-            w = dsoa_ld(&c.slot[bid]) & c.cap[t];
+        if (!w) {                      /* a block the search found: its slot word */
+            unsigned long long sw = dsoa_ld(&c.slot[bid]);
+            uint32_t dr = drain ? dsoa_ld8(&c.drain[bid]) : 0u;
+            /* a draining block: the other active blocks of the same level-0 word
+             * (one load each, no new search); when none is left, a new search */
+            bool again = false;
+            while (dr && skips < DSOA_DRAIN_SKIPS) {
+                ++skips;
+                w0 &= ~(1ull << ((uint64_t)bid & 63u));
+                const uint32_t r0 = dsoa_hash(h + skips * 0x9E3779B9u) & 63u;
+                const uint64_t nb = ((uint64_t)bid & ~63ull) |
+                                    (((uint32_t)__ffsll((long long)dsoa_rotr(w0, r0)) - 1u + r0) & 63u);
+                if (!w0 || nb >= c.M) { again = true; break; }
+                bid = (int64_t)nb;
+                sw = dsoa_ld(&c.slot[bid]);
+                dr = dsoa_ld8(&c.drain[bid]);
+            }
+            if (again) continue;
+            w = sw & c.cap[t];
             if (!w) continue;
         }
         const uint32_t r = rot ? (dsoa_hash(h + round) & 63u) : 0u;
@@ -602,19 +668,23 @@ __device__ __forceinline__ unsigned long long dsoa_leader_reserve(const dsoa_ctx
             continue;
         }
         const uint32_t bt = dsoa_ld32(&c.btype[bid]);
+        const uint32_t drn = drain ? dsoa_ld8(&c.drain[bid]) : 0u;
         /* FULL: this reservation took the last free real slots of the block's type
          * (a reservation of another type may take only slots beyond that type's
          * capacity, which leaves the block's state unchanged) */
         const unsigned long long capb = c.cap[bt < c.ntypes ? bt : t];
         const unsigned long long left = before & ~mask & capb;
         const bool full = left == 0ull && (before & capb) != 0ull;
-        if (full) dsoa_block_deactivate(c, bt, (uint64_t)bid);
+        if (full) {
+            dsoa_block_deactivate(c, bt, (uint64_t)bid);
+            if (drn) dsoa_st8(&c.drain[bid], 0u);
+        }
         if (bt != t) {                 /* block replaced by another type: roll back */
             if (hp) dsoa_hint_put(hp, 0ull, DSOA_NO_HINT_BLOCK);
             dsoa_rollback(c, bt, (uint64_t)bid, got);
             continue;
         }
-        if (hp) dsoa_hint_put(hp, left, full ? DSOA_NO_HINT_BLOCK : (uint64_t)bid);
+        if (hp) dsoa_hint_put(hp, left, (full || drn) ? DSOA_NO_HINT_BLOCK : (uint64_t)bid);
         *bid_out = (uint64_t)bid;
         return got;
     }

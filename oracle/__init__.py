@@ -161,7 +161,8 @@ def wator_run(w: int, h: int, steps: int, seed: int = 0, init=None, t0: int = 0,
     return grid.reshape(h, w), rows
 
 
-FRAG_POLICIES = {"first_fit": 0, "best_fit": 1, "random_fit": 2}
+FRAG_POLICIES = {"first_fit": 0, "best_fit": 1, "random_fit": 2, "hinted_random_fit": 3,
+                 "hinted_random_fit_drain": 4}
 
 
 def wator_frag(w: int, h: int, steps: int, seed: int, policy: str = "first_fit", every: int = 25):

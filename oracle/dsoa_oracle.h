@@ -95,7 +95,9 @@ int orc_wator_run(uint32_t w, uint32_t h, const uint8_t* init, uint64_t seed,
 
 /* Fragmentation of an idealised sequential allocator on the Wa-Tor run drawn
  * from `seed` (frag_model.c; analysis of Sec. 6.4, not a model of the GPU
- * allocator): policy 0 first fit, 1 best fit, 2 random fit over 64-slot blocks.
+ * allocator): policy 0 first fit, 1 best fit, 2 random fit, 3 random fit with
+ * 8192 per-slot block hints, 4 the same with draining (a block fallen to 8
+ * objects or fewer is left out until filled or emptied) over 64-slot blocks.
  * Every `every` steps one record: F = 1 - objects / (64 x blocks in use), fish,
  * sharks and blocks (arrays of steps / every entries; any may be NULL).
  * Returns 0 or -1. */

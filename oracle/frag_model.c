@@ -21,6 +21,15 @@
  *   0 first fit   the lowest-numbered block with a free slot
  *   1 best fit    a fullest block with a free slot (lowest-numbered among them)
  *   2 random fit  a block with a free slot chosen uniformly (xorshift64, fixed seed)
+ *   3 hinted random fit   FM_HINTS hint slots (standing for the warps of a GPU
+ *                 allocator); each allocation draws a slot uniformly and takes
+ *                 the slot's block if that still has a free slot, else a block
+ *                 with a free slot chosen uniformly, else a fresh block; the
+ *                 slot then names the block taken
+ *   4 hinted random fit with draining   as 3, but a block whose objects fall
+ *                 (by a death) to FM_DRAIN or fewer is draining until it is
+ *                 filled or emptied: the uniform choice leaves it out and a
+ *                 hint that names it is not taken
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -64,6 +73,9 @@ static int fm_empty(const fm_bits* m) {
     return 1;
 }
 
+#define FM_HINTS 8192u
+#define FM_DRAIN 8u
+
 typedef struct {
     int policy;
     uint32_t cap, nblocks, used, live;
@@ -72,9 +84,16 @@ typedef struct {
     fm_bits released;       /* blocks that were used and are empty again */
     fm_bits* level;         /* policy 0: level[1] = partly used; policy 1: level[n] = n objects */
     uint64_t level_mask;    /* policy 1: counts with a non-empty set */
-    uint32_t *pool, *pos, npool;   /* policy 2: partly used blocks, swap-remove */
+    uint32_t *pool, *pos, npool;   /* policies 2-4: partly used blocks (4: not draining), swap-remove */
+    uint32_t* hint;         /* policies 3-4: block + 1 per hint slot, 0 = none */
+    uint8_t* drain;         /* policy 4: 1 = draining */
     uint64_t rng;
 } fm_pool;
+
+static uint64_t fm_next(fm_pool* p) {
+    p->rng ^= p->rng << 13; p->rng ^= p->rng >> 7; p->rng ^= p->rng << 17;
+    return p->rng;
+}
 
 static int fm_pool_init(fm_pool* p, int policy, uint32_t cap) {
     memset(p, 0, sizeof(*p));
@@ -86,7 +105,9 @@ static int fm_pool_init(fm_pool* p, int policy, uint32_t cap) {
     p->pool = calloc(cap, 4);
     p->pos = calloc(cap, 4);
     p->level = calloc(64, sizeof(fm_bits));
-    if (!p->cnt || !p->freebits || !p->pool || !p->pos || !p->level) return -1;
+    p->hint = calloc(FM_HINTS, 4);
+    p->drain = calloc(cap, 1);
+    if (!p->cnt || !p->freebits || !p->pool || !p->pos || !p->level || !p->hint || !p->drain) return -1;
     if (fm_bits_init(&p->released, cap)) return -1;
     for (int q = 0; q < 64; ++q)
         if ((policy == 0 && q == 1) || (policy == 1 && q > 0))
@@ -94,7 +115,7 @@ static int fm_pool_init(fm_pool* p, int policy, uint32_t cap) {
     return 0;
 }
 static void fm_pool_free(fm_pool* p) {
-    free(p->cnt); free(p->freebits); free(p->pool); free(p->pos);
+    free(p->cnt); free(p->freebits); free(p->pool); free(p->pos); free(p->hint); free(p->drain);
     fm_bits_free(&p->released);
     if (p->level) {
         for (int q = 0; q < 64; ++q)
@@ -105,14 +126,19 @@ static void fm_pool_free(fm_pool* p) {
 /* the policy's set of partly used blocks (1..63 objects) */
 static void fm_enter(fm_pool* p, uint32_t b, uint32_t n) {
     if (n == 0 || n >= 64) return;
-    if (p->policy == 2) { p->pos[b] = p->npool; p->pool[p->npool++] = b; return; }
+    if (p->policy >= 2) {
+        if (p->policy == 4 && p->drain[b]) return;
+        p->pos[b] = p->npool; p->pool[p->npool++] = b;
+        return;
+    }
     uint32_t q = p->policy == 0 ? 1 : n;
     fm_set(&p->level[q], b);
     p->level_mask |= 1ull << q;
 }
 static void fm_leave(fm_pool* p, uint32_t b, uint32_t n) {
     if (n == 0 || n >= 64) return;
-    if (p->policy == 2) {
+    if (p->policy >= 2) {
+        if (p->policy == 4 && p->drain[b]) return;
         uint32_t i = p->pos[b], last = p->pool[--p->npool];
         p->pool[i] = last;
         p->pos[last] = i;
@@ -124,16 +150,23 @@ static void fm_leave(fm_pool* p, uint32_t b, uint32_t n) {
 }
 static void fm_count(fm_pool* p, uint32_t b, uint32_t n) {
     fm_leave(p, b, p->cnt[b]);
+    if (p->policy == 4) {
+        if (n < p->cnt[b] && n <= FM_DRAIN) p->drain[b] = 1;   /* fell to few objects */
+        if (n == 64 || n == 0) p->drain[b] = 0;               /* filled or emptied */
+    }
     p->cnt[b] = n;
     fm_enter(p, b, n);
 }
 static int64_t fm_alloc(fm_pool* p) {
     int64_t b = -1;
-    if (p->policy == 2) {
-        if (p->npool) {
-            p->rng ^= p->rng << 13; p->rng ^= p->rng >> 7; p->rng ^= p->rng << 17;
-            b = p->pool[p->rng % p->npool];
-        }
+    uint32_t hs = FM_HINTS;
+    if (p->policy >= 3) {
+        hs = (uint32_t)(fm_next(p) % FM_HINTS);
+        const int64_t hb = (int64_t)p->hint[hs] - 1;
+        if (hb >= 0 && p->cnt[hb] > 0 && p->cnt[hb] < 64 && !(p->policy == 4 && p->drain[hb])) b = hb;
+    }
+    if (p->policy >= 2) {
+        if (b < 0 && p->npool) b = p->pool[fm_next(p) % p->npool];
     } else if (p->level_mask) {
         uint32_t q = 63u - (uint32_t)__builtin_clzll(p->level_mask);   /* first fit: the one set */
         b = fm_first(&p->level[q]);
@@ -144,8 +177,10 @@ static int64_t fm_alloc(fm_pool* p) {
         else if (p->nblocks < p->cap) b = p->nblocks++;
         else return -1;
         p->freebits[b] = ~0ull;
+        p->drain[b] = 0;
         p->used++;
     }
+    if (hs < FM_HINTS) p->hint[hs] = (uint32_t)b + 1u;
     uint32_t s = (uint32_t)__builtin_ctzll(p->freebits[b]);
     p->freebits[b] &= ~(1ull << s);
     fm_count(p, (uint32_t)b, p->cnt[b] + 1);
@@ -168,8 +203,8 @@ static uint32_t fm_w0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2) {
 
 int orc_wator_frag(uint32_t w, uint32_t h, uint64_t seed, uint32_t steps, int policy, uint32_t every,
                    double* F_out, uint32_t* fish_out, uint32_t* sharks_out, uint32_t* blocks_out) {
-    if (w == 0 || h == 0 || policy < 0 || policy > 2 || every == 0) return -1;
-    const uint32_t n = w * h, cap = (n + 63) / 64 + 2;
+    if (w == 0 || h == 0 || policy < 0 || policy > 4 || every == 0) return -1;
+    const uint32_t n = w * h, cap = n + 2;   /* a block in use holds an object: blocks <= objects <= n */
     uint8_t* kind = calloc(n, 1);
     uint8_t* eats = calloc(n, 1);
     uint32_t *age = calloc(n, 4), *en = calloc(n, 4), *movers = malloc((size_t)n * 4);

@@ -28,7 +28,7 @@ struct Layout {
     uint64_t M = 0, tiles = 0, bm_stride = 0;
     uint32_t nlevels = 0;
     uint64_t lvl_off[DSOA_MAX_LEVELS] = {0}, lvl_words[DSOA_MAX_LEVELS] = {0};
-    uint64_t off_data = 0, off_slot = 0, off_btype = 0, off_bm = 0, off_R = 0, off_Rocc = 0,
+    uint64_t off_data = 0, off_slot = 0, off_btype = 0, off_drain = 0, off_bm = 0, off_R = 0, off_Rocc = 0,
              off_tcnt = 0, off_toff = 0, off_lb = 0, off_hint = 0, off_grid = 0, off_small = 0, total = 0;
     uint64_t hint_slots = 0;
 };
@@ -108,6 +108,7 @@ bool make_layout(uint64_t M, uint32_t block_bytes, int ntypes, Layout* L) {
     L->off_data = p;  p = align_up(p + M * block_bytes, kAlign);
     L->off_slot = p;  p = align_up(p + M * 8, kAlign);
     L->off_btype = p; p = align_up(p + M * 4, kAlign);
+    L->off_drain = p; p = align_up(p + M, kAlign);
     L->off_bm = p;    p = align_up(p + (uint64_t)nbm * L->bm_stride * 8, kAlign);
     L->off_R = p;     p = align_up(p + M * 4 * (uint64_t)ntypes, kAlign);
     L->off_Rocc = p;  p = align_up(p + M * 8 * (uint64_t)ntypes, kAlign);
@@ -1047,6 +1048,7 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     c.data = base + L.off_data;
     c.slot = (unsigned long long*)(base + L.off_slot);
     c.btype = (uint32_t*)(base + L.off_btype);
+    c.drain = (uint8_t*)(base + L.off_drain);
     c.bm = (unsigned long long*)(base + L.off_bm);
     uint64_t* small = (uint64_t*)(base + L.off_small);
     c.err = (int*)(small + 0);
@@ -1083,6 +1085,7 @@ int dsoa_heap_freeze(dsoa_heap* h) {
     h->meta_bytes = L.total - L.M * block_bytes;
     DSOA_CUDA_TRY(cudaMemsetAsync(c.slot, 0, L.M * 8, h->stream));            // all slots taken
     DSOA_CUDA_TRY(cudaMemsetAsync(c.btype, 0xFF, L.M * 4, h->stream));
+    DSOA_CUDA_TRY(cudaMemsetAsync(c.drain, 0, L.M, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(c.bm, 0, (uint64_t)nbm * L.bm_stride * 8, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(small, 0, kSmallWords * 8, h->stream));
     DSOA_CUDA_TRY(cudaMemsetAsync(c.hint, 0xFF, ((uint64_t)c.hint_mask + 1) * (uint64_t)h->ntypes * sizeof(dsoa_hint),
@@ -1379,7 +1382,7 @@ static const uint64_t kImageMagic = 0x31304D4941534F44ull;   // "DOSAIM01"
 static void image_header(const dsoa_heap* h, dsoa_image_header* H) {
     std::memset(H, 0, sizeof(*H));
     H->magic = kImageMagic;
-    H->version = 2;
+    H->version = 3;
     H->bytes = h->bytes;
     H->M = h->ctx.M;
     H->meta = h->meta_bytes;
@@ -1501,7 +1504,7 @@ int dsoa_set_launch(dsoa_heap* h, int tpb, int ctas_per_sm, int slots_per_thread
 int dsoa_set_flags(dsoa_heap* h, uint32_t flags) {
     if (!h || (flags & ~(DSOA_FLAG_NO_COALESCE | DSOA_FLAG_NO_ROTATE | DSOA_FLAG_NO_HINT | DSOA_FLAG_FUSED |
                          DSOA_FLAG_PDL | DSOA_FLAG_ENUM_TICKETS | DSOA_FLAG_NO_FRESH_GROUP |
-                         DSOA_FLAG_PAPER_R | DSOA_FLAG_R_PER_ROUND)))
+                         DSOA_FLAG_PAPER_R | DSOA_FLAG_R_PER_ROUND | DSOA_FLAG_DRAIN)))
         return DSOA_ERR_INVALID_ARG;
     h->flags = flags;
     return DSOA_OK;

@@ -24,6 +24,7 @@ DEV_OOM, DEV_SPIN, DEV_DOUBLE_FREE, DEV_BAD_HANDLE, DEV_BAD_INDEX = 1, 2, 4, 8, 
 FLAG_NO_COALESCE, FLAG_NO_ROTATE, FLAG_NO_HINT, FLAG_FUSED, FLAG_PDL = 1, 2, 4, 8, 16
 FLAG_ENUM_TICKETS = 32
 FLAG_NO_FRESH_GROUP, FLAG_PAPER_R, FLAG_R_PER_ROUND = 128, 256, 512
+FLAG_DRAIN = 1024
 CHECK_NAMES = ["hier", "free_xor", "multi_type", "active_subset", "type", "free_word",
                "empty_alloc", "active_exact", "tail_bits", "cap_bits"]
 CAPACITY_UNIFORM, CAPACITY_PER_TYPE = 0, 1

@@ -79,6 +79,9 @@ FRAG_VARIANTS = {
     # attempts failed, then takes a fresh block
     "paper_r": D.FLAG_PAPER_R,
     "paper_r_no_hint": D.FLAG_PAPER_R | D.FLAG_NO_HINT,
+    # blocks that fell to an eighth of their capacity drain: searches pass over
+    # them and a warp drops its hint to one
+    "drain": D.FLAG_DRAIN,
 }
 
 
@@ -122,7 +125,7 @@ def ablation(steps=200):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     variants = {"dsoa": 0, "no_coalesce": D.FLAG_NO_COALESCE, "no_rotate": D.FLAG_NO_ROTATE,
                 "no_coalesce_no_rotate": D.FLAG_NO_COALESCE | D.FLAG_NO_ROTATE,
-                "no_hint": D.FLAG_NO_HINT, "fused": D.FLAG_FUSED}
+                "no_hint": D.FLAG_NO_HINT, "fused": D.FLAG_FUSED, "drain": D.FLAG_DRAIN}
     rows, ref = [], None
     for name, fl in variants.items():
         heap, w = _world(heap_bytes=2 << 30, flags=fl)
@@ -194,12 +197,17 @@ def capacity(steps=300):
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("which", choices=["frag", "lookups", "ablation", "heapsize", "capacity", "problemsize"])
+    p.add_argument("--variants", default=None,
+                   help="frag / lookups: comma-separated allocation policies (" + ", ".join(FRAG_VARIANTS) + ")")
     a = p.parse_args()
     build.build()
+    kw = {}
+    if a.variants and a.which in ("frag", "lookups"):
+        kw["variants"] = tuple(a.variants.split(","))
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         res = {"frag": frag_over_time, "lookups": frag_vs_lookups, "ablation": ablation,
-               "heapsize": heap_size, "capacity": capacity, "problemsize": problem_size}[a.which]()
+               "heapsize": heap_size, "capacity": capacity, "problemsize": problem_size}[a.which](**kw)
     print(json.dumps(res))
 
 

@@ -96,7 +96,7 @@ def test_batched_instances_match_alone():
 
 @pytest.mark.parametrize("launch,flags", [(dict(), 16), (dict(scan_tiles=1, waves=8), 16), (dict(scan_tiles=4), 16),
                                           (dict(scan_tiles=5), 0), (dict(scan_tiles=5, waves=8), 16),
-                                          (dict(), 256), (dict(tpb=512, waves=2), 128 | 16)])
+                                          (dict(), 256), (dict(tpb=512, waves=2), 128 | 16), (dict(), 1024)])
 def test_launch_modes_graph_captured(launch, flags):
     """Programmatic dependent launch, the two-kernel and the streamed enumeration:
     a graph-captured generation replayed 30 times equals the oracle."""

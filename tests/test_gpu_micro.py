@@ -101,7 +101,7 @@ def test_scale_variants_agree(method):
     assert_clean(m)
 
 
-@pytest.mark.parametrize("flags", [1, 2, 3, 4, 7, 8, 15, 16, 24, 128, 256, 256 | 4, 384 | 3])
+@pytest.mark.parametrize("flags", [1, 2, 3, 4, 7, 8, 15, 16, 24, 128, 256, 256 | 4, 384 | 3, 1024, 1024 | 4, 1024 | 1])
 def test_ablations_keep_semantics(flags):
     """NoCoal / NoShift / both (Sec. 6.4) change placement and speed, not results:
     every variant, NoShift included, must finish each round with the oracle's

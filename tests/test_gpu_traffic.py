@@ -89,10 +89,10 @@ def test_full_config_sampled_rings():
     assert heap.get_error() == 0
 
 
-@pytest.mark.parametrize("flags", [16, 256, 128 | 16])
+@pytest.mark.parametrize("flags", [16, 256, 128 | 16, 1024])
 def test_launch_flags_keep_semantics(flags):
     """The batch stepped with programmatic dependent launch (16) and / or the
-    allocation-policy experiment flags (128, 256) equals the oracle."""
+    allocation-policy flags (128, 256, 1024) equals the oracle."""
     L = [16, 23, 300, 4096, 5000]
     thr = [int(d * 2**32) for d in (0.3, 0.6, 0.2, 0.1, 0.3)]
     seed = 78

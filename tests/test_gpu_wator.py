@@ -95,7 +95,8 @@ def test_batched_instances_match_alone():
                                           (dict(waves=1), 0), (dict(tpb=128, slots_per_thread=2, waves=16), 0),
                                           (dict(), 16), (dict(tpb=128, scan_tiles=2, waves=8), 16),
                                           (dict(tpb=512, ctas_per_sm=1, waves=1), 20),
-                                          (dict(), 128), (dict(tpb=128, waves=8), 256 | 16), (dict(waves=1), 384 | 4)])
+                                          (dict(), 128), (dict(tpb=128, waves=8), 256 | 16), (dict(waves=1), 384 | 4),
+                                          (dict(), 1024), (dict(scan_tiles=5, waves=8), 1024 | 16)])
 def test_graph_captured_steps_match_oracle(launch, flags):
     """One step captured as a CUDA graph and replayed: the step index lives in
     device memory, so replays advance the simulation exactly like plain steps."""

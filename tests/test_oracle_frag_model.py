@@ -9,7 +9,8 @@ import pytest
 import oracle
 
 
-@pytest.mark.parametrize("policy", ["first_fit", "best_fit", "random_fit"])
+@pytest.mark.parametrize("policy", ["first_fit", "best_fit", "random_fit", "hinted_random_fit",
+                                    "hinted_random_fit_drain"])
 @pytest.mark.parametrize("w,h,seed", [(64, 48, 3), (96, 96, 0x5EED0003)])
 def test_populations_equal_the_oracle_run(policy, w, h, seed):
     steps, every = 60, 5
@@ -28,3 +29,15 @@ def test_random_fit_keeps_more_blocks_than_first_fit():
     b = oracle.wator_frag(128, 128, 200, 11, "random_fit", 50)
     assert np.array_equal(a["fish"], b["fish"])
     assert b["blocks"][-1] >= a["blocks"][-1]
+
+
+def test_draining_keeps_no_more_blocks_than_the_hinted_policy_it_restricts():
+    """Policy 4 is policy 3 with blocks that fell to 8 objects or fewer left out
+    of every choice until they fill or empty: on the same run, fewer blocks stay
+    in use once the first population wave has receded (both runs see the same
+    populations)."""
+    a = oracle.wator_frag(256, 256, 300, 11, "hinted_random_fit", 100)
+    b = oracle.wator_frag(256, 256, 300, 11, "hinted_random_fit_drain", 100)
+    assert np.array_equal(a["fish"], b["fish"]) and np.array_equal(a["sharks"], b["sharks"])
+    assert b["blocks"][-1] <= a["blocks"][-1]
+    assert b["F"][-1] <= a["F"][-1]
