@@ -266,38 +266,88 @@ struct Kill {
     }
 };
 
-// Agents of instance `target` from an explicit grid or from Philox draws.
-__global__ void k_init(dsoa_ctx c, dsoa_wator_args a, uint64_t n) {
-    const dsoa_inst I = a.inst[a.target];
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t cell = (uint32_t)i;
-        uint32_t kind;
-        if (a.init) {
-            kind = a.init[cell];
+// Agents of instance `target` from an explicit grid or from Philox draws.  Every
+// CTA takes tiles of kInitTile cells: each thread draws the kinds of 8
+// consecutive cells, the tile's fish cells and shark cells are compacted into
+// two lists in shared memory, and the agents are then allocated list by list,
+// so that the warps of one allocation request one type only (full warps, one
+// leader reservation per up to 32 agents) instead of a few agents of each type.
+// Every cell is written once: its claim word by the thread that drew it, its
+// occupancy and handle by that thread if empty, else by the thread that
+// allocated its agent (0 if the heap was full).
+constexpr uint32_t kInitTile = 2048;
+
+__device__ __forceinline__ uint32_t init_kind(const dsoa_wator_args& a, const dsoa_inst& I, uint32_t cell) {
+    if (a.init) return a.init[cell];
+    const uint32_t u = dsoa_philox_w0(I.seed, 0xFFFFFFFFu, cell, 0u, 0u);
+    return u < kFishThr ? 1u : (u < kSharkThr ? 2u : 0u);
+}
+
+__device__ __forceinline__ void init_agent(const dsoa_ctx& c, const dsoa_wator_args& a, const dsoa_inst& I,
+                                           uint32_t kind, uint32_t cell) {
+    const dsoa_obj o = dsoa_new(c, (uint32_t)(kind == 1u ? a.fish_type : a.shark_type));
+    if (o) {
+        dsoa_field<uint32_t>(c, o, 0) = a.target;
+        dsoa_field<uint32_t>(c, o, 1) = cell;
+        dsoa_field<uint32_t>(c, o, 2) = 0u;
+        if (kind == 1u) {
+            dsoa_field<uint32_t>(c, o, 3) = kNone;
         } else {
-            const uint32_t u = dsoa_philox_w0(I.seed, 0xFFFFFFFFu, cell, 0u, 0u);
-            kind = u < kFishThr ? 1u : (u < kSharkThr ? 2u : 0u);
+            dsoa_field<uint32_t>(c, o, 3) = kSharkEnergy;
+            dsoa_field<uint32_t>(c, o, 4) = kNone;
+            dsoa_field<uint32_t>(c, o, 5) = 0u;
         }
-        dsoa_obj o = 0;
-        if (kind == 1u || kind == 2u) {
-            o = dsoa_new(c, (uint32_t)(kind == 1u ? a.fish_type : a.shark_type));
-            if (o) {
-                dsoa_field<uint32_t>(c, o, 0) = a.target;
-                dsoa_field<uint32_t>(c, o, 1) = cell;
-                dsoa_field<uint32_t>(c, o, 2) = 0u;
-                if (kind == 1u) {
-                    dsoa_field<uint32_t>(c, o, 3) = kNone;
-                } else {
-                    dsoa_field<uint32_t>(c, o, 3) = kSharkEnergy;
-                    dsoa_field<uint32_t>(c, o, 4) = kNone;
-                    dsoa_field<uint32_t>(c, o, 5) = 0u;
-                }
+    }
+    I.occ[cell] = o ? (uint8_t)kind : 0;
+    I.cellmap[cell] = o;
+}
+
+__global__ void __launch_bounds__(256) k_init(dsoa_ctx c, dsoa_wator_args a, uint64_t n) {
+    __shared__ uint32_t fl[kInitTile], sl[kInitTile];
+    __shared__ uint32_t wcount[8];
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const dsoa_inst I = a.inst[a.target];
+    const uint64_t tiles = (n + kInitTile - 1) / kInitTile;
+    for (uint64_t tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
+        const uint64_t c0 = tl * kInitTile + (uint64_t)tid * 8u;
+        uint32_t kinds = 0, own = 0;                /* 2 bits per cell; fish | sharks << 16 */
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint64_t cell = c0 + i;
+            uint32_t k = 0;
+            if (cell < n) {
+                k = init_kind(a, I, (uint32_t)cell);
+                I.claim[cell] = kNone;
+                if (k != 1u && k != 2u) { I.occ[cell] = 0; I.cellmap[cell] = 0; k = 0; }
             }
+            kinds |= k << (2 * i);
+            own += k == 1u ? 1u : (k == 2u ? 0x10000u : 0u);
         }
-        I.occ[cell] = o ? (uint8_t)kind : 0;
-        I.cellmap[cell] = o;
-        I.claim[cell] = kNone;
+        uint32_t x = own;                           /* inclusive warp scan of both counts */
+#pragma unroll
+        for (uint32_t o = 1; o < 32u; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31u) wcount[warp] = x;
+        __syncthreads();
+        uint32_t pos = x - own, total = 0;
+        for (uint32_t w = 0; w < 8u; ++w) {
+            if (w < warp) pos += wcount[w];
+            total += wcount[w];
+        }
+        uint32_t pf = pos & 0xFFFFu, ps = pos >> 16;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t k = (kinds >> (2 * i)) & 3u;
+            if (k == 1u) fl[pf++] = (uint32_t)(c0 + i);
+            else if (k == 2u) sl[ps++] = (uint32_t)(c0 + i);
+        }
+        __syncthreads();
+        const uint32_t nf = total & 0xFFFFu, ns = total >> 16;
+        for (uint32_t i = tid; i < nf; i += blockDim.x) init_agent(c, a, I, 1u, fl[i]);
+        for (uint32_t i = tid; i < ns; i += blockDim.x) init_agent(c, a, I, 2u, sl[i]);
+        __syncthreads();                            /* lists and counts reused */
     }
 }
 
@@ -405,8 +455,10 @@ int dsoa_wator_kernel(dsoa_heap* h, int kernel, uint64_t n, const void* a, size_
             if (args.target >= args.n_inst || args.fish_type < 0 || args.fish_type >= h->ntypes ||
                 args.shark_type < 0 || args.shark_type >= h->ntypes)
                 return DSOA_ERR_INVALID_ARG;
-            const int tpb = 256;
-            k_init<<<dsoa_new_grid(h, n, tpb), tpb, 0, h->stream>>>(dsoa_launch_ctx(h), args, n);
+            const uint64_t tiles = (n + kInitTile - 1) / kInitTile;
+            const uint64_t resident = (uint64_t)std::max(1, dsoa_resident_ctas(reinterpret_cast<const void*>(&k_init), 256)) *
+                                      (uint64_t)h->num_sms;
+            k_init<<<(unsigned)std::min(tiles, resident), 256, 0, h->stream>>>(dsoa_launch_ctx(h), args, n);
             return dsoa_check_launch(h);
         }
         case DSOA_K_WATOR_BIRTHS: {

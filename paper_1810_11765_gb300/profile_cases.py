@@ -55,16 +55,21 @@ def case_doall(log2n: int, holes: bool, iters: int, method: str = "vec"):
 def case_wator(side: int, steps: int, defer: bool = False, flush: bool = False):
     """`flush`: a 256 MiB write before every step, as between the benchmark's timed
     steps, so that a capture without cache control sees each kernel's DRAM traffic
-    as it is inside a benchmarked step (the first kernel to touch a line reads it)."""
+    as it is inside a benchmarked step (the first kernel to touch a line reads it).
+    A read of a second 256 MiB buffer follows the write, so that the write's dirty
+    lines are written back before the step and not counted as the step kernels'
+    DRAM writes."""
     heap = D.Heap(512 << 20)
     w = WatorWorld(heap)
     w.defer_births = defer
     heap.freeze()
     w.add(side, side, 0x5EED0003)
     buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda") if flush else None
+    rd = torch.ones(64 << 20, dtype=torch.int32, device="cuda") if flush else None
     for _ in range(steps):
         if buf is not None:
             buf.zero_()
+            rd.sum()
         a, b = _ev(), _ev()
         a.record()
         w.step()
