@@ -130,8 +130,10 @@ struct dsoa_ctx {
 #ifndef DSOA_DOALL_MAXNREG
 #define DSOA_DOALL_MAXNREG 48
 #endif
+#ifndef DSOA_FRESH_GROUP
 #define DSOA_FRESH_GROUP 16u              /* group size that takes a fresh block
                                              after a lost race (leader_reserve)    */
+#endif
 #define DSOA_FLAG_NO_COALESCE 1u          /* ablation: one request per leader       */
 #define DSOA_FLAG_NO_ROTATE 2u            /* ablation: plain find-first-set         */
 #define DSOA_FLAG_NO_HINT 4u              /* ablation: no per-warp block hint       */
