@@ -78,6 +78,26 @@ def test_full_config_1024_500():
     assert all(v == 0 for v in heap.check().values())
 
 
+@pytest.mark.parametrize("flags", [1024, 256 | 4, 2])
+def test_full_config_under_allocation_policies(flags):
+    """The configured workload (1024 x 1024, 500 steps) with blocks left to drain
+    (1024), with Alg. 1's reading of r and no hint (256 | 4), and without bitmap
+    rotation (2): placement changes, the result is the oracle's."""
+    cfg, (ref, st) = full_reference()
+    heap, w = world(512 << 20)
+    heap.set_flags(flags)
+    s = w.add(cfg.width, cfg.height, cfg.seed)
+    for k in range(cfg.steps):
+        w.step()
+        if k % 100 == 99:
+            assert w.counts() == (st[k]["fish"], st[k]["sharks"]), k
+    assert np.array_equal(w.read(s), ref)
+    assert heap.get_error() == 0
+    assert all(v == 0 for v in heap.check().values())
+    host = host_check(heap, 2)
+    assert all(v == 0 for v in host["violations"].values()), host
+
+
 def test_batched_instances_match_alone():
     heap, w = world(64 << 20, capacity=3)
     specs = [(50, 40, 31), (128, 64, 32), (17, 90, 33)]
