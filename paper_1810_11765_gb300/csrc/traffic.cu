@@ -36,8 +36,20 @@ struct Move {
         const uint32_t pos = *posp;
         if (!dsoa_index_ok(c, pos, L)) return;
         uint32_t v = min(*vp + 1u, kVmax);                 // accelerate
-        uint32_t gap = 0;                                  // free cells ahead
-        while (gap < v && !cur[b + (pos + gap + 1u) % L]) ++gap;
+        // free cells ahead: the kVmax cells in front are read at once (independent
+        // loads, one round trip) and scanned in registers, instead of one load per
+        // cell that waits for the previous one
+        uint8_t ahead[kVmax];
+#pragma unroll
+        for (uint32_t k = 0; k < kVmax; ++k) {
+            uint32_t q = pos + 1u + k;
+            if (q >= L) q %= L;
+            ahead[k] = cur[b + q];
+        }
+        uint32_t gap = v;
+#pragma unroll
+        for (uint32_t k = kVmax; k-- > 0;)
+            if (k < v && ahead[k]) gap = k;
         v = min(v, gap);                                   // brake
         if (v > 0u && dsoa_philox_w0(a.seed, step, pos, i, 1u) < a.slow_thr) v -= 1u;  // dawdle
         const uint32_t np = (pos + v) % L;                 // move
